@@ -1,0 +1,75 @@
+"""Solvers around the operator (test infrastructure only).
+
+* cg: plain Hestenes-Stiefel conjugate gradients, as used for each linear system
+  in Sec. 5.3 (the paper states neither tolerance nor initial guess; reading:
+  x0 = 0 for the Poisson problem, relative 2-norm residual test).
+* allen_cahn_step: the semi-implicit step
+  (I + tau eps^2 A) u^{n+1} = u^n + tau (u^n - (u^n)^3) for
+  u_t = -eps^2 (-Delta)^{alpha/2} u + u - u^3 with u = 0 outside the box; the
+  paper's own model (eqs. AC-1, AC-2) uses Crank-Nicolson and u = -1 outside,
+  this is the semi-implicit variant of the same equation.
+* strang_symbol / strang_solve: the multilevel Strang circulant of the Toeplitz
+  matrix (first column t_{min(j, n-j)} per axis), inverted by FFTs of size n.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def cg(apply, f: np.ndarray, x0=None, rtol: float = 1e-10, maxit: int = 100000, precond=None):
+    """Solve A x = f; returns (x, iterations, true relative residual ||f - A x|| / ||f||).
+
+    With `precond` (a callable z = M^-1 r) this is preconditioned CG.
+    """
+    x = np.zeros_like(f) if x0 is None else x0.copy()
+    r = f - apply(x) if x0 is not None else f.copy()
+    z = precond(r) if precond is not None else r
+    p = z.copy()
+    rz = float(np.vdot(r, z))
+    nf = float(np.linalg.norm(f))
+    it = 0
+    while it < maxit and np.linalg.norm(r) > rtol * nf:
+        q = apply(p)
+        a = rz / float(np.vdot(p, q))
+        x += a * p
+        r -= a * q
+        z = precond(r) if precond is not None else r
+        rz_new = float(np.vdot(r, z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+    relres = float(np.linalg.norm(f - apply(x)) / nf) if nf > 0 else 0.0
+    return x, it, relres
+
+
+def allen_cahn_rhs(u: np.ndarray, tau: float) -> np.ndarray:
+    """u + tau (u - u^3)."""
+    return u + tau * (u - u ** 3)
+
+
+def allen_cahn_step(apply, u: np.ndarray, tau: float, eps: float, rtol: float = 1e-10, maxit: int = 10000):
+    """One semi-implicit step: solve (I + tau eps^2 A) v = u + tau (u - u^3) by CG from v0 = u."""
+    rhs = allen_cahn_rhs(u, tau)
+    s = tau * eps * eps
+
+    def shifted(v):
+        return v + s * apply(v)
+
+    v, it, rel = cg(shifted, rhs, x0=u, rtol=rtol, maxit=maxit)
+    return v, it, rel
+
+
+def strang_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
+    """Eigenvalues of the multilevel Strang circulant of A (size n_r per axis).
+
+    Its first column keeps, along each axis, the Toeplitz entry of offset
+    min(j, n_r - j): the central diagonals of A, wrapped around.
+    """
+    idx = [np.minimum(np.arange(nr), nr - np.arange(nr)) for nr in shape]
+    col = -c * coef[np.ix_(*idx)]
+    return np.fft.fftn(col).real
+
+
+def strang_solve(lam_s: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """z = C^-1 r for the Strang circulant with eigenvalues lam_s."""
+    return np.fft.ifftn(np.fft.fftn(r) / lam_s).real
