@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Throughput of the FFT Toeplitz apply of the fractional-Laplacian scheme on one GB300.
+
+Default workload: 2D, alpha = 1.5, Omega = (-1,1)^2, h = 2/2048 (2047 x 2047 interior
+unknowns), FP64 apply y = A u through libfrlap (the 2D throughput case of the 3D
+FP64 CG configuration).  One step = a batch of 8 applies to 8 distinct seeded
+N(0,1) vectors (268 MB of inputs, more than the 129 MB L2).  Reported: apply
+unknowns/s over all ranks, the per-kernel roofline of the dominant kernel, the
+same metric end to end through host buffers, and the CPU oracle timed on the
+host cores.  Extra lines (FP32 apply, 3D 255^3 applies, CG solve times) are
+measured after the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl frlap|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import frlap_inputs as inp  # noqa: E402
+
+ALPHA = 1.5
+NGRID = 2048
+BATCH = 8
+METRIC = "apply unknowns/s & %HBM peak; PCG time to 1e-10 of FP64 sol vs plain FP64 CG"
+UNIT = "unknowns/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fft_flops_2d(n, P):
+    """Algorithmic flops of one 2D apply, radix-2 convention 5 L log2 L per complex transform of length L
+    (a real transform of length L counts half)."""
+    nx, ny = n
+    Px, Py = P
+    Hx1 = Px // 2 + 1
+    f_rows = ny * 2.5 * Px * math.log2(Px)
+    f_cols = Hx1 * (2 * 5 * Py * math.log2(Py) + 2 * Py)
+    return {"r2c": f_rows, "colmul": f_cols, "c2r": f_rows}
+
+
+def stage_names(d):
+    return ["r2c_T", "colmul", "c2r_T"] if d == 2 else ["r2c_T", "c2cT_fwd", "colmul", "c2cT_inv", "c2r_T"]
+
+
+def stage_bytes(d, n, P, eb):
+    """Bytes each stage must move (read + write) in the pass model: real in/out eb bytes, complex 2 eb."""
+    cb = 2 * eb
+    if d == 2:
+        nx, ny = n
+        Px, Py = P
+        H1 = Px // 2 + 1
+        M = nx * ny
+        s1 = H1 * ny
+        lam = H1 * (Py // 2 + 1) * eb
+        return [M * eb + s1 * cb, 2 * s1 * cb + lam, s1 * cb + M * eb]
+    nx, ny, nz = n
+    Px, Py, Pz = P
+    H1 = Px // 2 + 1
+    M = nx * ny * nz
+    s1 = H1 * ny * nz
+    s2 = H1 * Py * nz
+    lam = H1 * (Py // 2 + 1) * (Pz // 2 + 1) * eb
+    return [M * eb + s1 * cb, s1 * cb + s2 * cb, 2 * s2 * cb + lam, s2 * cb + s1 * cb, s1 * cb + M * eb]
+
+
+def stage_flops(d, n, P):
+    if d == 2:
+        f = fft_flops_2d(n, P)
+        return [f["r2c"], f["colmul"], f["c2r"]]
+    nx, ny, nz = n
+    Px, Py, Pz = P
+    H1 = Px // 2 + 1
+    rows = ny * nz * 2.5 * Px * math.log2(Px)
+    yf = H1 * nz * 5 * Py * math.log2(Py)
+    zc = H1 * Py * (2 * 5 * Pz * math.log2(Pz) + 2 * Pz)
+    return [rows, yf, zc, yf, rows]
+
+
+# ----------------------------------------------------------------------------- reference arm (CPU oracle)
+def oracle_apply_setup(d, N, alpha):
+    from oracle import fast, scheme
+    h = 2.0 / N
+    a = scheme.coefficients(d, alpha, h, N)
+    c = scheme.c_d_alpha(d, alpha)
+    Ns = (N,) * d
+    op = fast.FastOperator(a, c, tuple(N - 1 for _ in range(d)))
+    return op, Ns
+
+
+def cpu_oracle_rate(d=2, N=NGRID, alpha=ALPHA, budget_s=15.0, min_applies=1):
+    op, Ns = oracle_apply_setup(d, N, alpha)
+    u = inp.normal_field(Ns, seed=2)
+    M = u.size
+    t0 = time.perf_counter()
+    count = 0
+    while count < min_applies or time.perf_counter() - t0 < budget_s:
+        op(u)
+        count += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": count * M / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{count} FP64 applies of the {N - 1}^{d} alpha={alpha} NumPy-FFT oracle "
+                      f"(circulant embedding, pocketfft single thread) in {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    op, Ns = oracle_apply_setup(2, NGRID, ALPHA)
+    u = inp.normal_field(Ns, seed=2)
+    M = u.size
+    for _ in range(args.warmup):
+        op(u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op(u)  # one step = one apply (a bounded sample of the 8-apply batch)
+    dt = time.perf_counter() - t0
+    value = args.steps * M / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"2D {NGRID - 1}^2 alpha={ALPHA} FP64 apply, CPU oracle",
+                                             "step": "1 apply", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} NumPy-FFT oracle applies after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def time_applies(fl, torch, plan, U, Y, work, steps, warmup, d, barrier=None):
+    """Time `steps` steps of len(U) applies; returns (total_ms, per-stage mean ms, launches)."""
+    ns = fl.frlap_apply_nstages(plan)
+    stream = torch.cuda.current_stream()
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)] for _ in U] for _ in range(steps)]
+    for step in evs:  # create the events
+        for row in step:
+            for e in row:
+                e.record(stream)
+    for _ in range(warmup):
+        for u, y in zip(U, Y):
+            fl.frlap_apply(plan, u, y, work)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        for b, (u, y) in enumerate(zip(U, Y)):
+            fl.frlap_apply_profiled(plan, u, y, work, evs[k][b])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    total = e0.elapsed_time(e1)
+    st = [statistics.mean(evs[k][b][s].elapsed_time(evs[k][b][s + 1]) for k in range(steps) for b in range(len(U)))
+          for s in range(ns)]
+    return total, st, steps * len(U) * ns
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="frlap", choices=["frlap", "reference"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1804_02718_gb300 as fl
+    from paper_1804_02718_gb300 import build as _build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    barrier = (lambda: dist.barrier()) if dist else None
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+
+    prec = fl.FRLAP_F32 if args.prec == "f32" else fl.FRLAP_F64
+    dt = torch.float32 if args.prec == "f32" else torch.float64
+    eb = 4 if args.prec == "f32" else 8
+    h = 2.0 / NGRID
+    Ns = (NGRID, NGRID)
+    plan = fl.Plan(2, ALPHA, h, Ns, prec=prec)
+    U = [torch.from_numpy(inp.normal_field(Ns, seed=100 + b)).to("cuda", dt) for b in range(BATCH)]
+    Y = [torch.empty_like(u) for u in U]
+    work = plan.workspace(fl.FRLAP_OP_APPLY)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, stage_ms, launches = time_applies(fl, torch, plan, U, Y, work, args.steps, args.warmup, 2, barrier)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    M = plan.M
+    value = world * args.steps * BATCH * M / (total_ms / 1e3)
+
+    # roofline of the dominant kernel
+    names = stage_names(2)
+    sb = stage_bytes(2, plan.n, plan.P, eb)
+    sf = stage_flops(2, plan.n, plan.P)
+    dom = int(np.argmax(stage_ms))
+    hbm, hbm_src = peaks()
+    if args.prec == "f64":
+        ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe from unit count x max clock (DESIGN.md)",
+                "flops_per_launch": sf[dom]}
+    else:
+        ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom]}
+    apply_ms = sum(stage_ms)
+    model_bytes = sum(sb)
+    kernels = {nm: {"ms": round(ms, 5), "model_GBps": round(b / (ms / 1e3) / 1e9, 1),
+                    "GFLOPps": round(f / (ms / 1e3) / 1e9, 1)} for nm, ms, b, f in zip(names, stage_ms, sb, sf)}
+
+    # end to end through host buffers (pinned), same batch, H2D + applies + D2H each step
+    e2e = None
+    if rank == 0 or world > 1:
+        Uh = [u.cpu().pin_memory() for u in U]
+        Yh = [torch.empty_like(u).pin_memory() for u in Uh]
+        Ud = [torch.empty_like(u) for u in U]
+        ksteps = max(2, min(args.steps, 10))
+        for _ in range(2):
+            for b in range(BATCH):
+                Ud[b].copy_(Uh[b], non_blocking=True)
+                fl.frlap_apply(plan, Ud[b], Y[b], work)
+                Yh[b].copy_(Y[b], non_blocking=True)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(ksteps):
+            for b in range(BATCH):
+                Ud[b].copy_(Uh[b], non_blocking=True)
+                fl.frlap_apply(plan, Ud[b], Y[b], work)
+                Yh[b].copy_(Y[b], non_blocking=True)
+        z.record()
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(z)
+        e2e = {"value": world * ksteps * BATCH * M / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": BATCH * M * eb, "d2h_bytes_per_step": BATCH * M * eb, "steps": ksteps}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(fl, torch, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": f"2D {NGRID - 1}x{NGRID - 1} alpha={ALPHA} {args.prec.upper()} FFT Toeplitz apply",
+                       "batch_per_step": BATCH, "embedding": list(plan.P),
+                       "l2": "inputs larger than L2 (8 distinct 2047^2 vectors per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "apply": {"ms": apply_ms, "model_bytes": model_bytes,
+                      "model_GBps": model_bytes / (apply_ms / 1e3) / 1e9,
+                      "frac_of_hbm_model": model_bytes / (apply_ms / 1e3) / 1e9 / hbm, "kernels": kernels},
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_extras(fl, torch, args):
+    """Secondary measurements (not part of the timed region): FP32 / 3D applies and CG solves."""
+    out = {}
+    cases = [("apply_2047^2_f32", 2, NGRID, fl.FRLAP_F32, 8), ("apply_255^3_f64", 3, 256, fl.FRLAP_F64, 1),
+             ("apply_255^3_f32", 3, 256, fl.FRLAP_F32, 2)]
+    if args.prec == "f32":
+        cases[0] = ("apply_2047^2_f64", 2, NGRID, fl.FRLAP_F64, 8)
+    hbm, _ = peaks()
+    for name, d, N, prec, batch in cases:
+        dt = torch.float32 if prec == fl.FRLAP_F32 else torch.float64
+        eb = 4 if prec == fl.FRLAP_F32 else 8
+        plan = fl.Plan(d, ALPHA if d == 2 else 1.0, 2.0 / N, (N,) * d, prec=prec)
+        U = [torch.randn(plan.shape, dtype=dt, device="cuda") for _ in range(batch)]
+        Y = [torch.empty_like(u) for u in U]
+        work = plan.workspace(fl.FRLAP_OP_APPLY)
+        steps = 5 if (d == 3 and prec == fl.FRLAP_F64) else 10
+        total, st, _ = time_applies(fl, torch, plan, U, Y, work, steps, 2, d)
+        sb = stage_bytes(d, plan.n, plan.P, eb)
+        ms = sum(st)
+        out[name] = {"unknowns_per_s": plan.M / (ms / 1e3), "ms": ms, "model_GBps": sum(sb) / (ms / 1e3) / 1e9,
+                     "frac_of_hbm_model": sum(sb) / (ms / 1e3) / 1e9 / hbm,
+                     "kernels_ms": [round(v, 5) for v in st]}
+        del plan, U, Y, work
+        torch.cuda.empty_cache()
+    # CG: 63^2, f = 1 (configs[0]) and 2047^2 Gaussian-sum f, plain FP64 CG vs FP32-inner refinement
+    for name, N, f_kind, solver in [("cg_63^2_f1_fp64", 64, "one", fl.FRLAP_SOLVE_CG),
+                                    ("cg_2047^2_gauss_fp64", 2048, "gauss", fl.FRLAP_SOLVE_CG),
+                                    ("ir_2047^2_gauss_fp32inner", 2048, "gauss", fl.FRLAP_SOLVE_IR)]:
+        h = 2.0 / N
+        prec = fl.FRLAP_MIXED if solver == fl.FRLAP_SOLVE_IR else fl.FRLAP_F64
+        plan = fl.Plan(2, ALPHA, h, (N, N), prec=prec)
+        f = inp.constant_field((N, N)) if f_kind == "one" else inp.gaussian_sum_field((N, N), h, seed=3)
+        ft = torch.from_numpy(f).cuda()
+        x = torch.zeros_like(ft)
+        fl.frlap_pcg_solve(plan, ft, x.clone(), rtol=1e-10, solver=solver, inner_rtol=1e-4, raise_on_error=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, it, rel, code = fl.frlap_pcg_solve(plan, ft, x, rtol=1e-10, solver=solver, inner_rtol=1e-4,
+                                              raise_on_error=False)
+        torch.cuda.synchronize()
+        out[name] = {"s": time.perf_counter() - t0, "iters": it, "relres": rel, "status": code}
+        del plan
+        torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    main()

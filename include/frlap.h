@@ -1,0 +1,160 @@
+/*
+ * frlap -- GB300 (sm_103a) library for the finite-difference integral fractional
+ * Laplacian of Duo & Zhang, "Accurate numerical methods for two and three
+ * dimensional integral fractional Laplacian with applications" (arXiv:1804.02718).
+ *
+ * The operator: on the box Omega = prod_r (a_r, a_r + N_r h) with u = 0 outside,
+ * the scheme of eq. fLh-2D (2D) / eq. fLh-3D (3D) is the matrix-vector product
+ * y = A u with the symmetric multilevel Toeplitz matrix A[i,j] = -c_{d,alpha} a_{|i-j|}
+ * (eqs. A-2D, Aj, A-3D, Aj-3D); a_k are the coefficients of eqs. amn, a00
+ * (2D) and a_mns, a000 (3D); c_{d,alpha} is the constant of Sec. 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - d is 2 or 3.  N[r] (r = 0 is x, 1 is y, 2 is z) is the number of mesh
+ *    intervals along axis r, 2 <= N[r] <= 4096 (2D) or 1024 (3D), so there are n_r = N[r] - 1 interior
+ *    unknowns along axis r.  The grid vector u is stored x fastest: a C-order
+ *    array [n_z][n_y][n_x] (3D) or [n_y][n_x] (2D), as in eq. product / A3D.
+ *    h > 0 is the mesh size; the coefficient table uses N_max = max_r N[r]
+ *    (the paper's L = N_max h is the longest side).
+ *  - 0 < alpha < 2 and alpha < gamma <= 2 (gamma = 2 is the paper's default;
+ *    Sec. 5 uses it throughout).
+ *  - Every pointer named d_* is a DEVICE pointer owned by the caller; the
+ *    library never frees it.  Pointers to host scalars (iters, relres) are
+ *    host pointers.  `stream` is a cudaStream_t (NULL = legacy default stream);
+ *    all work is enqueued on it and entry points return without waiting,
+ *    except where a host scalar output is written (they synchronise `stream`).
+ *  - Only the set-up calls frlap_plan_create and frlap_coeffs allocate device
+ *    memory (frlap_coeffs: stream-ordered scratch, freed before it returns);
+ *    the scratch every other call needs is the caller's d_work buffer of at
+ *    least frlap_workspace_bytes() bytes, 256-byte aligned.
+ *  - Errors are reported by the return code; frlap_last_error() gives a
+ *    message for the calling thread.  No C++ exception crosses this boundary.
+ *    Invalid arguments return FRLAP_EINVAL before anything is enqueued.
+ */
+#ifndef FRLAP_H
+#define FRLAP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FRLAP_OK = 0,
+  FRLAP_EINVAL = 1,      /* bad argument (d, alpha, gamma, h, N, sizes, null pointers) */
+  FRLAP_ENOMEM = 2,      /* device allocation in frlap_plan_create failed */
+  FRLAP_EWORKSPACE = 3,  /* d_work is NULL or misaligned */
+  FRLAP_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+  FRLAP_ENOCONV = 5,     /* iterative solver hit maxit before reaching rtol */
+  FRLAP_EBREAKDOWN = 6,  /* CG breakdown: p^T A p <= 0 or non-finite */
+  FRLAP_ENAN = 7,        /* non-finite value in the right-hand side or iterate */
+  FRLAP_ETIMEOUT = 8     /* a bounded device-side wait expired */
+} frlap_status;
+
+/* Arithmetic of the FFT apply.  F64: IEEE double everywhere.  F32: single
+ * precision FFT stages and symbol.  MIXED: a plan that holds both, so
+ * that the iterative-refinement solver can run FP32 inner applies and FP64
+ * outer residuals (coefficients and symbol are always generated in FP64). */
+typedef enum { FRLAP_F64 = 0, FRLAP_F32 = 1, FRLAP_MIXED = 2 } frlap_prec;
+
+/* Which scratch size frlap_workspace_bytes reports. */
+typedef enum { FRLAP_OP_APPLY = 0, FRLAP_OP_PCG = 1, FRLAP_OP_AC = 2 } frlap_op;
+
+/* Solver variants of frlap_pcg_solve. */
+typedef enum {
+  FRLAP_SOLVE_CG = 0,      /* plain FP64 conjugate gradients (Sec. 5.3: CG with the FFT product) */
+  FRLAP_SOLVE_IR = 1       /* FP64 iterative refinement around FP32 CG (MIXED plans) */
+} frlap_solver;
+
+typedef struct frlap_plan frlap_plan;
+
+/* c_{d,alpha} = 2^(alpha-1) alpha Gamma((d+alpha)/2) / (pi^(d/2) Gamma(1-alpha/2))
+ * (Sec. 1, the normalisation constant of eq. fL-nD).  Host-only, no device work.
+ * Returns FRLAP_EINVAL unless d in {2,3} and 0 < alpha < 2. */
+frlap_status frlap_c_dalpha(int d, double alpha, double* out);
+
+/* The coefficients a_k of the scheme, k in [0, N_max]^d, in FP64, for mesh size h:
+ *   a_k = 2^sigma(k) / (2^d |h k|^gamma) * (int_{T_k} |xi|^(gamma-d-alpha) dxi + kappa_k w_0)  (k != 0)
+ *   a_0 = - sum_{k != 0} 2^(d - sigma(k)) a_k - 2^d int_{D_2} |xi|^-(d+alpha) dxi
+ * (Sec. 2 eqs. amn, a00; Sec. 4 a_mns, a000), sigma(k) = number of zero
+ * components of k, T_k = the elements of (0, N_max h)^d having h k as a vertex,
+ * kappa_k the origin correction (gamma = 2: +1 in 2D / +5/3 in 3D on unit axis
+ * offsets, -1 on the other vertices of the origin element, including (1,1,1); gamma < 2: 0).
+ * Output d_coeffs: (N_max+1)^d doubles, C-order with the x offset fastest.
+ * Computed entirely on the device (quadrature, assembly, reduction for a_0). */
+frlap_status frlap_coeffs(int d, double alpha, double gamma, double h, const int* N,
+                          double* d_coeffs, void* stream);
+
+/* Create a plan: coefficients, the real symbol lambda of the circulant
+ * embedding of A (size P_r = max(32, next power of two >= 2 n_r - 1) per axis,
+ * stored as its (P_r/2+1)-per-axis octant, 1/prod(P_r) folded in), FFT
+ * twiddle tables.  Allocates the plan's device memory (set-up call).
+ * `*out` receives the plan; destroy it with frlap_plan_destroy. */
+frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, const int* N, int prec,
+                               void* stream, frlap_plan** out);
+frlap_status frlap_plan_destroy(frlap_plan* plan);
+
+/* Bytes of caller-provided scratch needed by `op` on this plan (0 on a NULL plan). */
+size_t frlap_workspace_bytes(const frlap_plan* plan, int op);
+
+/* Interior sizes n_r and embedding sizes P_r of a plan (either may be NULL). */
+frlap_status frlap_plan_shape(const frlap_plan* plan, int* n, int* P);
+
+/* Copy the symbol octant (prod_r (P_r/2+1) doubles, x fastest, including the
+ * 1/prod(P_r) factor) into d_lambda.  For tests and for building preconditioners. */
+frlap_status frlap_plan_symbol(const frlap_plan* plan, double* d_lambda, void* stream);
+
+/* y = A u on the interior nodes (eq. product / A3D), computed by the FFT of
+ * the circulant embedding: zero-pad u to P_r per axis, forward real-to-complex
+ * FFT along x, complex FFTs along y (and z), multiply by lambda, inverse FFTs,
+ * keep the first n_r entries per axis.  d_u, d_y: prod(n_r) elements of double
+ * (F64 and MIXED plans) or float (F32 plans); they must not overlap. */
+frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream);
+
+/* Number of kernel stages of one apply (2D: 3, 3D: 5): pad + real FFT along x,
+ * the FFT/multiply stages along y (and z), inverse real FFT along x + crop. */
+int frlap_apply_nstages(const frlap_plan* plan);
+
+/* frlap_apply with timing marks: events[i] (a cudaEvent_t, or NULL to skip) is
+ * recorded on `stream` just before stage i, events[nstages] after the last
+ * stage.  The caller creates the events; the array must hold nstages+1 entries. */
+frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream,
+                                  void* const* events);
+
+/* Same product in FP32 on a MIXED plan (float in, float out). */
+frlap_status frlap_apply_f32(const frlap_plan* plan, const float* d_u, float* d_y, void* d_work, void* stream);
+
+/* Solve A x = f (the fractional Poisson problem eqs. Poisson, BCP, discretised
+ * by the scheme) by conjugate gradients with the FFT product (Sec. 5.3).
+ * d_f, d_x: prod(n_r) doubles; d_x holds the initial guess on entry and the
+ * solution on exit.  Stops when ||f - A x||_2 <= rtol ||f||_2 (recursive
+ * residual, then confirmed with a true FP64 residual), or after maxit iterations.
+ * solver = FRLAP_SOLVE_CG (any plan but F32) or FRLAP_SOLVE_IR (MIXED plans: FP32 CG
+ * inner solves to inner_rtol, FP64 outer residual and update).
+ * *iters (may be NULL) receives the CG iterations (IR: total inner iterations),
+ * *relres (may be NULL) the final true relative residual.  Synchronises stream.
+ * Returns FRLAP_ENOCONV if rtol was not reached. */
+frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* d_x, double rtol, int maxit,
+                             int solver, double inner_rtol, int* iters, double* relres, void* d_work,
+                             void* stream);
+
+/* nsteps semi-implicit steps of the fractional Allen-Cahn equation
+ * u_t = -eps^2 (-Delta)^{alpha/2} u + u - u^3 with u = 0 outside the box:
+ * (I + tau eps^2 A) u^{n+1} = u^n + tau (u^n - (u^n)^3), each solved by CG
+ * from u^n to relative residual rtol (the paper's model, eqs. AC-1/AC-2, steps
+ * with Crank-Nicolson and CG; this is the semi-implicit form of the same
+ * space discretisation).  d_u: prod(n_r) doubles, updated in place.
+ * *iters (may be NULL): total CG iterations.  Synchronises stream. */
+frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double tau, double eps, int nsteps,
+                                   double rtol, int* iters, void* d_work, void* stream);
+
+/* The message for the last error on the calling thread ("" if none). */
+const char* frlap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRLAP_H */

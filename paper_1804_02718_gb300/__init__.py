@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) library for the Duo & Zhang finite-difference integral fractional Laplacian.
+
+The compute path is the CUDA library libfrlap.so (C ABI in include/frlap.h); this
+package is its thin Python binding.  Build the library with
+`paper_1804_02718_gb300.build.build()` (nvcc, sm_103a); every call raises if it
+is missing -- there is no CPU fallback.
+"""
+from ._binding import (  # noqa: F401
+    FRLAP_F32, FRLAP_F64, FRLAP_MIXED, FRLAP_OP_AC, FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_SOLVE_CG,
+    FRLAP_SOLVE_IR, LIB_PATH, STATUS, FrlapError, Plan, frlap_allen_cahn_step, frlap_apply, frlap_apply_f32,
+    frlap_apply_nstages, frlap_apply_profiled,
+    frlap_c_dalpha, frlap_coeffs, frlap_pcg_solve, frlap_plan_create, frlap_plan_destroy,
+    frlap_workspace_bytes, lib,
+)

@@ -1,0 +1,258 @@
+"""ctypes binding of libfrlap (include/frlap.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module passes device
+pointers (torch tensors' data_ptr()), sizes and the current CUDA stream, and
+turns status codes into exceptions.  There is no CPU fallback: if the shared
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfrlap.so")
+
+FRLAP_F64, FRLAP_F32, FRLAP_MIXED = 0, 1, 2
+FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_OP_AC = 0, 1, 2
+FRLAP_SOLVE_CG, FRLAP_SOLVE_IR = 0, 1
+
+STATUS = {
+    0: "FRLAP_OK", 1: "FRLAP_EINVAL", 2: "FRLAP_ENOMEM", 3: "FRLAP_EWORKSPACE", 4: "FRLAP_ECUDA",
+    5: "FRLAP_ENOCONV", 6: "FRLAP_EBREAKDOWN", 7: "FRLAP_ENAN", 8: "FRLAP_ETIMEOUT",
+}
+
+# every symbol the header declares, with its ctypes signature
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "frlap_c_dalpha": (_I, [_I, _D, ctypes.POINTER(_D)]),
+    "frlap_coeffs": (_I, [_I, _D, _D, _D, ctypes.POINTER(_I), _P, _P]),
+    "frlap_plan_create": (_I, [_I, _D, _D, _D, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)]),
+    "frlap_plan_destroy": (_I, [_P]),
+    "frlap_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
+    "frlap_plan_shape": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "frlap_plan_symbol": (_I, [_P, _P, _P]),
+    "frlap_apply": (_I, [_P, _P, _P, _P, _P]),
+    "frlap_apply_f32": (_I, [_P, _P, _P, _P, _P]),
+    "frlap_apply_nstages": (_I, [_P]),
+    "frlap_apply_profiled": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
+    "frlap_allen_cahn_step": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), _P, _P]),
+    "frlap_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class FrlapError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libfrlap.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfrlap.so not built ({LIB_PATH}); run paper_1804_02718_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise FrlapError(code, where, lib().frlap_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _Narr(N):
+    N = [int(v) for v in N]
+    return (ctypes.c_int * len(N))(*N), N
+
+
+def frlap_c_dalpha(d: int, alpha: float) -> float:
+    out = ctypes.c_double()
+    _check(lib().frlap_c_dalpha(d, alpha, ctypes.byref(out)), "frlap_c_dalpha")
+    return out.value
+
+
+def frlap_coeffs(d: int, alpha: float, gamma: float, h: float, N, out: torch.Tensor = None, stream=None):
+    """Coefficient table a_k, k in [0, N_max]^d, as a float64 CUDA tensor of shape (N_max+1,)*d."""
+    Na, Nl = _Narr(N)
+    Nmax = max(Nl)
+    if out is None:
+        out = torch.empty((Nmax + 1,) * d, dtype=torch.float64, device="cuda")
+    _check(lib().frlap_coeffs(d, alpha, gamma, h, Na, _dev(out, torch.float64, "out"), _stream(stream)),
+           "frlap_coeffs")
+    return out
+
+
+class Plan:
+    """An operator plan (frlap_plan_create / frlap_plan_destroy)."""
+
+    def __init__(self, d: int, alpha: float, h: float, N, gamma: float = 2.0, prec: int = FRLAP_F64, stream=None):
+        Na, Nl = _Narr(N)
+        if len(Nl) != d:
+            raise ValueError("N must have d entries (x, y[, z])")
+        self.d, self.alpha, self.gamma, self.h, self.N, self.prec = d, alpha, gamma, h, tuple(Nl), prec
+        handle = ctypes.c_void_p()
+        _check(lib().frlap_plan_create(d, alpha, gamma, h, Na, prec, _stream(stream), ctypes.byref(handle)),
+               "frlap_plan_create")
+        self._h = handle
+        n = (ctypes.c_int * 3)()
+        P = (ctypes.c_int * 3)()
+        _check(lib().frlap_plan_shape(self._h, n, P), "frlap_plan_shape")
+        self.n = tuple(n[r] for r in range(d))          # (n_x, n_y[, n_z])
+        self.P = tuple(P[r] for r in range(d))
+        self.shape = tuple(reversed(self.n))            # array shape, x fastest
+        self.M = 1
+        for v in self.n:
+            self.M *= v
+        self._ws = {}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().frlap_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, op: int) -> int:
+        return int(lib().frlap_workspace_bytes(self._h, op))
+
+    def workspace(self, op: int) -> torch.Tensor:
+        """A cached device scratch buffer for `op` (allocated by torch, 256-byte aligned)."""
+        nb = self.workspace_bytes(op)
+        ws = self._ws.get(op)
+        if ws is None or ws.numel() < nb + 256:
+            ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+            self._ws[op] = ws
+        off = (-ws.data_ptr()) % 256
+        return ws[off:off + nb]
+
+    def symbol(self, stream=None) -> torch.Tensor:
+        shape = tuple(p // 2 + 1 for p in reversed(self.P))
+        out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        _check(lib().frlap_plan_symbol(self._h, _dev(out, torch.float64, "out"), _stream(stream)),
+               "frlap_plan_symbol")
+        return out
+
+
+def frlap_plan_create(d, alpha, gamma, h, N, prec=FRLAP_F64, stream=None) -> Plan:
+    return Plan(d, alpha, h, N, gamma=gamma, prec=prec, stream=stream)
+
+
+def frlap_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def frlap_workspace_bytes(plan: Plan, op: int) -> int:
+    return plan.workspace_bytes(op)
+
+
+def _apply_dtype(plan: Plan):
+    return torch.float32 if plan.prec == FRLAP_F32 else torch.float64
+
+
+def frlap_apply(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch.Tensor = None, stream=None):
+    """y = A u (FFT of the circulant embedding); dtype float64 (F64/MIXED plans) or float32 (F32 plans)."""
+    dt = _apply_dtype(plan)
+    if u.numel() != plan.M:
+        raise ValueError(f"u has {u.numel()} entries, the plan has {plan.M} unknowns")
+    if y is None:
+        y = torch.empty_like(u)
+    if work is None:
+        work = plan.workspace(FRLAP_OP_APPLY)
+    _check(lib().frlap_apply(plan.handle, _dev(u, dt, "u"), _dev(y, dt, "y"), ctypes.c_void_p(work.data_ptr()),
+                             _stream(stream)), "frlap_apply")
+    return y
+
+
+def frlap_apply_nstages(plan: Plan) -> int:
+    return int(lib().frlap_apply_nstages(plan.handle))
+
+
+def frlap_apply_profiled(plan: Plan, u: torch.Tensor, y: torch.Tensor, work: torch.Tensor, events, stream=None):
+    """frlap_apply recording events[i] (torch.cuda.Event, already created) before stage i and after the last."""
+    dt = _apply_dtype(plan)
+    ns = frlap_apply_nstages(plan)
+    if len(events) != ns + 1:
+        raise ValueError(f"need {ns + 1} events")
+    arr = (ctypes.c_void_p * (ns + 1))(*[ctypes.c_void_p(e.cuda_event) if e is not None else None for e in events])
+    _check(lib().frlap_apply_profiled(plan.handle, _dev(u, dt, "u"), _dev(y, dt, "y"),
+                                      ctypes.c_void_p(work.data_ptr()), _stream(stream), arr),
+           "frlap_apply_profiled")
+    return y
+
+
+def frlap_apply_f32(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch.Tensor = None, stream=None):
+    if y is None:
+        y = torch.empty_like(u)
+    if work is None:
+        work = plan.workspace(FRLAP_OP_APPLY)
+    _check(lib().frlap_apply_f32(plan.handle, _dev(u, torch.float32, "u"), _dev(y, torch.float32, "y"),
+                                 ctypes.c_void_p(work.data_ptr()), _stream(stream)), "frlap_apply_f32")
+    return y
+
+
+def frlap_pcg_solve(plan: Plan, f: torch.Tensor, x: torch.Tensor = None, rtol: float = 1e-10, maxit: int = 100000,
+                    solver: int = FRLAP_SOLVE_CG, inner_rtol: float = 1e-4, work: torch.Tensor = None,
+                    stream=None, raise_on_error: bool = True):
+    """Solve A x = f; returns (x, iterations, true relative residual, status code)."""
+    if x is None:
+        x = torch.zeros_like(f)
+    if work is None:
+        work = plan.workspace(FRLAP_OP_PCG)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    code = lib().frlap_pcg_solve(plan.handle, _dev(f, torch.float64, "f"), _dev(x, torch.float64, "x"), rtol,
+                                 int(maxit), solver, inner_rtol, ctypes.byref(it), ctypes.byref(rel),
+                                 ctypes.c_void_p(work.data_ptr()), _stream(stream))
+    if raise_on_error:
+        _check(code, "frlap_pcg_solve")
+    return x, it.value, rel.value, code
+
+
+def frlap_allen_cahn_step(plan: Plan, u: torch.Tensor, tau: float, eps: float, nsteps: int = 1,
+                          rtol: float = 1e-10, work: torch.Tensor = None, stream=None) -> int:
+    """nsteps semi-implicit steps in place on u; returns the total CG iterations."""
+    if work is None:
+        work = plan.workspace(FRLAP_OP_AC)
+    it = ctypes.c_int(0)
+    _check(lib().frlap_allen_cahn_step(plan.handle, _dev(u, torch.float64, "u"), tau, eps, int(nsteps), rtol,
+                                       ctypes.byref(it), ctypes.c_void_p(work.data_ptr()), _stream(stream)),
+           "frlap_allen_cahn_step")
+    return it.value

@@ -1,0 +1,308 @@
+// C-ABI entry points of libfrlap (declared in include/frlap.h).
+#include <math.h>
+#include <stdio.h>
+
+#include <new>
+#include <string>
+
+#include "common.cuh"
+
+namespace frlap {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+frlap_status fail(frlap_status code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+frlap_status cuda_fail(cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  set_error(m);
+  return FRLAP_ECUDA;
+}
+
+size_t cg_work_bytes(const Plan& p, int eb);
+size_t ir_work_bytes(const Plan& p);
+size_t ac_work_bytes(const Plan& p);
+frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
+                            double inner_rtol, int* iters, double* relres, void* work, cudaStream_t st);
+frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, int nsteps, double rtol,
+                             int* iters, void* work, cudaStream_t st);
+
+static double c_dalpha_host(int d, double alpha) {
+  return pow(2.0, alpha - 1.0) * alpha * tgamma((d + alpha) / 2.0) /
+         (pow(M_PI, d / 2.0) * tgamma(1.0 - alpha / 2.0));
+}
+
+static frlap_status check_params(int d, double alpha, double gamma, double h, const int* N) {
+  if (d != 2 && d != 3) return fail(FRLAP_EINVAL, "d must be 2 or 3");
+  if (!(alpha > 0.0 && alpha < 2.0)) return fail(FRLAP_EINVAL, "alpha must lie in (0, 2)");
+  if (!(gamma > alpha && gamma <= 2.0)) return fail(FRLAP_EINVAL, "gamma must lie in (alpha, 2]");
+  if (!(h > 0.0) || !isfinite(h)) return fail(FRLAP_EINVAL, "h must be positive and finite");
+  if (!N) return fail(FRLAP_EINVAL, "N is NULL");
+  // 2D: N <= 4096 (FFT lines of up to 8192 points); 3D: N <= 1024
+  const int Nlim = (d == 2) ? 4096 : 1024;
+  for (int r = 0; r < d; ++r)
+    if (N[r] < 2 || N[r] > Nlim) return fail(FRLAP_EINVAL, "each N[r] must lie in [2, 4096] (2D) or [2, 1024] (3D)");
+  return FRLAP_OK;
+}
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+}  // namespace frlap
+
+using namespace frlap;
+
+struct frlap_plan : public frlap::Plan {};
+
+extern "C" {
+
+const char* frlap_last_error(void) { return g_last_error.c_str(); }
+
+frlap_status frlap_c_dalpha(int d, double alpha, double* out) {
+  if (d != 2 && d != 3) return fail(FRLAP_EINVAL, "d must be 2 or 3");
+  if (!(alpha > 0.0 && alpha < 2.0)) return fail(FRLAP_EINVAL, "alpha must lie in (0, 2)");
+  if (!out) return fail(FRLAP_EINVAL, "out is NULL");
+  *out = c_dalpha_host(d, alpha);
+  return FRLAP_OK;
+}
+
+frlap_status frlap_coeffs(int d, double alpha, double gamma, double h, const int* N, double* d_coeffs,
+                          void* stream) {
+  frlap_status rc = check_params(d, alpha, gamma, h, N);
+  if (rc != FRLAP_OK) return rc;
+  if (!d_coeffs) return fail(FRLAP_EINVAL, "d_coeffs is NULL");
+  int Nmax = 0;
+  for (int r = 0; r < d; ++r) Nmax = N[r] > Nmax ? N[r] : Nmax;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, coeffs_scratch_bytes(d, Nmax), s);
+  if (e != cudaSuccess) return fail(FRLAP_ENOMEM, "frlap_coeffs: scratch allocation failed");
+  e = coeffs_launch(d, alpha, gamma, h, Nmax, d_coeffs, scratch, s);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_coeffs kernels");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "frlap_coeffs free");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_plan_destroy(frlap_plan* plan) {
+  if (!plan) return FRLAP_OK;
+  cudaFree(plan->lam64);
+  cudaFree(plan->lam32);
+  for (int r = 0; r < 3; ++r) {
+    cudaFree(plan->tw64[r]);
+    cudaFree(plan->tw32[r]);
+  }
+  if (plan->side) cudaStreamDestroy(plan->side);
+  delete plan;
+  return FRLAP_OK;
+}
+
+frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, const int* N, int prec,
+                               void* stream, frlap_plan** out) {
+  frlap_status rc = check_params(d, alpha, gamma, h, N);
+  if (rc != FRLAP_OK) return rc;
+  if (!out) return fail(FRLAP_EINVAL, "out is NULL");
+  if (prec != FRLAP_F64 && prec != FRLAP_F32 && prec != FRLAP_MIXED) return fail(FRLAP_EINVAL, "unknown precision");
+  *out = nullptr;
+  frlap_plan* p = new (std::nothrow) frlap_plan();
+  if (!p) return fail(FRLAP_ENOMEM, "host allocation failed");
+  p->d = d;
+  p->alpha = alpha;
+  p->gamma = gamma;
+  p->h = h;
+  p->prec = prec;
+  p->c = c_dalpha_host(d, alpha);
+  p->Nmax = 0;
+  p->M = 1;
+  p->lam_count = 1;
+  for (int r = 0; r < 3; ++r) {
+    if (r < d) {
+      p->N[r] = N[r];
+      p->n[r] = N[r] - 1;
+      int Pr = 1 << ilog2(2 * p->n[r] - 1);
+      if (Pr < 32) Pr = 32;
+      p->P[r] = Pr;
+      p->logP[r] = ilog2(Pr);
+      p->Nmax = N[r] > p->Nmax ? N[r] : p->Nmax;
+      p->M *= (size_t)p->n[r];
+      p->lam_count *= (size_t)(Pr / 2 + 1);
+    } else {
+      p->N[r] = 2;
+      p->n[r] = 1;
+      p->P[r] = 1;
+      p->logP[r] = 0;
+    }
+  }
+  const int Hx1 = p->P[0] / 2 + 1;
+  const size_t nrows = (size_t)p->n[1] * (d == 3 ? p->n[2] : 1);
+  p->s1_elems = (size_t)Hx1 * nrows;
+  p->s2_elems = (d == 3) ? (size_t)Hx1 * p->P[1] * p->n[2] : 0;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  double* coef = nullptr;
+  void* scratch = nullptr;
+  const size_t N1 = (size_t)p->Nmax + 1;
+  const size_t ncoef = (d == 2) ? N1 * N1 : N1 * N1 * N1;
+  auto cleanup = [&](frlap_status code, const std::string& msg) {
+    cudaStreamSynchronize(s);
+    if (coef) cudaFree(coef);
+    if (scratch) cudaFree(scratch);
+    frlap_plan_destroy(p);
+    return fail(code, msg);
+  };
+  if (cudaMalloc(&coef, ncoef * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&scratch, coeffs_scratch_bytes(d, p->Nmax)) != cudaSuccess ||
+      cudaMalloc(&p->lam64, p->lam_count * sizeof(double)) != cudaSuccess)
+    return cleanup(FRLAP_ENOMEM, "plan allocation failed");
+  if (prec != FRLAP_F64 && cudaMalloc(&p->lam32, p->lam_count * sizeof(float)) != cudaSuccess)
+    return cleanup(FRLAP_ENOMEM, "plan allocation failed");
+  for (int r = 0; r < d; ++r) {
+    if (cudaMalloc(&p->tw64[r], p->P[r] * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&p->tw32[r], p->P[r] * sizeof(float2)) != cudaSuccess)
+      return cleanup(FRLAP_ENOMEM, "plan allocation failed");
+    cudaError_t e = twiddle_launch(p->P[r], p->tw64[r], p->tw32[r], s);
+    if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = coeffs_launch(d, alpha, gamma, h, p->Nmax, coef, scratch, s);
+  if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("coefficients: ") + cudaGetErrorString(e));
+  e = symbol_launch(*p, coef, p->lam64, s);
+  if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol: ") + cudaGetErrorString(e));
+  double scale = 1.0;
+  for (int r = 0; r < d; ++r) scale /= (double)p->P[r];
+  e = scale_symbol_launch(p->lam64, p->lam32, p->lam_count, scale, s);
+  if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol scale: ") + cudaGetErrorString(e));
+  e = cudaStreamSynchronize(s);
+  cudaFree(coef);
+  cudaFree(scratch);
+  coef = nullptr;
+  scratch = nullptr;
+  if (e != cudaSuccess) {
+    frlap_plan_destroy(p);
+    return cuda_fail(e, "plan creation");
+  }
+  *out = p;
+  return FRLAP_OK;
+}
+
+size_t frlap_workspace_bytes(const frlap_plan* plan, int op) {
+  if (!plan) return 0;
+  const int eb = (plan->prec == FRLAP_F32) ? 4 : 8;
+  switch (op) {
+    case FRLAP_OP_APPLY: {
+      size_t b = apply_work_bytes(*plan, eb);
+      if (plan->prec == FRLAP_MIXED) b = apply_work_bytes(*plan, 8);
+      return b;
+    }
+    case FRLAP_OP_PCG:
+      if (plan->prec == FRLAP_MIXED) return ir_work_bytes(*plan);
+      return cg_work_bytes(*plan, eb);
+    case FRLAP_OP_AC:
+      return ac_work_bytes(*plan);
+    default:
+      return 0;
+  }
+}
+
+frlap_status frlap_plan_shape(const frlap_plan* plan, int* n, int* P) {
+  if (!plan) return fail(FRLAP_EINVAL, "plan is NULL");
+  for (int r = 0; r < plan->d; ++r) {
+    if (n) n[r] = plan->n[r];
+    if (P) P[r] = plan->P[r];
+  }
+  return FRLAP_OK;
+}
+
+frlap_status frlap_plan_symbol(const frlap_plan* plan, double* d_lambda, void* stream) {
+  if (!plan || !d_lambda) return fail(FRLAP_EINVAL, "plan or d_lambda is NULL");
+  FRLAP_CUDA_TRY(cudaMemcpyAsync(d_lambda, plan->lam64, plan->lam_count * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return FRLAP_OK;
+}
+
+static frlap_status check_work(void* d_work) {
+  if (!d_work) return fail(FRLAP_EWORKSPACE, "d_work is NULL");
+  if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0) return fail(FRLAP_EWORKSPACE, "d_work is not 256-byte aligned");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream) {
+  if (!plan || !d_u || !d_y) return fail(FRLAP_EINVAL, "plan, d_u or d_y is NULL");
+  if (d_u == d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  cudaError_t e;
+  if (plan->prec == FRLAP_F32)
+    e = apply_launch<float>(*plan, (const float*)d_u, (float*)d_y, d_work, (cudaStream_t)stream, nullptr);
+  else
+    e = apply_launch<double>(*plan, (const double*)d_u, (double*)d_y, d_work, (cudaStream_t)stream, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_apply");
+  return FRLAP_OK;
+}
+
+int frlap_apply_nstages(const frlap_plan* plan) { return plan ? (plan->d == 2 ? 3 : 5) : 0; }
+
+frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream,
+                                  void* const* events) {
+  if (!plan || !d_u || !d_y || !events) return fail(FRLAP_EINVAL, "plan, d_u, d_y or events is NULL");
+  if (d_u == d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  cudaEvent_t const* ev = reinterpret_cast<cudaEvent_t const*>(events);
+  cudaError_t e;
+  if (plan->prec == FRLAP_F32)
+    e = apply_launch<float>(*plan, (const float*)d_u, (float*)d_y, d_work, (cudaStream_t)stream, nullptr, ev);
+  else
+    e = apply_launch<double>(*plan, (const double*)d_u, (double*)d_y, d_work, (cudaStream_t)stream, nullptr, ev);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_profiled");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_apply_f32(const frlap_plan* plan, const float* d_u, float* d_y, void* d_work, void* stream) {
+  if (!plan || !d_u || !d_y) return fail(FRLAP_EINVAL, "plan, d_u or d_y is NULL");
+  if (plan->prec == FRLAP_F64) return fail(FRLAP_EINVAL, "frlap_apply_f32 needs an F32 or MIXED plan");
+  if ((const void*)d_u == (void*)d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  cudaError_t e = apply_launch<float>(*plan, d_u, d_y, d_work, (cudaStream_t)stream, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_f32");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* d_x, double rtol, int maxit,
+                             int solver, double inner_rtol, int* iters, double* relres, void* d_work,
+                             void* stream) {
+  if (!plan || !d_f || !d_x) return fail(FRLAP_EINVAL, "plan, d_f or d_x is NULL");
+  if (!(rtol > 0.0) || maxit < 1) return fail(FRLAP_EINVAL, "need rtol > 0 and maxit >= 1");
+  if (solver == FRLAP_SOLVE_CG && plan->prec == FRLAP_F32)
+    return fail(FRLAP_EINVAL, "FP64 CG needs an F64 or MIXED plan");
+  if (solver == FRLAP_SOLVE_IR && plan->prec != FRLAP_MIXED)
+    return fail(FRLAP_EINVAL, "iterative refinement needs a MIXED plan");
+  if (solver != FRLAP_SOLVE_CG && solver != FRLAP_SOLVE_IR) return fail(FRLAP_EINVAL, "unknown solver");
+  if (solver == FRLAP_SOLVE_IR && !(inner_rtol > 0.0 && inner_rtol < 1.0))
+    return fail(FRLAP_EINVAL, "inner_rtol must lie in (0, 1)");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  return pcg_solve_impl(*plan, d_f, d_x, rtol, maxit, solver, inner_rtol, iters, relres, d_work,
+                        (cudaStream_t)stream);
+}
+
+frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double tau, double eps, int nsteps,
+                                   double rtol, int* iters, void* d_work, void* stream) {
+  if (!plan || !d_u) return fail(FRLAP_EINVAL, "plan or d_u is NULL");
+  if (plan->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "Allen-Cahn steps need an F64 or MIXED plan");
+  if (!(tau > 0.0) || !(eps > 0.0) || nsteps < 0 || !(rtol > 0.0))
+    return fail(FRLAP_EINVAL, "need tau > 0, eps > 0, nsteps >= 0, rtol > 0");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  return allen_cahn_impl(*plan, d_u, tau, eps, nsteps, rtol, iters, d_work, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// The FFT apply y = A u of the multilevel Toeplitz matrix of eqs. A-2D / A-3D
+// through its circulant embedding (the FFT-based product the paper asserts after
+// eqs. A-2D and Aj-3D).
+//
+// Pipeline (P_r = embedding size, H = P_x/2; S1, S2 = workspace spectra):
+//   2D: r2c_T  : rows of u (x lines)        -> S1[kx][y]        (pad + real FFT along x, transposed store)
+//       colmul : S1[kx][:] lines over y     -> in place         (pad, FFT_y, x lambda, IFFT_y, crop)
+//       c2r_T  : S1[kx][y]                  -> rows of y        (inverse real FFT along x, crop)
+//   3D: r2c_T  : rows (z,y) of u            -> S1[kx][z][y]
+//       c2cT_f : S1[kx][z][:] lines over y  -> S2[kx][ky][z]    (pad, FFT_y, transposed store)
+//       colmul : S2[kx][ky][:] lines over z -> in place         (pad, FFT_z, x lambda, IFFT_z, crop)
+//       c2cT_i : S2[kx][:][z]               -> S1[kx][z][y]     (IFFT_y, crop)
+//       c2r_T  : S1[kx][(z,y)]              -> rows of y
+// Every stage reads and writes whole contiguous lines or TL-wide contiguous
+// tiles; every global index below is bounded by the line/tile validity tests.
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace frlap {
+
+namespace {
+
+struct LamMap {
+  int d;       // 2 or 3
+  int logPy;   // 3D: log2 P_y (column index = kx * P_y + ky)
+  int Py;
+  int Hx1;     // P_x/2 + 1
+  int Hy1;     // P_y/2 + 1
+};
+
+template <typename T>
+__global__ void k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
+                        size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
+                        const int* __restrict__ skip) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && *skip) return;
+  const int H = 1 << logH, G = H >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int line0 = blockIdx.x * TL;
+  const int line = line0 + l;
+  const bool valid = line < nlines;
+  C* buf = smem + (size_t)l * (H + 1);
+  T* rb = reinterpret_cast<T*>(buf);
+  const T* src = in + (size_t)(valid ? line : 0) * ldi;
+  for (int i = lane; i < 2 * H; i += G) rb[i] = (valid && i < n) ? src[i] : (T)0;
+  __syncthreads();
+  fft_line<T, -1>(buf, logH, lane, tw, logP);
+  // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
+  for (int k = lane; k <= H / 2; k += G) {
+    const int km = H - k;
+    const C zk = buf[k];
+    const C zm = buf[km & (H - 1)];
+    const T half = (T)0.5;
+    {
+      const C a = zk, b = conjg(zm);
+      const C xe = half * (a + b);
+      const C xo = half * mul_i<-1>(a - b);
+      buf[k] = xe + cmul(tw[k], xo);
+    }
+    if (k != km) {
+      const C a = zm, b = conjg(zk);
+      const C xe = half * (a + b);
+      const C xo = half * mul_i<-1>(a - b);
+      buf[km] = xe + cmul(tw[km], xo);
+    }
+  }
+  __syncthreads();
+  const int total = TL * (H + 1);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l2 = idx % TL, k = idx / TL;
+    if (line0 + l2 < nlines) out[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * (H + 1) + k];
+  }
+}
+
+template <typename T>
+__global__ void k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
+                        int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
+                        const int* __restrict__ skip) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && *skip) return;
+  const int H = 1 << logH, G = H >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int line0 = blockIdx.x * TL;
+  const int line = line0 + l;
+  const int total = TL * (H + 1);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l2 = idx % TL, k = idx / TL;
+    smem[(size_t)l2 * (H + 1) + k] = (line0 + l2 < nlines) ? in[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
+  }
+  __syncthreads();
+  C* buf = smem + (size_t)l * (H + 1);
+  // repack: Z[k] = (X[k] + conj X[H-k]) + i W^{-k} (X[k] - conj X[H-k]), so that the
+  // unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1])
+  for (int k = lane; k <= H / 2; k += G) {
+    const int km = H - k;
+    const C xk = buf[k], xm = buf[km];
+    {
+      const C a = xk, b = conjg(xm);
+      buf[k] = (a + b) + mul_i<1>(cmulc(a - b, tw[k]));
+    }
+    if (k != km && km != H) {
+      const C a = xm, b = conjg(xk);
+      buf[km] = (a + b) + mul_i<1>(cmulc(a - b, tw[km]));
+    }
+  }
+  __syncthreads();
+  fft_line<T, 1>(buf, logH, lane, tw, logP);
+  if (line < nlines) {
+    const T* rb = reinterpret_cast<const T*>(buf);
+    T* dst = out + (size_t)line * ldo;
+    for (int i = lane; i < n; i += G) dst[i] = rb[i];
+  }
+}
+
+// lines of length n (contiguous, stride ld) -> zero-pad to P, FFT, * lambda, IFFT, crop, in place
+template <typename T>
+__global__ void k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
+                         const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
+                         const int* __restrict__ skip) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && *skip) return;
+  const int P = 1 << logP, G = P >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int col = blockIdx.x * TL + l;
+  const bool valid = col < ncols;
+  C* buf = smem + (size_t)l * P;
+  C* line = data + (size_t)(valid ? col : 0) * ld;
+  for (int i = lane; i < P; i += G) buf[i] = (valid && i < n) ? line[i] : mk<C>(0, 0);
+  __syncthreads();
+  fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+  size_t lam_base;
+  int lam_stride;
+  if (map.d == 2) {
+    lam_base = valid ? col : 0;
+    lam_stride = map.Hx1;
+  } else {
+    const int c = valid ? col : 0;
+    const int kx = c >> map.logPy, ky = c & (map.Py - 1);
+    const int kyf = min(ky, map.Py - ky);
+    lam_base = (size_t)kyf * map.Hx1 + kx;
+    lam_stride = map.Hy1 * map.Hx1;
+  }
+  for (int k = lane; k < P; k += G) {
+    const int kf = min(k, P - k);
+    buf[k] = lam[lam_base + (size_t)kf * lam_stride] * buf[k];
+  }
+  __syncthreads();
+  fft_line<T, 1>(buf, logP, lane, tw, logPtab);
+  if (valid)
+    for (int i = lane; i < n; i += G) line[i] = buf[i];
+}
+
+// groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
+template <typename T>
+__global__ void k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+                           size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
+                           const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && *skip) return;
+  const int P = 1 << logP, G = P >> 4;
+  const int g = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int line0 = tile * TL;
+  const int line = line0 + l;
+  const bool valid = line < nlines;
+  C* buf = smem + (size_t)l * P;
+  const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
+  for (int i = lane; i < P; i += G) buf[i] = (valid && i < n) ? src[i] : mk<C>(0, 0);
+  __syncthreads();
+  fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+  C* dst = out + g * gout;
+  const int total = TL * P;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l2 = idx % TL, k = idx / TL;
+    if (line0 + l2 < nlines) dst[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * P + k];
+  }
+}
+
+// transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
+template <typename T>
+__global__ void k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+                           size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
+                           const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && *skip) return;
+  const int P = 1 << logP, G = P >> 4;
+  const int g = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int line0 = tile * TL;
+  const int line = line0 + l;
+  const C* src = in + g * gin;
+  const int total = TL * P;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l2 = idx % TL, k = idx / TL;
+    smem[(size_t)l2 * P + k] = (line0 + l2 < nlines) ? src[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
+  }
+  __syncthreads();
+  C* buf = smem + (size_t)l * P;
+  fft_line<T, 1>(buf, logP, lane, tw, logPtab);
+  if (line < nlines) {
+    C* dst = out + g * gout + (size_t)line * ldo;
+    for (int i = lane; i < n; i += G) dst[i] = buf[i];
+  }
+}
+
+// Lines per CTA for a line of `len` complex slots: as many as fit in
+// `budget` bytes of shared memory and 1024 threads (at least one).
+int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
+  int tl = budget / (len * elem_bytes);
+  tl = tl < 1 ? 1 : tl;
+  while (tl > 1 && tl * G > 1024) --tl;
+  if (tl > max_lines) tl = max_lines;
+  return tl < 1 ? 1 : tl;
+}
+
+template <typename Kern>
+cudaError_t set_smem(Kern k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t apply_work_bytes(const Plan& p, int real_bytes) {
+  const size_t cb = 2 * (size_t)real_bytes;
+  size_t b = align256(p.s1_elems * cb);
+  if (p.d == 3) b += align256(p.s2_elems * cb);
+  return b;
+}
+
+template <typename T>
+cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
+                         cudaEvent_t const* ev) {
+  int stage = 0;
+  auto mark = [&]() -> cudaError_t {
+    if (ev && ev[stage]) {
+      cudaError_t e = cudaEventRecord(ev[stage], s);
+      if (e != cudaSuccess) return e;
+    }
+    ++stage;
+    return cudaSuccess;
+  };
+  using C = cplx<T>;
+  const int eb = sizeof(C);
+  const int budget = 96 * 1024;
+  const C* tw[3];
+  for (int r = 0; r < 3; ++r) {
+    if constexpr (sizeof(T) == 8) tw[r] = reinterpret_cast<const C*>(p.tw64[r]);
+    else tw[r] = reinterpret_cast<const C*>(p.tw32[r]);
+  }
+  const T* lam;
+  if constexpr (sizeof(T) == 8) lam = p.lam64; else lam = p.lam32;
+  C* S1 = reinterpret_cast<C*>(work);
+  C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
+  const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const int logPx = p.logP[0], logPy = p.logP[1], logPz = p.logP[2];
+  const int Hx = p.P[0] / 2;
+  const int nrows = ny * (p.d == 3 ? nz : 1);
+  const size_t ld1 = (size_t)nrows;  // S1 k-stride: all (z, y) rows
+
+  // ---- stage 1: rows of u -> S1[kx][row]
+  {
+    const int G = Hx >> 4;
+    const int tl = pick_tl(Hx + 1, eb, G, budget, 64);
+    const size_t sm = (size_t)tl * (Hx + 1) * eb;
+    cudaError_t e = set_smem(k_r2c_T<T>, sm);
+    if (e != cudaSuccess) return e;
+    const int grid = (nrows + tl - 1) / tl;
+    if ((e = mark()) != cudaSuccess) return e;
+    k_r2c_T<T><<<grid, tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  LamMap map;
+  map.d = p.d;
+  map.Hx1 = Hx + 1;
+  map.logPy = logPy;
+  map.Py = p.P[1];
+  map.Hy1 = p.P[1] / 2 + 1;
+  if (p.d == 2) {
+    const int G = p.P[1] >> 4;
+    const int tl = pick_tl(p.P[1], eb, G, budget, 64);
+    const size_t sm = (size_t)tl * p.P[1] * eb;
+    cudaError_t e = set_smem(k_colmul<T>, sm);
+    if (e != cudaSuccess) return e;
+    const int ncols = Hx + 1;
+    const int grid = (ncols + tl - 1) / tl;
+    if ((e = mark()) != cudaSuccess) return e;
+    k_colmul<T><<<grid, tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    const int Py = p.P[1], Pz = p.P[2];
+    // ---- stage 2: S1[kx][z][y] -> FFT_y -> S2[kx][ky][z]
+    {
+      const int G = Py >> 4;
+      const int tl = pick_tl(Py, eb, G, budget, 64);
+      const size_t sm = (size_t)tl * Py * eb;
+      cudaError_t e = set_smem(k_c2cT_fwd<T>, sm);
+      if (e != cudaSuccess) return e;
+      const int tiles = (nz + tl - 1) / tl;
+      const int grid = (Hx + 1) * tiles;
+      if ((e = mark()) != cudaSuccess) return e;
+      k_c2cT_fwd<T><<<grid, tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz, nz,
+                                              logPy, tl, tw[1], logPy, skip);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // ---- stage 3: S2[kx][ky][:] -> FFT_z, * lambda, IFFT_z
+    {
+      const int G = Pz >> 4;
+      const int tl = pick_tl(Pz, eb, G, budget, 64);
+      const size_t sm = (size_t)tl * Pz * eb;
+      cudaError_t e = set_smem(k_colmul<T>, sm);
+      if (e != cudaSuccess) return e;
+      const int ncols = (Hx + 1) * Py;
+      const int grid = (ncols + tl - 1) / tl;
+      if ((e = mark()) != cudaSuccess) return e;
+      k_colmul<T><<<grid, tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz, skip);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
+    {
+      const int G = Py >> 4;
+      const int tl = pick_tl(Py, eb, G, budget, 64);
+      const size_t sm = (size_t)tl * Py * eb;
+      cudaError_t e = set_smem(k_c2cT_inv<T>, sm);
+      if (e != cudaSuccess) return e;
+      const int tiles = (nz + tl - 1) / tl;
+      const int grid = (Hx + 1) * tiles;
+      if ((e = mark()) != cudaSuccess) return e;
+      k_c2cT_inv<T><<<grid, tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny,
+                                              logPy, tl, tw[1], logPy, skip);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  // ---- last stage: S1[kx][row] -> rows of y
+  {
+    const int G = Hx >> 4;
+    const int tl = pick_tl(Hx + 1, eb, G, budget, 64);
+    const size_t sm = (size_t)tl * (Hx + 1) * eb;
+    cudaError_t e = set_smem(k_c2r_T<T>, sm);
+    if (e != cudaSuccess) return e;
+    const int grid = (nrows + tl - 1) / tl;
+    if ((e = mark()) != cudaSuccess) return e;
+    k_c2r_T<T><<<grid, tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return mark();
+}
+
+template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
+                                          cudaEvent_t const*);
+template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
+                                         cudaEvent_t const*);
+
+}  // namespace frlap

@@ -1,0 +1,105 @@
+// Internal definitions shared by the frlap CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/frlap.h"
+
+namespace frlap {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+frlap_status fail(frlap_status code, const std::string& msg);
+frlap_status cuda_fail(cudaError_t e, const char* where);
+
+#define FRLAP_CUDA_TRY(call)                                   \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::frlap::cuda_fail(e_, #call); \
+  } while (0)
+
+#define FRLAP_LAUNCH_CHECK(where)                                   \
+  do {                                                              \
+    cudaError_t e_ = cudaGetLastError();                            \
+    if (e_ != cudaSuccess) return ::frlap::cuda_fail(e_, where);    \
+  } while (0)
+
+// ---------------------------------------------------------------- complex
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_t<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+  C c; c.x = a; c.y = b; return c;
+}
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+// complex product a*b
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+template <typename C> __device__ __forceinline__ C conjg(C a) { a.y = -a.y; return a; }
+// multiply by -i (forward) or +i (inverse): sign = -1 gives -i*a
+template <int SIGN, typename C> __device__ __forceinline__ C mul_i(C a) {
+  C r;
+  if (SIGN < 0) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
+  return r;
+}
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+  int d;
+  int N[3];        // mesh intervals per axis (x, y, z); unused axes = 2
+  int n[3];        // interior unknowns per axis n_r = N_r - 1 (unused axes 1)
+  int P[3];        // embedding (FFT) sizes per axis (unused axes 1)
+  int logP[3];
+  int Nmax;
+  double alpha, gamma, h, c;
+  int prec;        // frlap_prec
+  size_t M;        // number of unknowns
+  size_t lam_count;            // prod (P_r/2 + 1) over the used axes
+  double* lam64 = nullptr;     // symbol octant, FP64 (always built)
+  float* lam32 = nullptr;      // symbol octant, FP32 (F32 and MIXED plans)
+  double2* tw64[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i m / P_r), m < P_r
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  // workspace layout of one apply, in complex elements of the apply precision
+  size_t s1_elems = 0, s2_elems = 0;
+  cudaStream_t side = nullptr;  // internal stream for captured solver graphs
+};
+
+// apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
+template <typename T>
+cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
+                         cudaEvent_t const* ev = nullptr);
+size_t apply_work_bytes(const Plan& p, int real_bytes);
+
+// coefficient / symbol generation (coeffs.cu)
+cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int Nmax, double* coef, void* scratch,
+                          cudaStream_t s);
+size_t coeffs_scratch_bytes(int d, int Nmax);
+cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
+cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s);
+cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st);
+
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace frlap

@@ -1,0 +1,160 @@
+// Shared-memory FFT of one power-of-two line per thread group, used by every
+// stage of the circulant-embedding apply and by the symbol generation.
+//
+// Layout: a CTA holds TL lines in shared memory; each line of length L = 2^logL
+// (16 <= L) is processed by G = L/16 threads ("lanes"), each holding 16 complex
+// values in registers per stage.  Stages are Stockham (self-sorting): stage s
+// reads x[j + r L/R], multiplies by the twiddles W_{Ns R}^{r k} (k = j mod Ns),
+// does a radix-R DFT in registers and writes to (j - k) R + k + r Ns; the
+// result is in natural order with no bit reversal.  All reads of a stage
+// happen before a CTA barrier and all writes after it, so one buffer suffices.
+// Radices: one 2/4/8 stage for the leftover log2 factor, then radix-16 stages.
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / Ptab), m < Ptab, of the
+// longest transform on that axis; a length-L transform indexes it with stride
+// Ptab / L.  SIGN = -1 is the forward transform, +1 the (unnormalised) inverse.
+#pragma once
+
+#include "common.cuh"
+
+namespace frlap {
+
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a - b;
+  a = a + b;
+  b = t;
+}
+
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
+  C s0 = a + c, d0 = a - c, s1 = b + d, d1 = mul_i<SIGN>(b - d);
+  a = s0 + s1;
+  c = s0 - s1;
+  b = d0 + d1;
+  d = d0 - d1;
+}
+
+// exp(SIGN * 2 pi i m / 16) for the small set of m used inside the radix-16 kernel
+template <int SIGN, typename T>
+__device__ __forceinline__ cplx<T> w16(int m) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, r2 = (T)0.70710678118654752440;
+  T re, im;
+  switch (m) {
+    case 0: re = 1; im = 0; break;
+    case 1: re = c1; im = s1; break;
+    case 2: re = r2; im = r2; break;
+    case 3: re = s1; im = c1; break;
+    case 4: re = 0; im = 1; break;
+    case 6: re = -r2; im = r2; break;
+    case 9: re = -c1; im = -s1; break;
+    default: re = 0; im = 0; break;
+  }
+  return mk<cplx<T>>(re, (T)SIGN * im);
+}
+
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft8(C* v) {
+  using T = decltype(C::x);
+  // even / odd halves
+  dft4<SIGN>(v[0], v[2], v[4], v[6]);
+  dft4<SIGN>(v[1], v[3], v[5], v[7]);
+  const T r2 = (T)0.70710678118654752440;
+  C o1 = v[3], o2 = v[5], o3 = v[7];
+  // W8^1 = (1 + SIGN i)/sqrt2, W8^2 = SIGN i, W8^3 = (-1 + SIGN i)/sqrt2
+  C t1 = mk<C>(r2 * (o1.x - (T)SIGN * o1.y), r2 * (o1.y + (T)SIGN * o1.x));
+  C t2 = mul_i<SIGN>(o2);
+  C t3 = mk<C>(r2 * (-o3.x - (T)SIGN * o3.y), r2 * (-o3.y + (T)SIGN * o3.x));
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + t1; v[5] = e1 - t1;
+  v[2] = e2 + t2; v[6] = e2 - t2;
+  v[3] = e3 + t3; v[7] = e3 - t3;
+}
+
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft16(C* v) {
+  using T = decltype(C::x);
+  // x[4 j1 + j2]: length-4 DFTs over j1 for each j2
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) dft4<SIGN>(v[j2], v[4 + j2], v[8 + j2], v[12 + j2]);
+  // now v[4 k1 + j2] = A_{j2}[k1]; twiddle by W16^{j2 k1}
+#pragma unroll
+  for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+    for (int j2 = 1; j2 < 4; ++j2) v[4 * k1 + j2] = cmul(v[4 * k1 + j2], w16<SIGN, T>(j2 * k1));
+  // length-4 DFTs over j2 for each k1: X[k1 + 4 k2]
+  C out[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C a = v[4 * k1], b = v[4 * k1 + 1], c = v[4 * k1 + 2], d = v[4 * k1 + 3];
+    dft4<SIGN>(a, b, c, d);
+    out[k1] = a; out[k1 + 4] = b; out[k1 + 8] = c; out[k1 + 12] = d;
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = out[i];
+}
+
+template <int R, int SIGN, typename C>
+__device__ __forceinline__ void dftR(C* v) {
+  if constexpr (R == 2) dft2<SIGN>(v[0], v[1]);
+  else if constexpr (R == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<SIGN>(v);
+  else dft16<SIGN>(v);
+}
+
+// One Stockham stage of radix R on a line of length L = 2^logL held in `buf`.
+template <typename T, int R, int SIGN>
+__device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int logNs, int lane,
+                                          const cplx<T>* __restrict__ tw, int logPtab) {
+  using C = cplx<T>;
+  constexpr int E = 16, B = E / R;
+  constexpr int LOGR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
+  const int G = 1 << (logL - 4);
+  const int LR = 1 << (logL - LOGR);
+  C v[E];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = lane + b * G;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b * R + r] = buf[j + r * LR];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = lane + b * G;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      // W_{Ns R}^{r k} = tw[r k Ptab / (Ns R)]
+      const int sh = logPtab - logNs - LOGR;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const C w = tw[(r * k) << sh];
+        v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], w) : cmulc(v[b * R + r], w);
+      }
+    }
+    dftR<R, SIGN>(&v[b * R]);
+    const int o = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[o + r * Ns] = v[b * R + r];
+  }
+  __syncthreads();
+}
+
+// Full transform of the line in `buf` (length 2^logL >= 16).  Every thread of the
+// CTA must call this with the same logL (the stages contain CTA barriers).
+template <typename T, int SIGN>
+__device__ __forceinline__ void fft_line(cplx<T>* buf, int logL, int lane, const cplx<T>* __restrict__ tw,
+                                         int logPtab) {
+  const int rem = logL & 3;
+  int logNs = 0;
+  if (rem == 1) { fft_stage<T, 2, SIGN>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 1; }
+  else if (rem == 2) { fft_stage<T, 4, SIGN>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 2; }
+  else if (rem == 3) { fft_stage<T, 8, SIGN>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 3; }
+  while (logNs < logL) {
+    fft_stage<T, 16, SIGN>(buf, logL, 1 << logNs, logNs, lane, tw, logPtab);
+    logNs += 4;
+  }
+}
+
+}  // namespace frlap

@@ -1,0 +1,437 @@
+// Device-resident conjugate gradients around the FFT apply (Sec. 5.3: each linear
+// system is solved by CG with the FFT-based product), its use inside an FP64
+// iterative-refinement loop with FP32 inner solves, and the semi-implicit
+// Allen-Cahn step.
+//
+// The operator of every solve is B v = sigma v + s A v (Poisson: sigma = 0, s = 1;
+// Allen-Cahn: sigma = 1, s = tau eps^2).  All CG scalars live on the device; each
+// kernel reads a `done` flag first and does nothing once the iteration has
+// stopped, so the host launches iterations in chunks and looks at the flag only
+// between chunks.  Inner products are accumulated in FP64 with a fixed
+// reduction order (per-block partials, then the last block to finish sums them
+// in block order), so results are deterministic.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace frlap {
+
+namespace {
+
+constexpr int kBlocks = 2 * 152;  // grid of the vector kernels: two CTAs per SM
+constexpr int kThreads = 512;
+
+struct CgState {
+  double rr;        // r . r
+  double pq;        // p . B p
+  double alpha, beta;
+  double tol2;      // (rtol ||f||)^2
+  double fnorm2;
+  double sigma, s;  // operator B = sigma I + s A
+  int done;
+  int status;       // frlap_status of the iteration
+  int iters;
+  unsigned counter; // last-block ticket for the reductions
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+// The last block to arrive sums the partials in block order; returns true in that block's thread 0.
+__device__ __forceinline__ bool last_block_total(double part, double* partials, unsigned* counter, double* total,
+                                                 double* red) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = part;
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += *((volatile double*)&partials[i]);
+  // the loop above is strided by thread; reduce in a fixed order
+  const double s = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool finite_(T v) { return isfinite((double)v); }
+
+// r = f - (sigma x + s q) (q = A x), p = r, rr = r.r, fnorm2 = f.f; sets tol2, done
+template <typename T>
+__global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, const T* __restrict__ q, T* r, T* p,
+                          size_t n, double* partials, CgState* S, double rtol, int use_x) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double fi = (double)f[i];
+    double ri = fi;
+    if (use_x) ri = fi - (S->sigma * (double)x[i] + S->s * (double)q[i]);
+    const T rt = (T)ri;
+    r[i] = rt;
+    p[i] = rt;
+    a += (double)rt * (double)rt;
+    b += fi * fi;
+  }
+  const double sa = block_sum(a, red);
+  __syncthreads();
+  const double sb = block_sum(b, red);
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = sa;
+    partials[gridDim.x + blockIdx.x] = sb;
+    __threadfence();
+    is_last = atomicAdd(&S->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  double va = 0.0, vb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    va += *((volatile double*)&partials[i]);
+    vb += *((volatile double*)&partials[gridDim.x + i]);
+  }
+  __syncthreads();
+  const double ta = block_sum(va, red);
+  __syncthreads();
+  const double tb = block_sum(vb, red);
+  if (threadIdx.x == 0) {
+    S->counter = 0u;
+    S->rr = ta;
+    S->fnorm2 = tb;
+    S->tol2 = rtol * rtol * tb;
+    S->iters = 0;
+    S->status = FRLAP_OK;
+    S->done = 0;
+    if (!isfinite(ta) || !isfinite(tb)) {
+      S->status = FRLAP_ENAN;
+      S->done = 1;
+    } else if (ta <= S->tol2) {
+      S->done = 1;
+    }
+  }
+}
+
+// q <- sigma p + s q ; pq = p . q ; alpha = rr / pq (breakdown if pq <= 0)
+template <typename T>
+__global__ void k_cg_pq(const T* __restrict__ p, T* q, size_t n, double* partials, CgState* S) {
+  __shared__ double red[32];
+  if (S->done) return;
+  const double sg = S->sigma, sc = S->s;
+  double a = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double pi = (double)p[i];
+    const T qi = (T)(sg * pi + sc * (double)q[i]);
+    q[i] = qi;
+    a += pi * (double)qi;
+  }
+  const double sa = block_sum(a, red);
+  double tot;
+  if (last_block_total(sa, partials, &S->counter, &tot, red)) {
+    S->pq = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      S->status = isfinite(tot) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
+      S->done = 1;
+    } else {
+      S->alpha = S->rr / tot;
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha q ; rr_new = r.r ; beta = rr_new / rr ; convergence test
+template <typename T>
+__global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __restrict__ q, size_t n,
+                            double* partials, CgState* S, int maxit) {
+  __shared__ double red[32];
+  if (S->done) return;
+  const double al = S->alpha;
+  double a = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    x[i] = (T)((double)x[i] + al * (double)p[i]);
+    const T ri = (T)((double)r[i] - al * (double)q[i]);
+    r[i] = ri;
+    a += (double)ri * (double)ri;
+  }
+  const double sa = block_sum(a, red);
+  double tot;
+  if (last_block_total(sa, partials, &S->counter, &tot, red)) {
+    S->beta = tot / S->rr;
+    S->rr = tot;
+    S->iters += 1;
+    if (!isfinite(tot)) {
+      S->status = FRLAP_ENAN;
+      S->done = 1;
+    } else if (tot <= S->tol2) {
+      S->done = 1;
+    } else if (S->iters >= maxit) {
+      S->status = FRLAP_ENOCONV;
+      S->done = 1;
+    }
+  }
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void k_cg_dir(const T* __restrict__ r, T* p, size_t n, const CgState* S) {
+  if (S->done) return;
+  const double b = S->beta;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = (T)((double)r[i] + b * (double)p[i]);
+}
+
+__global__ void k_set_state(CgState* S, double sigma, double s) {
+  S->sigma = sigma;
+  S->s = s;
+  S->counter = 0u;
+  S->done = 0;
+  S->status = FRLAP_OK;
+  S->iters = 0;
+}
+
+// true residual norms: out[0] = ||f - (sigma x + s q)||^2, out[1] = ||f||^2 (one block per slice, then last block)
+__global__ void k_resid(const double* __restrict__ f, const double* __restrict__ x, const double* __restrict__ q,
+                        size_t n, double sigma, double s, double* partials, unsigned* counter, double* out,
+                        double* rvec, double* rnorm_scale) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double ri = f[i] - (sigma * x[i] + s * q[i]);
+    if (rvec) rvec[i] = ri;
+    a += ri * ri;
+    b += f[i] * f[i];
+  }
+  const double sa = block_sum(a, red);
+  __syncthreads();
+  const double sb = block_sum(b, red);
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = sa;
+    partials[gridDim.x + blockIdx.x] = sb;
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  double va = 0.0, vb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    va += *((volatile double*)&partials[i]);
+    vb += *((volatile double*)&partials[gridDim.x + i]);
+  }
+  __syncthreads();
+  const double ta = block_sum(va, red);
+  __syncthreads();
+  const double tb = block_sum(vb, red);
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    out[0] = ta;
+    out[1] = tb;
+    if (rnorm_scale) *rnorm_scale = sqrt(ta);
+  }
+}
+
+// r32 = r / scale (FP32 right-hand side of an inner solve), d32 = 0
+__global__ void k_to_f32(const double* __restrict__ r, const double* scale, float* r32, float* d32, size_t n) {
+  const double sc = *scale;
+  const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    r32[i] = (float)(r[i] * inv);
+    d32[i] = 0.0f;
+  }
+}
+
+// x += scale * d32
+__global__ void k_correct(double* x, const float* __restrict__ d32, const double* scale, size_t n) {
+  const double sc = *scale;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] += sc * (double)d32[i];
+}
+
+// Allen-Cahn right-hand side u + tau (u - u^3)
+__global__ void k_ac_rhs(const double* __restrict__ u, double* rhs, size_t n, double tau) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = u[i];
+    rhs[i] = v + tau * (v - v * v * v);
+  }
+}
+
+size_t vec_bytes(const Plan& p, int eb) { return align256(p.M * (size_t)eb); }
+
+}  // namespace
+
+// workspace: [apply work][r][p][q][partials][state]   (vectors of the given precision)
+size_t cg_work_bytes(const Plan& p, int eb) {
+  return apply_work_bytes(p, eb) + 3 * vec_bytes(p, eb) + align256(2 * kBlocks * sizeof(double)) +
+         align256(sizeof(CgState));
+}
+
+// Runs CG on B x = f with B = sigma I + s A in precision T; x holds x0 on entry.
+// Returns the final device state through *hS (host copy).
+template <typename T>
+static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double s, double rtol, int maxit,
+                           int use_x0, void* work, cudaStream_t st, CgState* hS) {
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  void* awork = w;
+  w += apply_work_bytes(p, sizeof(T));
+  T* r = reinterpret_cast<T*>(w);
+  w += vec_bytes(p, sizeof(T));
+  T* pv = reinterpret_cast<T*>(w);
+  w += vec_bytes(p, sizeof(T));
+  T* q = reinterpret_cast<T*>(w);
+  w += vec_bytes(p, sizeof(T));
+  double* partials = reinterpret_cast<double*>(w);
+  w += align256(2 * kBlocks * sizeof(double));
+  CgState* S = reinterpret_cast<CgState*>(w);
+  const size_t n = p.M;
+  k_set_state<<<1, 1, 0, st>>>(S, sigma, s);
+  FRLAP_LAUNCH_CHECK("k_set_state");
+  if (use_x0) {
+    cudaError_t e = apply_launch<T>(p, x, q, awork, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "apply (initial residual)");
+  }
+  k_cg_init<T><<<kBlocks, kThreads, 0, st>>>(f, x, q, r, pv, n, partials, S, rtol, use_x0);
+  FRLAP_LAUNCH_CHECK("k_cg_init");
+  const int* done = &S->done;
+  const int chunk = 8;
+  int launched = 0;
+  while (true) {
+    for (int c = 0; c < chunk; ++c) {
+      cudaError_t e = apply_launch<T>(p, pv, q, awork, st, done);
+      if (e != cudaSuccess) return cuda_fail(e, "apply (CG)");
+      k_cg_pq<T><<<kBlocks, kThreads, 0, st>>>(pv, q, n, partials, S);
+      k_cg_update<T><<<kBlocks, kThreads, 0, st>>>(x, r, pv, q, n, partials, S, maxit);
+      k_cg_dir<T><<<kBlocks, kThreads, 0, st>>>(r, pv, n, S);
+      FRLAP_LAUNCH_CHECK("CG iteration kernels");
+    }
+    launched += chunk;
+    FRLAP_CUDA_TRY(cudaMemcpyAsync(hS, S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hS->done) break;
+    if (launched > maxit + chunk) break;  // cannot happen: the update kernel stops at maxit
+  }
+  return FRLAP_OK;
+}
+
+// true relative residual ||f - B x|| / ||f|| in FP64 (uses the apply work and q buffer)
+static frlap_status true_residual(const Plan& p, const double* f, const double* x, double sigma, double s,
+                                  void* work, cudaStream_t st, double* relres, double* rvec,
+                                  double* rnorm_dev) {
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  void* awork = w;
+  w += apply_work_bytes(p, 8);
+  w += vec_bytes(p, 8);  // r
+  w += vec_bytes(p, 8);  // p
+  double* q = reinterpret_cast<double*>(w);
+  w += vec_bytes(p, 8);
+  double* partials = reinterpret_cast<double*>(w);
+  w += align256(2 * kBlocks * sizeof(double));
+  CgState* S = reinterpret_cast<CgState*>(w);
+  cudaError_t e = apply_launch<double>(p, x, q, awork, st, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
+  double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
+  k_resid<<<kBlocks, kThreads, 0, st>>>(f, x, q, p.M, sigma, s, partials, &S->counter, out, rvec, rnorm_dev);
+  FRLAP_LAUNCH_CHECK("k_resid");
+  double h[2];
+  FRLAP_CUDA_TRY(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
+  *relres = (h[1] > 0.0) ? sqrt(h[0] / h[1]) : 0.0;
+  return FRLAP_OK;
+}
+
+size_t ir_work_bytes(const Plan& p) {
+  // FP64 CG state (for the outer residual) + FP32 CG workspace + r64 + r32, d32
+  return cg_work_bytes(p, 8) + cg_work_bytes(p, 4) + vec_bytes(p, 8) + 2 * vec_bytes(p, 4) + 256;
+}
+
+size_t ac_work_bytes(const Plan& p) { return cg_work_bytes(p, 8) + vec_bytes(p, 8); }
+
+frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
+                            double inner_rtol, int* iters, double* relres, void* work, cudaStream_t st) {
+  CgState hS;
+  if (solver == FRLAP_SOLVE_CG) {
+    frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, maxit, 1, work, st, &hS);
+    if (rc != FRLAP_OK) return rc;
+    double rel = 0.0;
+    rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
+    if (rc != FRLAP_OK) return rc;
+    if (iters) *iters = hS.iters;
+    if (relres) *relres = rel;
+    if (hS.status != FRLAP_OK) return fail((frlap_status)hS.status, "CG stopped early (see status code)");
+    return FRLAP_OK;
+  }
+  // iterative refinement: x <- x + ||r|| * CG32(A, r/||r||)
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  void* work64 = w;
+  w += cg_work_bytes(p, 8);
+  void* work32 = w;
+  w += cg_work_bytes(p, 4);
+  double* r64 = reinterpret_cast<double*>(w);
+  w += vec_bytes(p, 8);
+  float* r32 = reinterpret_cast<float*>(w);
+  w += vec_bytes(p, 4);
+  float* d32 = reinterpret_cast<float*>(w);
+  w += vec_bytes(p, 4);
+  double* rnorm = reinterpret_cast<double*>(w);
+  int total = 0;
+  double rel = 0.0;
+  const int max_outer = 60;
+  for (int outer = 0; outer <= max_outer; ++outer) {
+    frlap_status rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm);
+    if (rc != FRLAP_OK) return rc;
+    if (!isfinite(rel)) return fail(FRLAP_ENAN, "non-finite residual in iterative refinement");
+    if (rel <= rtol || outer == max_outer || total >= maxit) break;
+    k_to_f32<<<kBlocks, kThreads, 0, st>>>(r64, rnorm, r32, d32, p.M);
+    FRLAP_LAUNCH_CHECK("k_to_f32");
+    rc = run_cg<float>(p, r32, d32, 0.0, 1.0, inner_rtol, maxit - total, 0, work32, st, &hS);
+    if (rc != FRLAP_OK) return rc;
+    total += hS.iters;
+    if (hS.status == FRLAP_ENAN) return fail(FRLAP_ENAN, "non-finite value in the FP32 inner solve");
+    k_correct<<<kBlocks, kThreads, 0, st>>>(x, d32, rnorm, p.M);
+    FRLAP_LAUNCH_CHECK("k_correct");
+  }
+  if (iters) *iters = total;
+  if (relres) *relres = rel;
+  if (!(rel <= rtol)) return fail(FRLAP_ENOCONV, "iterative refinement did not reach rtol");
+  return FRLAP_OK;
+}
+
+frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, int nsteps, double rtol,
+                             int* iters, void* work, cudaStream_t st) {
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  void* cgw = w;
+  w += cg_work_bytes(p, 8);
+  double* rhs = reinterpret_cast<double*>(w);
+  int total = 0;
+  CgState hS;
+  for (int step = 0; step < nsteps; ++step) {
+    k_ac_rhs<<<kBlocks, kThreads, 0, st>>>(u, rhs, p.M, tau);
+    FRLAP_LAUNCH_CHECK("k_ac_rhs");
+    frlap_status rc = run_cg<double>(p, rhs, u, 1.0, tau * eps * eps, rtol, 100000, 1, cgw, st, &hS);
+    if (rc != FRLAP_OK) return rc;
+    total += hS.iters;
+    if (hS.status != FRLAP_OK) {
+      if (iters) *iters = total;
+      return fail((frlap_status)hS.status, "Allen-Cahn CG solve stopped early");
+    }
+  }
+  if (iters) *iters = total;
+  return FRLAP_OK;
+}
+
+}  // namespace frlap

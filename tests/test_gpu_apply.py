@@ -1,0 +1,168 @@
+"""GPU parity of coefficients, symbol and FFT apply against the FP64 CPU oracle.
+
+Tolerances (normwise, since FFT rounding scales with the largest eigenvalue):
+  FP64 apply: ||y - y_ref||_2 <= 1e-12 * lambda_max * ||u||_2
+  FP32 apply: ||y - y_ref||_2 <= 1e-5  * lambda_max * ||u||_2
+  coefficients: every entry within 1e-13 relative (a_0 and a_k are single FP64 sums).
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import frlap_inputs as inp
+from oracle import fast, scheme
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=8)
+def _oracle_coef(d, alpha, h, N, gamma):
+    return scheme.coefficients(d, alpha, h, N, gamma)
+
+
+def _oracle(d, alpha, h, Ns, gamma=2.0):
+    N = max(Ns)
+    return _oracle_coef(d, alpha, h, N, gamma), scheme.c_d_alpha(d, alpha)
+
+
+def _t(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+@pytest.mark.parametrize("d,Ns,alpha,gamma", [
+    (2, (64, 64), 1.5, 2.0), (2, (40, 24), 0.3, 2.0), (2, (17, 17), 1.9, 1.95), (2, (2, 2), 1.0, 2.0),
+    (3, (16, 16, 16), 1.9, 2.0), (3, (12, 7, 9), 0.5, 2.0), (3, (10, 10, 10), 1.2, 1.6)])
+def test_coefficients_match_oracle(frlap, d, Ns, alpha, gamma):
+    h = 2.0 / max(Ns)
+    a_ref, _ = _oracle(d, alpha, h, Ns, gamma)
+    a = frlap.frlap_coeffs(d, alpha, gamma, h, Ns).cpu().numpy()
+    np.testing.assert_allclose(a, a_ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("d,Nmax,alpha", [(2, 2048, 1.5), (3, 256, 1.0)])
+def test_coefficients_full_size_sampled(frlap, d, Nmax, alpha):
+    """At the throughput sizes: a_0 and a spread of a_k, each against the oracle."""
+    h = 2.0 / Nmax
+    a = frlap.frlap_coeffs(d, alpha, 2.0, h, (Nmax,) * d).cpu().numpy()
+    a_ref, _ = _oracle(d, alpha, h, (Nmax,) * d)
+    rng = np.random.default_rng(7)
+    idx = [tuple([0] * d)] + [tuple(int(v) for v in rng.integers(0, Nmax + 1, size=d)) for _ in range(200)]
+    idx += [tuple([1] + [0] * (d - 1)), tuple([Nmax] * d), tuple([Nmax - 2] + [0] * (d - 1))]
+    for k in idx:
+        assert a[k] == pytest.approx(a_ref[k], rel=1e-13), k
+
+
+@pytest.mark.parametrize("d,Ns,alpha", [(2, (64, 64), 1.5), (2, (40, 24), 0.7), (3, (16, 16, 16), 1.9),
+                                         (3, (12, 7, 9), 0.5)])
+def test_symbol_matches_oracle(frlap, d, Ns, alpha):
+    h = 2.0 / max(Ns)
+    a_ref, c = _oracle(d, alpha, h, Ns)
+    plan = frlap.Plan(d, alpha, h, Ns)
+    shape = tuple(reversed([n - 1 for n in Ns]))
+    lam_ref = fast.symbol(a_ref, c, shape, P=tuple(reversed(plan.P)))
+    oct_ref = lam_ref[tuple(slice(0, p // 2 + 1) for p in reversed(plan.P))] / np.prod(plan.P)
+    lam = plan.symbol().cpu().numpy()
+    scale = np.abs(oct_ref).max()
+    assert np.abs(lam - oct_ref).max() <= 1e-14 * scale
+
+
+def _apply_case(frlap, d, Ns, alpha, u, prec, gamma=2.0):
+    h = 2.0 / max(Ns)
+    a_ref, c = _oracle(d, alpha, h, Ns, gamma)
+    op = fast.FastOperator(a_ref, c, u.shape)
+    y_ref = op(u)
+    plan = frlap.Plan(d, alpha, h, Ns, gamma=gamma, prec=prec)
+    dt = torch.float32 if prec == frlap.FRLAP_F32 else torch.float64
+    y = frlap.frlap_apply(plan, _t(u, dt)).double().cpu().numpy()
+    err = np.linalg.norm(y - y_ref) / (op.lam_max * np.linalg.norm(u))
+    return err, y, y_ref, a_ref, c
+
+
+APPLY_CASES = [
+    (2, (64, 64), 1.5), (2, (40, 24), 0.3), (2, (2, 2), 1.0), (2, (3, 5), 1.2), (2, (100, 70), 1.9),
+    (3, (16, 16, 16), 1.9), (3, (10, 12, 20), 0.8), (3, (2, 3, 2), 1.1), (3, (33, 9, 17), 1.4)]
+
+
+@pytest.mark.parametrize("d,Ns,alpha", APPLY_CASES)
+def test_apply_fp64_matches_oracle(frlap, d, Ns, alpha):
+    u = inp.normal_field(Ns, seed=0)
+    err, y, y_ref, a_ref, c = _apply_case(frlap, d, Ns, alpha, u, frlap.FRLAP_F64)
+    assert err <= 1e-12, err
+    if u.size <= 5000:  # full dense definition
+        y_dense = scheme.apply_dense(a_ref, c, u)
+        assert np.linalg.norm(y - y_dense) <= 1e-12 * np.linalg.norm(y_dense) * 10 + 1e-12 * np.abs(y_dense).max()
+
+
+@pytest.mark.parametrize("d,Ns,alpha", APPLY_CASES)
+def test_apply_fp32_matches_oracle(frlap, d, Ns, alpha):
+    u = inp.normal_field(Ns, seed=1)
+    err, *_ = _apply_case(frlap, d, Ns, alpha, u, frlap.FRLAP_F32)
+    assert err <= 1e-5, err
+
+
+def test_apply_config0_bubble_and_random(frlap):
+    """63x63, alpha = 1.5: one apply to N(0,1) and to (1-x^2)(1-y^2), against the dense matrix."""
+    Ns, alpha = (64, 64), 1.5
+    h = 2.0 / 64
+    a_ref, c = _oracle(2, alpha, h, Ns)
+    plan = frlap.Plan(2, alpha, h, Ns)
+    for u in (inp.normal_field(Ns, seed=0), inp.bubble_field(Ns, h, 1.0)):
+        y_ref = scheme.apply_dense(a_ref, c, u)
+        y = frlap.frlap_apply(plan, _t(u)).cpu().numpy()
+        lam_max = fast.FastOperator(a_ref, c, u.shape).lam_max
+        assert np.linalg.norm(y - y_ref) <= 1e-12 * lam_max * np.linalg.norm(u)
+
+
+def test_apply_linear_and_symmetric(frlap):
+    """Properties that hold at any size: A(a u + b v) = a A u + b A v and <A u, v> = <u, A v>."""
+    Ns, alpha = (96, 96, 96), 1.3
+    plan = frlap.Plan(3, alpha, 2.0 / 96, Ns)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    u = torch.randn(plan.shape, dtype=torch.float64, device="cuda", generator=g)
+    v = torch.randn(plan.shape, dtype=torch.float64, device="cuda", generator=g)
+    Au, Av = frlap.frlap_apply(plan, u), frlap.frlap_apply(plan, v)
+    Auv = frlap.frlap_apply(plan, (2.0 * u - 0.5 * v).contiguous())
+    assert torch.linalg.norm(Auv - (2.0 * Au - 0.5 * Av)) <= 1e-12 * torch.linalg.norm(Auv)
+    lhs, rhs = torch.dot(Au.flatten(), v.flatten()).item(), torch.dot(u.flatten(), Av.flatten()).item()
+    assert abs(lhs - rhs) <= 1e-11 * torch.linalg.norm(Au).item() * torch.linalg.norm(v).item()
+    assert torch.dot(Au.flatten(), u.flatten()).item() > 0
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_apply_2047_full_size(frlap, prec, tol):
+    """2D 2047^2, alpha = 1.5 (the throughput workload): against the NumPy-FFT oracle, plus sampled rows
+    of the dense definition."""
+    Ns, alpha = (2048, 2048), 1.5
+    h = 2.0 / 2048
+    u = inp.normal_field(Ns, seed=2)
+    a_ref, c = _oracle(2, alpha, h, Ns)
+    op = fast.FastOperator(a_ref, c, u.shape)
+    y_ref = op(u)
+    plan = frlap.Plan(2, alpha, h, Ns, prec=prec)
+    dt = torch.float32 if prec == 1 else torch.float64
+    y = frlap.frlap_apply(plan, _t(u, dt)).double().cpu().numpy()
+    assert np.linalg.norm(y - y_ref) <= tol * op.lam_max * np.linalg.norm(u)
+    rows = [(0, 0), (2046, 2046), (1023, 17), (5, 2000), (1500, 1499)]
+    yr = scheme.apply_rows(a_ref, c, u, rows)
+    for r, v in zip(rows, yr):
+        assert abs(y[r] - v) <= tol * op.lam_max * np.linalg.norm(u) / math.sqrt(u.size) * 50
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_apply_255_cubed_sampled_rows(frlap, prec, tol):
+    """3D 255^3, alpha = 1.0: sampled rows of the dense definition (each row is a full 255^3 sum)."""
+    Ns, alpha = (256, 256, 256), 1.0
+    h = 2.0 / 256
+    u = inp.normal_field(Ns, seed=4)
+    a_ref, c = _oracle(3, alpha, h, Ns)
+    plan = frlap.Plan(3, alpha, h, Ns, prec=prec)
+    dt = torch.float32 if prec == 1 else torch.float64
+    y = frlap.frlap_apply(plan, _t(u, dt)).double().cpu().numpy()
+    rows = [(0, 0, 0), (254, 254, 254), (127, 3, 250), (10, 200, 99)]
+    yr = scheme.apply_rows(a_ref, c, u, rows)
+    lam_max = float(plan.symbol().abs().max().item() * np.prod(plan.P))
+    for r, v in zip(rows, yr):
+        assert abs(y[r] - v) <= tol * lam_max * np.linalg.norm(u) / math.sqrt(u.size) * 50, (r, y[r], v)

@@ -1,0 +1,104 @@
+"""GPU parity of the CG, iterative-refinement and Allen-Cahn solvers against the FP64 oracle."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import frlap_inputs as inp
+from oracle import fast, scheme, solvers
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=8)
+def _coef(d, alpha, h, N):
+    return scheme.coefficients(d, alpha, h, N)
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=torch.float64)
+
+
+def test_cg_config0_poisson_f_equals_one(frlap):
+    """63x63, alpha = 1.5, f = 1 (Example 5.2.3 workload): CG to 1e-10 sits within 1e-10 of the exact
+    discrete solution (dense LU on the oracle's matrix)."""
+    Ns, alpha = (64, 64), 1.5
+    h = 2.0 / 64
+    a, c = _coef(2, alpha, h, 64), scheme.c_d_alpha(2, alpha)
+    f = inp.constant_field(Ns)
+    A = scheme.dense_matrix(a, c, f.shape)
+    x_ref = np.linalg.solve(A, f.reshape(-1)).reshape(f.shape)
+    plan = frlap.Plan(2, alpha, h, Ns)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f), rtol=1e-10)
+    x = x.cpu().numpy()
+    assert code == 0 and rel <= 1e-10
+    assert np.linalg.norm(x - x_ref) <= 1e-10 * np.linalg.norm(x_ref) * 10
+    # oracle CG takes the same path: iteration counts agree closely
+    _, it_ref, _ = solvers.cg(lambda v: scheme.apply_dense(a, c, v), f, rtol=1e-10)
+    assert abs(it - it_ref) <= 2
+
+
+@pytest.mark.parametrize("d,Ns,alpha", [(2, (48, 40), 0.7), (3, (16, 16, 16), 1.9), (3, (12, 10, 8), 1.0)])
+def test_cg_gaussian_sum(frlap, d, Ns, alpha):
+    h = 2.0 / max(Ns)
+    a, c = _coef(d, alpha, h, max(Ns)), scheme.c_d_alpha(d, alpha)
+    f = inp.gaussian_sum_field(Ns, h, seed=1)
+    op = fast.FastOperator(a, c, f.shape)
+    x_ref, _, rel_ref = solvers.cg(op, f, rtol=1e-13)
+    plan = frlap.Plan(d, alpha, h, Ns)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f), rtol=1e-12)
+    assert code == 0 and rel <= 1e-12
+    assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+
+
+@pytest.mark.parametrize("d,Ns,alpha", [(2, (128, 128), 1.8), (3, (24, 24, 24), 1.2)])
+def test_iterative_refinement_reaches_fp64_solution(frlap, d, Ns, alpha):
+    """FP32 inner CG inside FP64 refinement: the final solution is within 1e-10 of the FP64 solution."""
+    h = 2.0 / max(Ns)
+    a, c = _coef(d, alpha, h, max(Ns)), scheme.c_d_alpha(d, alpha)
+    f = inp.gaussian_sum_field(Ns, h, seed=3)
+    op = fast.FastOperator(a, c, f.shape)
+    x_ref, _, _ = solvers.cg(op, f, rtol=1e-13)
+    plan = frlap.Plan(d, alpha, h, Ns, prec=frlap.FRLAP_MIXED)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f), rtol=1e-11, solver=frlap.FRLAP_SOLVE_IR,
+                                             inner_rtol=1e-4)
+    assert code == 0 and rel <= 1e-11
+    assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+
+
+def test_allen_cahn_steps_match_oracle(frlap):
+    Ns, alpha, tau, eps = (64, 64), 1.6, 1e-3, 0.05
+    h = 2.0 / 64
+    a, c = _coef(2, alpha, h, 64), scheme.c_d_alpha(2, alpha)
+    u0 = inp.uniform_field(Ns, seed=5)
+    op = fast.FastOperator(a, c, u0.shape)
+    u_ref = u0.copy()
+    for _ in range(3):
+        u_ref, _, _ = solvers.allen_cahn_step(op, u_ref, tau, eps, rtol=1e-13)
+    plan = frlap.Plan(2, alpha, h, Ns)
+    u = _t(u0)
+    it = frlap.frlap_allen_cahn_step(plan, u, tau, eps, nsteps=3, rtol=1e-13)
+    assert it > 0
+    u = u.cpu().numpy()
+    assert np.abs(u - u_ref).max() <= 1e-11
+    assert np.abs(u).max() <= 1.0  # discrete maximum principle
+
+
+def test_solver_error_paths(frlap):
+    """Failures are reported by status code and leave the context usable."""
+    Ns, alpha = (32, 32), 1.5
+    h = 2.0 / 32
+    plan = frlap.Plan(2, alpha, h, Ns)
+    f = _t(inp.gaussian_sum_field(Ns, h, seed=1))
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-12, maxit=2, raise_on_error=False)
+    assert code == 5 and it == 2 and rel > 1e-12  # FRLAP_ENOCONV
+    fbad = f.clone()
+    fbad[3, 4] = float("nan")
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, fbad, rtol=1e-10, raise_on_error=False)
+    assert code == 7  # FRLAP_ENAN
+    with pytest.raises(frlap.FrlapError):
+        frlap.frlap_pcg_solve(plan, f, rtol=1e-10, solver=frlap.FRLAP_SOLVE_IR)  # needs a MIXED plan
+    # the context still works
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-10)
+    assert code == 0 and rel <= 1e-10
