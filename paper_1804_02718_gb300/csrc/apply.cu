@@ -29,7 +29,7 @@ struct LamMap {
 };
 
 template <typename T>
-__global__ void k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
+__global__ void __launch_bounds__(512) k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -75,7 +75,7 @@ __global__ void k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int
 }
 
 template <typename T>
-__global__ void k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
+__global__ void __launch_bounds__(512) k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -118,7 +118,7 @@ __global__ void k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int
 
 // lines of length n (contiguous, stride ld) -> zero-pad to P, FFT, * lambda, IFFT, crop, in place
 template <typename T>
-__global__ void k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
+__global__ void __launch_bounds__(512) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
                          const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -158,7 +158,7 @@ __global__ void k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
 template <typename T>
-__global__ void k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+__global__ void __launch_bounds__(512) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -186,7 +186,7 @@ __global__ void k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__
 
 // transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
 template <typename T>
-__global__ void k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+__global__ void __launch_bounds__(512) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -215,10 +215,11 @@ __global__ void k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__
 
 // Lines per CTA for a line of `len` complex slots: as many as fit in
 // `budget` bytes of shared memory and 1024 threads (at least one).
+// (every apply kernel is compiled for at most 512 threads per CTA)
 int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
   int tl = budget / (len * elem_bytes);
   tl = tl < 1 ? 1 : tl;
-  while (tl > 1 && tl * G > 1024) --tl;
+  while (tl > 1 && tl * G > 512) --tl;
   if (tl > max_lines) tl = max_lines;
   return tl < 1 ? 1 : tl;
 }

@@ -255,7 +255,7 @@ __global__ void k_sym_init(const double* __restrict__ coef, int Nmax, int d, int
 
 // even DFT along one axis of the octant: for every line (stride `stride`, P/2+1 entries)
 // g(j) = sum_{k = -P/2+1}^{P/2} t(|k|) e^{-2 pi i j k / P}, j = 0..P/2 (real, since t is even)
-__global__ void k_sym_axis(double* lam, size_t nlines, int logP, size_t stride, size_t inner, int TL,
+__global__ void __launch_bounds__(512) k_sym_axis(double* lam, size_t nlines, int logP, size_t stride, size_t inner, int TL,
                            const double2* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* smem = reinterpret_cast<double2*>(smem_raw);
@@ -352,7 +352,7 @@ cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam, cudaSt
     const int G = P >> 4;
     int tl = (48 * 1024) / (P * 16);
     if (tl < 1) tl = 1;
-    while (tl > 1 && tl * G > 1024) --tl;
+    while (tl > 1 && tl * G > 512) --tl;
     // lines along axis r: stride = product of H1 of faster axes; inner = that same product
     size_t stride = 1;
     for (int q = 0; q < r; ++q) stride *= H1[q];

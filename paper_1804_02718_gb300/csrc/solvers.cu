@@ -342,6 +342,8 @@ static frlap_status true_residual(const Plan& p, const double* f, const double* 
   double* partials = reinterpret_cast<double*>(w);
   w += align256(2 * kBlocks * sizeof(double));
   CgState* S = reinterpret_cast<CgState*>(w);
+  // the reduction ticket must start at zero (this workspace may not have run a CG yet)
+  FRLAP_CUDA_TRY(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), st));
   cudaError_t e = apply_launch<double>(p, x, q, awork, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
   double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
