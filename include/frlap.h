@@ -123,6 +123,27 @@ int frlap_apply_nstages(const frlap_plan* plan);
 frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream,
                                   void* const* events);
 
+/* Size of the device array behind frlap_apply_noalloc: 32 MiB. */
+#define FRLAP_NOALLOC_MAX_BYTES (32u << 20)
+
+/* frlap_apply for callers that must not allocate device memory at call time:
+ * code inside a host framework that owns the GPU's memory and forbids
+ * cudaMalloc, and latency-bound loops that cannot afford the device-wide
+ * synchronisation a cudaMalloc/cudaFree implies.  The paper has no counterpart;
+ * this is a library convenience.  Same product, arguments and result as
+ * frlap_apply, but the scratch is a fixed library-owned device array of
+ * FRLAP_NOALLOC_MAX_BYTES, reserved on every GPU that loads the library until
+ * the process exits.  The call allocates nothing.
+ *  - Limit: plans whose frlap_workspace_bytes(plan, FRLAP_OP_APPLY) exceeds
+ *    FRLAP_NOALLOC_MAX_BYTES are rejected with FRLAP_EINVAL and a message
+ *    (2D: FP64 grids up to 1024^2 and FP32 up to 2047^2 fit; 3D FP64 up to 63^3).
+ *  - The first call on a device looks up the array's device address on the
+ *    current device; make that first call before any stream capture.
+ *  - All calls on a device share the array: two calls whose GPU work overlaps
+ *    (unordered streams) race and give wrong results.  Calls ordered on one
+ *    stream are safe; no state carries over from one call to the next. */
+frlap_status frlap_apply_noalloc(const frlap_plan* plan, const void* d_u, void* d_y, void* stream);
+
 /* Same product in FP32 on a MIXED plan (float in, float out). */
 frlap_status frlap_apply_f32(const frlap_plan* plan, const float* d_u, float* d_y, void* d_work, void* stream);
 

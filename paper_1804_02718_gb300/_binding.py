@@ -38,6 +38,7 @@ _SIGS = {
     "frlap_plan_symbol": (_I, [_P, _P, _P]),
     "frlap_apply": (_I, [_P, _P, _P, _P, _P]),
     "frlap_apply_f32": (_I, [_P, _P, _P, _P, _P]),
+    "frlap_apply_noalloc": (_I, [_P, _P, _P, _P]),
     "frlap_apply_nstages": (_I, [_P]),
     "frlap_apply_profiled": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
@@ -198,6 +199,19 @@ def frlap_apply(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch
         work = plan.workspace(FRLAP_OP_APPLY)
     _check(lib().frlap_apply(plan.handle, _dev(u, dt, "u"), _dev(y, dt, "y"), ctypes.c_void_p(work.data_ptr()),
                              _stream(stream)), "frlap_apply")
+    return y
+
+
+NOALLOC_MAX_BYTES = 32 << 20
+
+
+def frlap_apply_noalloc(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, stream=None):
+    """y = A u with the library's static scratch array (no workspace argument, no allocation in the call)."""
+    dt = _apply_dtype(plan)
+    if y is None:
+        y = torch.empty_like(u)
+    _check(lib().frlap_apply_noalloc(plan.handle, _dev(u, dt, "u"), _dev(y, dt, "y"), _stream(stream)),
+           "frlap_apply_noalloc")
     return y
 
 

@@ -60,8 +60,6 @@ static int ilog2(int v) {
 
 using namespace frlap;
 
-struct frlap_plan : public frlap::Plan {};
-
 extern "C" {
 
 const char* frlap_last_error(void) { return g_last_error.c_str(); }

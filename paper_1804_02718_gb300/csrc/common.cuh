@@ -103,3 +103,6 @@ cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s,
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace frlap
+
+// the opaque handle of the C ABI is the plan itself
+struct frlap_plan : public frlap::Plan {};
