@@ -29,7 +29,7 @@ struct LamMap {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -41,41 +41,43 @@ __global__ void __launch_bounds__(512) k_r2c_T(const T* __restrict__ in, cplx<T>
   const int line0 = blockIdx.x * TL;
   const int line = line0 + l;
   const bool valid = line < nlines;
-  C* buf = smem + (size_t)l * (H + 1);
+  const int LS = sline(H);
+  C* buf = smem + (size_t)l * LS;
   T* rb = reinterpret_cast<T*>(buf);
   const T* src = in + (size_t)(valid ? line : 0) * ldi;
-  for (int i = lane; i < 2 * H; i += G) rb[i] = (valid && i < n) ? src[i] : (T)0;
+  // real sample i is component (i & 1) of complex element i / 2 (even/odd packing)
+  for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? src[i] : (T)0;
   __syncthreads();
   fft_line<T, -1>(buf, logH, lane, tw, logP);
   // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
   for (int k = lane; k <= H / 2; k += G) {
     const int km = H - k;
-    const C zk = buf[k];
-    const C zm = buf[km & (H - 1)];
+    const C zk = buf[spad(k)];
+    const C zm = buf[spad(km & (H - 1))];
     const T half = (T)0.5;
     {
       const C a = zk, b = conjg(zm);
       const C xe = half * (a + b);
       const C xo = half * mul_i<-1>(a - b);
-      buf[k] = xe + cmul(tw[k], xo);
+      buf[spad(k)] = xe + cmul(tw[k], xo);
     }
     if (k != km) {
       const C a = zm, b = conjg(zk);
       const C xe = half * (a + b);
       const C xo = half * mul_i<-1>(a - b);
-      buf[km] = xe + cmul(tw[km], xo);
+      buf[spad(km)] = xe + cmul(tw[km], xo);
     }
   }
   __syncthreads();
   const int total = TL * (H + 1);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l2 = idx % TL, k = idx / TL;
-    if (line0 + l2 < nlines) out[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * (H + 1) + k];
+    if (line0 + l2 < nlines) out[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * LS + spad(k)];
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -86,25 +88,26 @@ __global__ void __launch_bounds__(512) k_c2r_T(const cplx<T>* __restrict__ in, T
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int line0 = blockIdx.x * TL;
   const int line = line0 + l;
+  const int LS = sline(H);
   const int total = TL * (H + 1);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l2 = idx % TL, k = idx / TL;
-    smem[(size_t)l2 * (H + 1) + k] = (line0 + l2 < nlines) ? in[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
+    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? in[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
   }
   __syncthreads();
-  C* buf = smem + (size_t)l * (H + 1);
+  C* buf = smem + (size_t)l * LS;
   // repack: Z[k] = (X[k] + conj X[H-k]) + i W^{-k} (X[k] - conj X[H-k]), so that the
   // unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1])
   for (int k = lane; k <= H / 2; k += G) {
     const int km = H - k;
-    const C xk = buf[k], xm = buf[km];
+    const C xk = buf[spad(k)], xm = buf[spad(km)];
     {
       const C a = xk, b = conjg(xm);
-      buf[k] = (a + b) + mul_i<1>(cmulc(a - b, tw[k]));
+      buf[spad(k)] = (a + b) + mul_i<1>(cmulc(a - b, tw[k]));
     }
     if (k != km && km != H) {
       const C a = xm, b = conjg(xk);
-      buf[km] = (a + b) + mul_i<1>(cmulc(a - b, tw[km]));
+      buf[spad(km)] = (a + b) + mul_i<1>(cmulc(a - b, tw[km]));
     }
   }
   __syncthreads();
@@ -112,13 +115,13 @@ __global__ void __launch_bounds__(512) k_c2r_T(const cplx<T>* __restrict__ in, T
   if (line < nlines) {
     const T* rb = reinterpret_cast<const T*>(buf);
     T* dst = out + (size_t)line * ldo;
-    for (int i = lane; i < n; i += G) dst[i] = rb[i];
+    for (int i = lane; i < n; i += G) dst[i] = rb[2 * spad(i >> 1) + (i & 1)];
   }
 }
 
 // lines of length n (contiguous, stride ld) -> zero-pad to P, FFT, * lambda, IFFT, crop, in place
 template <typename T>
-__global__ void __launch_bounds__(512) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
                          const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -129,9 +132,9 @@ __global__ void __launch_bounds__(512) k_colmul(cplx<T>* __restrict__ data, int 
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int col = blockIdx.x * TL + l;
   const bool valid = col < ncols;
-  C* buf = smem + (size_t)l * P;
+  C* buf = smem + (size_t)l * sline(P);
   C* line = data + (size_t)(valid ? col : 0) * ld;
-  for (int i = lane; i < P; i += G) buf[i] = (valid && i < n) ? line[i] : mk<C>(0, 0);
+  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? line[i] : mk<C>(0, 0);
   __syncthreads();
   fft_line<T, -1>(buf, logP, lane, tw, logPtab);
   size_t lam_base;
@@ -148,17 +151,17 @@ __global__ void __launch_bounds__(512) k_colmul(cplx<T>* __restrict__ data, int 
   }
   for (int k = lane; k < P; k += G) {
     const int kf = min(k, P - k);
-    buf[k] = lam[lam_base + (size_t)kf * lam_stride] * buf[k];
+    buf[spad(k)] = lam[lam_base + (size_t)kf * lam_stride] * buf[spad(k)];
   }
   __syncthreads();
   fft_line<T, 1>(buf, logP, lane, tw, logPtab);
   if (valid)
-    for (int i = lane; i < n; i += G) line[i] = buf[i];
+    for (int i = lane; i < n; i += G) line[i] = buf[spad(i)];
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
 template <typename T>
-__global__ void __launch_bounds__(512) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -171,22 +174,23 @@ __global__ void __launch_bounds__(512) k_c2cT_fwd(const cplx<T>* __restrict__ in
   const int line0 = tile * TL;
   const int line = line0 + l;
   const bool valid = line < nlines;
-  C* buf = smem + (size_t)l * P;
+  const int LS = sline(P);
+  C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
-  for (int i = lane; i < P; i += G) buf[i] = (valid && i < n) ? src[i] : mk<C>(0, 0);
+  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : mk<C>(0, 0);
   __syncthreads();
   fft_line<T, -1>(buf, logP, lane, tw, logPtab);
   C* dst = out + g * gout;
   const int total = TL * P;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l2 = idx % TL, k = idx / TL;
-    if (line0 + l2 < nlines) dst[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * P + k];
+    if (line0 + l2 < nlines) dst[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * LS + spad(k)];
   }
 }
 
 // transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
 template <typename T>
-__global__ void __launch_bounds__(512) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
   using C = cplx<T>;
@@ -199,17 +203,18 @@ __global__ void __launch_bounds__(512) k_c2cT_inv(const cplx<T>* __restrict__ in
   const int line0 = tile * TL;
   const int line = line0 + l;
   const C* src = in + g * gin;
+  const int LS = sline(P);
   const int total = TL * P;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l2 = idx % TL, k = idx / TL;
-    smem[(size_t)l2 * P + k] = (line0 + l2 < nlines) ? src[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
+    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? src[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
   }
   __syncthreads();
-  C* buf = smem + (size_t)l * P;
+  C* buf = smem + (size_t)l * LS;
   fft_line<T, 1>(buf, logP, lane, tw, logPtab);
   if (line < nlines) {
     C* dst = out + g * gout + (size_t)line * ldo;
-    for (int i = lane; i < n; i += G) dst[i] = buf[i];
+    for (int i = lane; i < n; i += G) dst[i] = buf[spad(i)];
   }
 }
 
@@ -271,8 +276,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
   // ---- stage 1: rows of u -> S1[kx][row]
   {
     const int G = Hx >> 4;
-    const int tl = pick_tl(Hx + 1, eb, G, budget, 64);
-    const size_t sm = (size_t)tl * (Hx + 1) * eb;
+    const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e = set_smem(k_r2c_T<T>, sm);
     if (e != cudaSuccess) return e;
     const int grid = (nrows + tl - 1) / tl;
@@ -288,8 +293,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
   map.Hy1 = p.P[1] / 2 + 1;
   if (p.d == 2) {
     const int G = p.P[1] >> 4;
-    const int tl = pick_tl(p.P[1], eb, G, budget, 64);
-    const size_t sm = (size_t)tl * p.P[1] * eb;
+    const int tl = pick_tl(sline(p.P[1]), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(p.P[1]) * eb;
     cudaError_t e = set_smem(k_colmul<T>, sm);
     if (e != cudaSuccess) return e;
     const int ncols = Hx + 1;
@@ -302,8 +307,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
     // ---- stage 2: S1[kx][z][y] -> FFT_y -> S2[kx][ky][z]
     {
       const int G = Py >> 4;
-      const int tl = pick_tl(Py, eb, G, budget, 64);
-      const size_t sm = (size_t)tl * Py * eb;
+      const int tl = pick_tl(sline(Py), eb, G, budget, 64);
+      const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e = set_smem(k_c2cT_fwd<T>, sm);
       if (e != cudaSuccess) return e;
       const int tiles = (nz + tl - 1) / tl;
@@ -316,8 +321,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
     // ---- stage 3: S2[kx][ky][:] -> FFT_z, * lambda, IFFT_z
     {
       const int G = Pz >> 4;
-      const int tl = pick_tl(Pz, eb, G, budget, 64);
-      const size_t sm = (size_t)tl * Pz * eb;
+      const int tl = pick_tl(sline(Pz), eb, G, budget, 64);
+      const size_t sm = (size_t)tl * sline(Pz) * eb;
       cudaError_t e = set_smem(k_colmul<T>, sm);
       if (e != cudaSuccess) return e;
       const int ncols = (Hx + 1) * Py;
@@ -329,8 +334,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
     // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
     {
       const int G = Py >> 4;
-      const int tl = pick_tl(Py, eb, G, budget, 64);
-      const size_t sm = (size_t)tl * Py * eb;
+      const int tl = pick_tl(sline(Py), eb, G, budget, 64);
+      const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e = set_smem(k_c2cT_inv<T>, sm);
       if (e != cudaSuccess) return e;
       const int tiles = (nz + tl - 1) / tl;
@@ -344,8 +349,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
   // ---- last stage: S1[kx][row] -> rows of y
   {
     const int G = Hx >> 4;
-    const int tl = pick_tl(Hx + 1, eb, G, budget, 64);
-    const size_t sm = (size_t)tl * (Hx + 1) * eb;
+    const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e = set_smem(k_c2r_T<T>, sm);
     if (e != cudaSuccess) return e;
     const int grid = (nrows + tl - 1) / tl;

@@ -266,15 +266,15 @@ __global__ void __launch_bounds__(512) k_sym_axis(double* lam, size_t nlines, in
   // line index -> base offset: lines enumerate (outer, inner) with `inner` lines per outer slab
   const size_t li = valid ? line : 0;
   const size_t base = (li / inner) * inner * (size_t)(H + 1) + (li % inner);
-  double2* buf = smem + (size_t)l * P;
+  double2* buf = smem + (size_t)l * sline(P);
   for (int j = lane; j < P; j += G) {
     const int kf = min(j, P - j);
-    buf[j] = make_double2(valid ? lam[base + (size_t)kf * stride] : 0.0, 0.0);
+    buf[spad(j)] = make_double2(valid ? lam[base + (size_t)kf * stride] : 0.0, 0.0);
   }
   __syncthreads();
   fft_line<double, -1>(buf, logP, lane, tw, logP);
   if (valid)
-    for (int j = lane; j <= H; j += G) lam[base + (size_t)j * stride] = buf[j].x;
+    for (int j = lane; j <= H; j += G) lam[base + (size_t)j * stride] = buf[spad(j)].x;
 }
 
 __global__ void k_scale_copy(double* lam64, float* lam32, size_t n, double s) {
@@ -350,14 +350,14 @@ cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam, cudaSt
     const int P = p.P[r];
     const int logP = p.logP[r];
     const int G = P >> 4;
-    int tl = (48 * 1024) / (P * 16);
+    int tl = (48 * 1024) / (sline(P) * 16);
     if (tl < 1) tl = 1;
     while (tl > 1 && tl * G > 512) --tl;
     // lines along axis r: stride = product of H1 of faster axes; inner = that same product
     size_t stride = 1;
     for (int q = 0; q < r; ++q) stride *= H1[q];
     const size_t nlines = total / H1[r];
-    const size_t sm = (size_t)tl * P * 16;
+    const size_t sm = (size_t)tl * sline(P) * 16;
     e = cudaFuncSetAttribute(k_sym_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((nlines + tl - 1) / tl);

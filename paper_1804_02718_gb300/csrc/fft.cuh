@@ -1,7 +1,8 @@
 // Shared-memory FFT of one power-of-two line per thread group, used by every
 // stage of the circulant-embedding apply and by the symbol generation.
 //
-// Layout: a CTA holds TL lines in shared memory; each line of length L = 2^logL
+// Layout: a CTA holds TL lines in shared memory, each in sline(L) slots with
+// element i at slot spad(i); each line of length L = 2^logL
 // (16 <= L) is processed by G = L/16 threads ("lanes"), each holding 16 complex
 // values in registers per stage.  Stages are Stockham (self-sorting): stage s
 // reads x[j + r L/R], multiplies by the twiddles W_{Ns R}^{r k} (k = j mod Ns),
@@ -18,6 +19,13 @@
 #include "common.cuh"
 
 namespace frlap {
+
+// Shared-memory index of logical element i of a line: one padding slot after
+// every 16 elements, so that the stride-R stores of the early Stockham stages
+// and the contiguous loads both spread over the banks.
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+// Slots per line for logical indices 0..L (L itself is used by the real-data transforms).
+__host__ __device__ __forceinline__ int sline(int L) { return L + (L >> 4) + 1; }
 
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft2(C& a, C& b) {
@@ -103,7 +111,35 @@ __device__ __forceinline__ void dftR(C* v) {
   else dft16<SIGN>(v);
 }
 
-// One Stockham stage of radix R on a line of length L = 2^logL held in `buf`.
+// The 15 twiddles W^r, r = 1..15, of one radix-16 butterfly (W = tw[idx1]).  FP64 loads
+// every power from the table (the FP64 pipe is the bottleneck there); FP32 loads
+// W, W^4 and W^8 and forms the rest with at most three chained products.
+template <typename T>
+__device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict__ tw, int k, int sh) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int r = 1; r < 16; ++r) w[r] = tw[(r * k) << sh];
+  } else {
+    w[1] = tw[k << sh];
+    w[4] = tw[(4 * k) << sh];
+    w[8] = tw[(8 * k) << sh];
+    w[2] = cmul(w[1], w[1]);
+    w[3] = cmul(w[2], w[1]);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+    w[9] = cmul(w[8], w[1]);
+    w[10] = cmul(w[8], w[2]);
+    w[11] = cmul(w[8], w[3]);
+    w[12] = cmul(w[8], w[4]);
+    w[13] = cmul(w[12], w[1]);
+    w[14] = cmul(w[12], w[2]);
+    w[15] = cmul(w[12], w[3]);
+  }
+}
+
+// One Stockham stage of radix R on a line of length L = 2^logL held in `buf`
+// (padded layout, see spad).
 template <typename T, int R, int SIGN>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int logNs, int lane,
                                           const cplx<T>* __restrict__ tw, int logPtab) {
@@ -117,7 +153,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
   for (int b = 0; b < B; ++b) {
     const int j = lane + b * G;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b * R + r] = buf[j + r * LR];
+    for (int r = 0; r < R; ++r) v[b * R + r] = buf[spad(j + r * LR)];
   }
   __syncthreads();
 #pragma unroll
@@ -127,16 +163,23 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
     if (Ns > 1) {
       // W_{Ns R}^{r k} = tw[r k Ptab / (Ns R)]
       const int sh = logPtab - logNs - LOGR;
+      if constexpr (R == 16) {
+        C w[16];
+        twiddles16<T>(w, tw, k, sh);
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const C w = tw[(r * k) << sh];
-        v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], w) : cmulc(v[b * R + r], w);
+        for (int r = 1; r < 16; ++r) v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], w[r]) : cmulc(v[b * R + r], w[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const C w = tw[(r * k) << sh];
+          v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], w) : cmulc(v[b * R + r], w);
+        }
       }
     }
     dftR<R, SIGN>(&v[b * R]);
     const int o = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[o + r * Ns] = v[b * R + r];
+    for (int r = 0; r < R; ++r) buf[spad(o + r * Ns)] = v[b * R + r];
   }
   __syncthreads();
 }
