@@ -68,6 +68,15 @@ typedef enum {
   FRLAP_SOLVE_IR = 1       /* FP64 iterative refinement around FP32 CG (MIXED plans) */
 } frlap_solver;
 
+/* Preconditioners of frlap_pcg_solve.  Each is a Fourier multiplier applied
+ * through the same circulant embedding as A (one FP32 apply per iteration),
+ * so the outer FP64 iteration is flexible (Polak-Ribiere) PCG. */
+typedef enum {
+  FRLAP_PRECOND_NONE = 0,
+  FRLAP_PRECOND_STRANG = 1,   /* inverse of the multilevel Strang circulant (built by frlap_precond_strang) */
+  FRLAP_PRECOND_LEARNED = 2   /* a multiplier set by frlap_precond_set_symbol (e.g. the learned MLP's) */
+} frlap_precond;
+
 typedef struct frlap_plan frlap_plan;
 
 /* c_{d,alpha} = 2^(alpha-1) alpha Gamma((d+alpha)/2) / (pi^(d/2) Gamma(1-alpha/2))
@@ -153,13 +162,35 @@ frlap_status frlap_apply_f32(const frlap_plan* plan, const float* d_u, float* d_
  * solution on exit.  Stops when ||f - A x||_2 <= rtol ||f||_2 (recursive
  * residual, then confirmed with a true FP64 residual), or after maxit iterations.
  * solver = FRLAP_SOLVE_CG (any plan but F32) or FRLAP_SOLVE_IR (MIXED plans: FP32 CG
- * inner solves to inner_rtol, FP64 outer residual and update).
+ * inner solves to inner_rtol, FP64 outer residual and update).  precond =
+ * frlap_precond (applied in FP32 inside the CG iteration: flexible PCG).
  * *iters (may be NULL) receives the CG iterations (IR: total inner iterations),
  * *relres (may be NULL) the final true relative residual.  Synchronises stream.
  * Returns FRLAP_ENOCONV if rtol was not reached. */
 frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* d_x, double rtol, int maxit,
-                             int solver, double inner_rtol, int* iters, double* relres, void* d_work,
+                             int solver, int precond, double inner_rtol, int* iters, double* relres, void* d_work,
                              void* stream);
+
+/* Build the Strang-circulant preconditioner of the plan (set-up call: allocates
+ * the symbol and temporary scratch).  The Strang circulant S keeps, along each
+ * axis, the Toeplitz entry of offset min(j, n_r - j) in its first column; its
+ * inverse is a multilevel circulant, applied through A's embedding.  Its
+ * eigenvalues are positive for this operator (A is strictly diagonally
+ * dominant); non-positive ones would be dropped and are counted in
+ * *n_nonpositive (may be NULL).  Synchronises stream. */
+frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* stream);
+
+/* z = M^-1 r for one of the plan's preconditioners, in FP32 (r, z: prod(n_r)
+ * floats, not overlapping; d_work: frlap_workspace_bytes(plan, FRLAP_OP_APPLY)). */
+frlap_status frlap_precond_apply(const frlap_plan* plan, int precond, const float* d_r, float* d_z, void* d_work,
+                                 void* stream);
+
+/* Install a preconditioner multiplier m (octant layout of frlap_plan_symbol:
+ * prod_r (P_r/2+1) doubles, x fastest) as FRLAP_PRECOND_LEARNED: M^-1 r =
+ * restrict(IDFT(m * DFT(zero-padded r))) with the 1/prod(P_r) factor applied
+ * by the library.  m must be positive for M to be SPD.  The plan keeps an FP32
+ * copy (allocated on the first call). */
+frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void* stream);
 
 /* nsteps semi-implicit steps of the fractional Allen-Cahn equation
  * u_t = -eps^2 (-Delta)^{alpha/2} u + u - u^3 with u = 0 outside the box:

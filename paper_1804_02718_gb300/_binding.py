@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfrlap.so")
 FRLAP_F64, FRLAP_F32, FRLAP_MIXED = 0, 1, 2
 FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_OP_AC = 0, 1, 2
 FRLAP_SOLVE_CG, FRLAP_SOLVE_IR = 0, 1
+FRLAP_PRECOND_NONE, FRLAP_PRECOND_STRANG, FRLAP_PRECOND_LEARNED = 0, 1, 2
 
 STATUS = {
     0: "FRLAP_OK", 1: "FRLAP_EINVAL", 2: "FRLAP_ENOMEM", 3: "FRLAP_EWORKSPACE", 4: "FRLAP_ECUDA",
@@ -41,7 +42,10 @@ _SIGS = {
     "frlap_apply_noalloc": (_I, [_P, _P, _P, _P]),
     "frlap_apply_nstages": (_I, [_P]),
     "frlap_apply_profiled": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
-    "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
+    "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
+    "frlap_precond_strang": (_I, [_P, ctypes.POINTER(_I), _P]),
+    "frlap_precond_set_symbol": (_I, [_P, _P, _P]),
+    "frlap_precond_apply": (_I, [_P, _I, _P, _P, _P, _P]),
     "frlap_allen_cahn_step": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), _P, _P]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
@@ -244,7 +248,7 @@ def frlap_apply_f32(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: t
 
 def frlap_pcg_solve(plan: Plan, f: torch.Tensor, x: torch.Tensor = None, rtol: float = 1e-10, maxit: int = 100000,
                     solver: int = FRLAP_SOLVE_CG, inner_rtol: float = 1e-4, work: torch.Tensor = None,
-                    stream=None, raise_on_error: bool = True):
+                    stream=None, raise_on_error: bool = True, precond: int = FRLAP_PRECOND_NONE):
     """Solve A x = f; returns (x, iterations, true relative residual, status code)."""
     if x is None:
         x = torch.zeros_like(f)
@@ -253,11 +257,35 @@ def frlap_pcg_solve(plan: Plan, f: torch.Tensor, x: torch.Tensor = None, rtol: f
     it = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
     code = lib().frlap_pcg_solve(plan.handle, _dev(f, torch.float64, "f"), _dev(x, torch.float64, "x"), rtol,
-                                 int(maxit), solver, inner_rtol, ctypes.byref(it), ctypes.byref(rel),
+                                 int(maxit), solver, precond, inner_rtol, ctypes.byref(it), ctypes.byref(rel),
                                  ctypes.c_void_p(work.data_ptr()), _stream(stream))
     if raise_on_error:
         _check(code, "frlap_pcg_solve")
     return x, it.value, rel.value, code
+
+
+def frlap_precond_strang(plan: Plan, stream=None) -> int:
+    """Build the Strang-circulant preconditioner; returns the number of dropped non-positive eigenvalues."""
+    bad = ctypes.c_int(0)
+    _check(lib().frlap_precond_strang(plan.handle, ctypes.byref(bad), _stream(stream)), "frlap_precond_strang")
+    return bad.value
+
+
+def frlap_precond_apply(plan: Plan, precond: int, r: torch.Tensor, z: torch.Tensor = None, work=None, stream=None):
+    """z = M^-1 r (FP32) for the plan's Strang or learned preconditioner."""
+    if z is None:
+        z = torch.empty_like(r)
+    if work is None:
+        work = plan.workspace(FRLAP_OP_APPLY)
+    _check(lib().frlap_precond_apply(plan.handle, precond, _dev(r, torch.float32, "r"), _dev(z, torch.float32, "z"),
+                                     ctypes.c_void_p(work.data_ptr()), _stream(stream)), "frlap_precond_apply")
+    return z
+
+
+def frlap_precond_set_symbol(plan: Plan, m: torch.Tensor, stream=None):
+    """Install a multiplier octant (float64, shape of plan.symbol()) as the LEARNED preconditioner."""
+    _check(lib().frlap_precond_set_symbol(plan.handle, _dev(m, torch.float64, "m"), _stream(stream)),
+           "frlap_precond_set_symbol")
 
 
 def frlap_allen_cahn_step(plan: Plan, u: torch.Tensor, tau: float, eps: float, nsteps: int = 1,

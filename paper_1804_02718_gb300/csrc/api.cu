@@ -28,7 +28,11 @@ size_t cg_work_bytes(const Plan& p, int eb);
 size_t ir_work_bytes(const Plan& p);
 size_t ac_work_bytes(const Plan& p);
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
-                            double inner_rtol, int* iters, double* relres, void* work, cudaStream_t st);
+                            const float* mu, double inner_rtol, int* iters, double* relres, void* work,
+                            cudaStream_t st);
+size_t strang_scratch_bytes(const Plan& p);
+cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host);
+cudaError_t scale_to_f32_launch(const double* src, float* dst, size_t n, double s, cudaStream_t st);
 frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, int nsteps, double rtol,
                              int* iters, void* work, cudaStream_t st);
 
@@ -94,6 +98,8 @@ frlap_status frlap_plan_destroy(frlap_plan* plan) {
   if (!plan) return FRLAP_OK;
   cudaFree(plan->lam64);
   cudaFree(plan->lam32);
+  cudaFree(plan->mu_strang);
+  cudaFree(plan->mu_learned);
   for (int r = 0; r < 3; ++r) {
     cudaFree(plan->tw64[r]);
     cudaFree(plan->tw32[r]);
@@ -275,9 +281,19 @@ frlap_status frlap_apply_f32(const frlap_plan* plan, const float* d_u, float* d_
 }
 
 frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* d_x, double rtol, int maxit,
-                             int solver, double inner_rtol, int* iters, double* relres, void* d_work,
+                             int solver, int precond, double inner_rtol, int* iters, double* relres, void* d_work,
                              void* stream) {
   if (!plan || !d_f || !d_x) return fail(FRLAP_EINVAL, "plan, d_f or d_x is NULL");
+  const float* mu = nullptr;
+  if (precond == FRLAP_PRECOND_STRANG) {
+    if (!plan->mu_strang) return fail(FRLAP_EINVAL, "Strang preconditioner not built (frlap_precond_strang)");
+    mu = plan->mu_strang;
+  } else if (precond == FRLAP_PRECOND_LEARNED) {
+    if (!plan->mu_learned) return fail(FRLAP_EINVAL, "no learned multiplier set (frlap_precond_set_symbol)");
+    mu = plan->mu_learned;
+  } else if (precond != FRLAP_PRECOND_NONE) {
+    return fail(FRLAP_EINVAL, "unknown preconditioner");
+  }
   if (!(rtol > 0.0) || maxit < 1) return fail(FRLAP_EINVAL, "need rtol > 0 and maxit >= 1");
   if (solver == FRLAP_SOLVE_CG && plan->prec == FRLAP_F32)
     return fail(FRLAP_EINVAL, "FP64 CG needs an F64 or MIXED plan");
@@ -288,8 +304,51 @@ frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* 
     return fail(FRLAP_EINVAL, "inner_rtol must lie in (0, 1)");
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
-  return pcg_solve_impl(*plan, d_f, d_x, rtol, maxit, solver, inner_rtol, iters, relres, d_work,
+  return pcg_solve_impl(*plan, d_f, d_x, rtol, maxit, solver, mu, inner_rtol, iters, relres, d_work,
                         (cudaStream_t)stream);
+}
+
+frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* stream) {
+  if (!plan) return fail(FRLAP_EINVAL, "plan is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!plan->mu_strang && cudaMalloc(&plan->mu_strang, plan->lam_count * sizeof(float)) != cudaSuccess)
+    return fail(FRLAP_ENOMEM, "Strang symbol allocation failed");
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, strang_scratch_bytes(*plan), s) != cudaSuccess)
+    return fail(FRLAP_ENOMEM, "Strang scratch allocation failed");
+  unsigned bad = 0;
+  cudaError_t e = strang_build(*plan, scratch, s, &bad);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_strang");
+  if (n_nonpositive) *n_nonpositive = (int)bad;
+  return FRLAP_OK;
+}
+
+frlap_status frlap_precond_apply(const frlap_plan* plan, int precond, const float* d_r, float* d_z, void* d_work,
+                                 void* stream) {
+  if (!plan || !d_r || !d_z) return fail(FRLAP_EINVAL, "plan, d_r or d_z is NULL");
+  if ((const void*)d_r == (void*)d_z) return fail(FRLAP_EINVAL, "d_r and d_z must not overlap");
+  const float* mu = precond == FRLAP_PRECOND_STRANG ? plan->mu_strang
+                    : precond == FRLAP_PRECOND_LEARNED ? plan->mu_learned : nullptr;
+  if (!mu) return fail(FRLAP_EINVAL, "preconditioner not available on this plan");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  cudaError_t e = apply_launch<float>(*plan, d_r, d_z, d_work, (cudaStream_t)stream, nullptr, nullptr, mu);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_apply");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void* stream) {
+  if (!plan || !d_m) return fail(FRLAP_EINVAL, "plan or d_m is NULL");
+  if (!plan->mu_learned && cudaMalloc(&plan->mu_learned, plan->lam_count * sizeof(float)) != cudaSuccess)
+    return fail(FRLAP_ENOMEM, "multiplier allocation failed");
+  double scale = 1.0;
+  for (int r = 0; r < plan->d; ++r) scale /= (double)plan->P[r];
+  cudaError_t e = scale_to_f32_launch(d_m, plan->mu_learned, plan->lam_count, scale, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_set_symbol");
+  return FRLAP_OK;
 }
 
 frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double tau, double eps, int nsteps,

@@ -245,7 +245,7 @@ size_t apply_work_bytes(const Plan& p, int real_bytes) {
 
 template <typename T>
 cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
-                         cudaEvent_t const* ev) {
+                         cudaEvent_t const* ev, const T* lam_override) {
   int stage = 0;
   auto mark = [&]() -> cudaError_t {
     if (ev && ev[stage]) {
@@ -265,6 +265,7 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
   }
   const T* lam;
   if constexpr (sizeof(T) == 8) lam = p.lam64; else lam = p.lam32;
+  if (lam_override) lam = lam_override;
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -362,8 +363,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
 }
 
 template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
-                                          cudaEvent_t const*);
+                                          cudaEvent_t const*, const double*);
 template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
-                                         cudaEvent_t const*);
+                                         cudaEvent_t const*, const float*);
 
 }  // namespace frlap

@@ -345,6 +345,13 @@ cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam, cudaSt
                                                              p.d == 3 ? p.n[2] : 1, Hx1, Hy1, Hz1, p.c, lam);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return symbol_axes_launch(p, lam, s);
+}
+
+cudaError_t symbol_axes_launch(const Plan& p, double* lam, cudaStream_t s) {
+  const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1, Hz1 = (p.d == 3) ? p.P[2] / 2 + 1 : 1;
+  const size_t total = (size_t)Hx1 * Hy1 * Hz1;
+  cudaError_t e;
   const int H1[3] = {Hx1, Hy1, Hz1};
   for (int r = 0; r < p.d; ++r) {
     const int P = p.P[r];

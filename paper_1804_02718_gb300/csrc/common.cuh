@@ -84,12 +84,15 @@ struct Plan {
   // workspace layout of one apply, in complex elements of the apply precision
   size_t s1_elems = 0, s2_elems = 0;
   cudaStream_t side = nullptr;  // internal stream for captured solver graphs
+  // preconditioner symbols (octant layout of lam, FP32; nullptr until built)
+  float* mu_strang = nullptr;   // inverse of the multilevel Strang circulant, embedded like A
+  float* mu_learned = nullptr;  // learned Fourier multiplier
 };
 
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
 template <typename T>
 cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
-                         cudaEvent_t const* ev = nullptr);
+                         cudaEvent_t const* ev = nullptr, const T* lam_override = nullptr);
 size_t apply_work_bytes(const Plan& p, int real_bytes);
 
 // coefficient / symbol generation (coeffs.cu)
@@ -99,6 +102,8 @@ size_t coeffs_scratch_bytes(int d, int Nmax);
 cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
 cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s);
 cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st);
+// even DFT of the octant along every axis (used for both the operator and preconditioner symbols)
+cudaError_t symbol_axes_launch(const Plan& p, double* lam_oct, cudaStream_t s);
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 

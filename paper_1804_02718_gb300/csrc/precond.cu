@@ -1,0 +1,164 @@
+// Preconditioner symbols for the PCG solves.
+//
+// Strang circulant.  The multilevel Strang circulant S of A keeps, along every
+// axis, the Toeplitz entry of offset min(j, n_r - j) in its first column.  Its
+// eigenvalues are the size-n_r DFTs of that column (real, as the column is even),
+// and S^-1 is again a multilevel circulant: its first column g is the inverse DFT
+// of 1/lambda_S.  Read as a Toeplitz matrix (entry g[(i - j) mod n] at offset i - j),
+// S^-1 is applied exactly like A: g is embedded in the same P_r-point circulant
+// and its octant symbol is stored, so a preconditioner solve costs one FP32
+// apply and needs no FFT of the (generally odd) length n_r.  The size-n_r DFTs
+// of the set-up are direct O(n_r) sums per output in FP64.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace frlap {
+
+namespace {
+
+// first column of the Strang circulant: s[j] = -c a[min(j_r, n_r - j_r)], j in [0, n)^d, x fastest
+__global__ void k_strang_col(const double* __restrict__ coef, int Nmax, int d, int nx, int ny, int nz, double c,
+                             double* s) {
+  const size_t total = (size_t)nx * ny * nz;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int jx = (int)(e % nx), jy = (int)((e / nx) % ny), jz = (int)(e / ((size_t)nx * ny));
+  const int kx = min(jx, nx - jx), ky = min(jy, ny - jy), kz = min(jz, nz - jz);
+  const size_t N1 = (size_t)Nmax + 1;
+  const size_t ci = (d == 2) ? (size_t)ky * N1 + kx : ((size_t)kz * N1 + ky) * N1 + kx;
+  s[e] = -c * coef[ci];
+}
+
+// out[j] = scale * sum_{k < n} in[k] cos(2 pi j k / n) along one axis, in place, one line per CTA
+__global__ void k_even_dft(double* data, int n, size_t stride, size_t inner, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* line = reinterpret_cast<double*>(smem_raw);
+  double* ctab = line + n;
+  const size_t li = blockIdx.x;
+  const size_t base = (li / inner) * inner * (size_t)n + (li % inner);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    line[k] = data[base + (size_t)k * stride];
+    ctab[k] = cospi(2.0 * k / n);
+  }
+  __syncthreads();
+  double outv[8];
+  int cnt = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double acc = 0.0;
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+      acc = fma(line[k], ctab[m], acc);
+      m += j;
+      if (m >= n) m -= n;
+    }
+    if (cnt < 8) outv[cnt] = acc * scale;
+    ++cnt;
+  }
+  __syncthreads();
+  cnt = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (cnt < 8) data[base + (size_t)j * stride] = outv[cnt];
+    ++cnt;
+  }
+}
+
+// v <- 1 / v ; counts entries that are not positive (their modes are dropped: inverse set to 0)
+__global__ void k_invert(double* v, size_t n, unsigned* bad) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double x = v[i];
+    if (!(x > 0.0) || !isfinite(x)) {
+      atomicAdd(bad, 1u);
+      v[i] = 0.0;
+    } else {
+      v[i] = 1.0 / x;
+    }
+  }
+}
+
+// octant fill: oct[k] = g[k] for k_r <= n_r - 1 (inside the octant), 0 elsewhere
+__global__ void k_oct_from_grid(const double* __restrict__ g, int nx, int ny, int nz, int Hx1, int Hy1, int Hz1,
+                                double* oct) {
+  const size_t total = (size_t)Hx1 * Hy1 * Hz1;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int kx = (int)(e % Hx1), ky = (int)((e / Hx1) % Hy1), kz = (int)(e / ((size_t)Hx1 * Hy1));
+  double v = 0.0;
+  if (kx < nx && ky < ny && kz < nz) v = g[((size_t)kz * ny + ky) * nx + kx];
+  oct[e] = v;
+}
+
+__global__ void k_scale_to_f32(const double* __restrict__ src, float* dst, size_t n, double s) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)(src[i] * s);
+}
+
+}  // namespace
+
+cudaError_t scale_to_f32_launch(const double* src, float* dst, size_t n, double s, cudaStream_t st) {
+  k_scale_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n, s);
+  return cudaGetLastError();
+}
+
+size_t strang_scratch_bytes(const Plan& p) {
+  const size_t N1 = (size_t)p.Nmax + 1;
+  const size_t ncoef = (p.d == 2) ? N1 * N1 : N1 * N1 * N1;
+  return align256(ncoef * 8) + align256(coeffs_scratch_bytes(p.d, p.Nmax)) + align256(p.M * 8) +
+         align256(p.lam_count * 8) + 256;
+}
+
+// Builds plan->mu_strang (FP32 octant, 1/prod(P) folded in).  Returns the number of
+// non-positive Strang eigenvalues through *bad_host (0 for this operator: A is strictly
+// diagonally dominant, and so is its Strang circulant).
+cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host) {
+  unsigned char* w = reinterpret_cast<unsigned char*>(scratch);
+  const size_t N1 = (size_t)p.Nmax + 1;
+  const size_t ncoef = (p.d == 2) ? N1 * N1 : N1 * N1 * N1;
+  double* coef = reinterpret_cast<double*>(w);
+  w += align256(ncoef * 8);
+  void* cscratch = w;
+  w += align256(coeffs_scratch_bytes(p.d, p.Nmax));
+  double* grid = reinterpret_cast<double*>(w);
+  w += align256(p.M * 8);
+  double* oct = reinterpret_cast<double*>(w);
+  w += align256(p.lam_count * 8);
+  unsigned* bad = reinterpret_cast<unsigned*>(w);
+  cudaError_t e = coeffs_launch(p.d, p.alpha, p.gamma, p.h, p.Nmax, coef, cscratch, s);
+  if (e != cudaSuccess) return e;
+  const int nx = p.n[0], ny = p.n[1], nz = (p.d == 3) ? p.n[2] : 1;
+  k_strang_col<<<(unsigned)((p.M + 255) / 256), 256, 0, s>>>(coef, p.Nmax, p.d, nx, ny, nz, p.c, grid);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nn[3] = {nx, ny, nz};
+  // forward: lambda_S = DFT_n of the column; then 1/lambda_S; then g = inverse DFT (scale 1/n per axis)
+  for (int pass = 0; pass < 2; ++pass) {
+    size_t stride = 1;
+    for (int r = 0; r < p.d; ++r) {
+      const int n = nn[r];
+      const size_t nlines = p.M / n;
+      const size_t sm = 2 * (size_t)n * sizeof(double);
+      e = cudaFuncSetAttribute(k_even_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      const int threads = n <= 256 ? 256 : 512;
+      const double scale = pass == 0 ? 1.0 : 1.0 / n;
+      k_even_dft<<<(unsigned)nlines, threads, sm, s>>>(grid, n, stride, stride, scale);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      stride *= n;
+    }
+    if (pass == 0) {
+      if ((e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+      k_invert<<<2 * 152, 256, 0, s>>>(grid, p.M, bad);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1, Hz1 = (p.d == 3) ? p.P[2] / 2 + 1 : 1;
+  k_oct_from_grid<<<(unsigned)((p.lam_count + 255) / 256), 256, 0, s>>>(grid, nx, ny, nz, Hx1, Hy1, Hz1, oct);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = symbol_axes_launch(p, oct, s)) != cudaSuccess) return e;
+  double scale = 1.0;
+  for (int r = 0; r < p.d; ++r) scale /= (double)p.P[r];
+  if ((e = scale_symbol_launch(oct, p.mu_strang, p.lam_count, scale, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace frlap

@@ -25,6 +25,7 @@ constexpr int kThreads = 512;
 
 struct CgState {
   double rr;        // r . r
+  double rz;        // r . z (z = M^-1 r; equals rr without a preconditioner)
   double pq;        // p . B p
   double alpha, beta;
   double tol2;      // (rtol ||f||)^2
@@ -49,71 +50,60 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// The last block to arrive sums the partials in block order; returns true in that block's thread 0.
-__device__ __forceinline__ bool last_block_total(double part, double* partials, unsigned* counter, double* total,
-                                                 double* red) {
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = part;
-    __threadfence();
-    const unsigned t = atomicAdd(counter, 1u);
-    is_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += *((volatile double*)&partials[i]);
-  // the loop above is strided by thread; reduce in a fixed order
-  const double s = block_sum(v, red);
-  if (threadIdx.x == 0) {
-    *total = s;
-    *counter = 0u;
-  }
-  return threadIdx.x == 0;
-}
-
-template <typename T>
-__device__ __forceinline__ bool finite_(T v) { return isfinite((double)v); }
-
-// r = f - (sigma x + s q) (q = A x), p = r, rr = r.r, fnorm2 = f.f; sets tol2, done
-template <typename T>
-__global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, const T* __restrict__ q, T* r, T* p,
-                          size_t n, double* partials, CgState* S, double rtol, int use_x) {
+// Two block sums, then the last block to arrive reduces all partials in block order.
+// Returns true in thread 0 of the last block, with the totals in *ta, *tb.
+__device__ __forceinline__ bool grid_sum2(double a, double b, double* partials, unsigned* counter, double* ta,
+                                          double* tb) {
   __shared__ double red[32];
-  double a = 0.0, b = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double fi = (double)f[i];
-    double ri = fi;
-    if (use_x) ri = fi - (S->sigma * (double)x[i] + S->s * (double)q[i]);
-    const T rt = (T)ri;
-    r[i] = rt;
-    p[i] = rt;
-    a += (double)rt * (double)rt;
-    b += fi * fi;
-  }
+  __shared__ bool is_last;
   const double sa = block_sum(a, red);
   __syncthreads();
   const double sb = block_sum(b, red);
-  __shared__ bool is_last;
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = sa;
     partials[gridDim.x + blockIdx.x] = sb;
     __threadfence();
-    is_last = atomicAdd(&S->counter, 1u) == gridDim.x - 1;
+    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!is_last) return;
+  if (!is_last) return false;
   double va = 0.0, vb = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
     va += *((volatile double*)&partials[i]);
     vb += *((volatile double*)&partials[gridDim.x + i]);
   }
   __syncthreads();
-  const double ta = block_sum(va, red);
+  const double xa = block_sum(va, red);
   __syncthreads();
-  const double tb = block_sum(vb, red);
+  const double xb = block_sum(vb, red);
   if (threadIdx.x == 0) {
-    S->counter = 0u;
+    *ta = xa;
+    *tb = xb;
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+#define GRID_STRIDE(i, n) \
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+// r = f - (sigma x + s q) (q = A x when use_x); rr = r.r, fnorm2 = f.f; sets tol2, done
+template <typename T>
+__global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, const T* __restrict__ q, T* r, size_t n,
+                          double* partials, CgState* S, double rtol, int use_x) {
+  double a = 0.0, b = 0.0;
+  const double sg = S->sigma, sc = S->s;
+  GRID_STRIDE(i, n) {
+    const double fi = (double)f[i];
+    double ri = fi;
+    if (use_x) ri = fi - (sg * (double)x[i] + sc * (double)q[i]);
+    const T rt = (T)ri;
+    r[i] = rt;
+    a += (double)rt * (double)rt;
+    b += fi * fi;
+  }
+  double ta, tb;
+  if (grid_sum2(a, b, partials, &S->counter, &ta, &tb)) {
     S->rr = ta;
     S->fnorm2 = tb;
     S->tol2 = rtol * rtol * tb;
@@ -129,56 +119,77 @@ __global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, cons
   }
 }
 
-// q <- sigma p + s q ; pq = p . q ; alpha = rr / pq (breakdown if pq <= 0)
+// z (from the preconditioner output zp, or r itself), p = z, rz = r.z
+template <typename T, typename TP>
+__global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, T* z, T* p, size_t n,
+                            double* partials, CgState* S) {
+  double a = 0.0;
+  GRID_STRIDE(i, n) {
+    const T zi = zp ? (T)zp[i] : r[i];
+    if (zp) z[i] = zi;
+    p[i] = zi;
+    a += (double)r[i] * (double)zi;
+  }
+  double ta, tb;
+  if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
+    S->rz = ta;
+    if (zp && !(ta > 0.0) && !S->done) {
+      S->status = isfinite(ta) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
+      S->done = 1;
+    }
+  }
+}
+
+// q <- sigma p + s q ; pq = p . q ; alpha = rz / pq (breakdown if pq <= 0)
 template <typename T>
 __global__ void k_cg_pq(const T* __restrict__ p, T* q, size_t n, double* partials, CgState* S) {
-  __shared__ double red[32];
   if (S->done) return;
   const double sg = S->sigma, sc = S->s;
   double a = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(i, n) {
     const double pi = (double)p[i];
     const T qi = (T)(sg * pi + sc * (double)q[i]);
     q[i] = qi;
     a += pi * (double)qi;
   }
-  const double sa = block_sum(a, red);
-  double tot;
-  if (last_block_total(sa, partials, &S->counter, &tot, red)) {
-    S->pq = tot;
-    if (!(tot > 0.0) || !isfinite(tot)) {
-      S->status = isfinite(tot) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
+  double ta, tb;
+  if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
+    S->pq = ta;
+    if (!(ta > 0.0) || !isfinite(ta)) {
+      S->status = isfinite(ta) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
       S->done = 1;
     } else {
-      S->alpha = S->rr / tot;
+      S->alpha = S->rz / ta;
     }
   }
 }
 
-// x += alpha p ; r -= alpha q ; rr_new = r.r ; beta = rr_new / rr ; convergence test
+// x += alpha p ; r -= alpha q ; rr = r.r ; convergence test.  Without a preconditioner also
+// beta = rr_new / rr_old (z = r).  With one, beta is formed after the preconditioner solve.
 template <typename T>
 __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __restrict__ q, size_t n,
-                            double* partials, CgState* S, int maxit) {
-  __shared__ double red[32];
+                            double* partials, CgState* S, int maxit, int precond) {
   if (S->done) return;
   const double al = S->alpha;
   double a = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(i, n) {
     x[i] = (T)((double)x[i] + al * (double)p[i]);
     const T ri = (T)((double)r[i] - al * (double)q[i]);
     r[i] = ri;
     a += (double)ri * (double)ri;
   }
-  const double sa = block_sum(a, red);
-  double tot;
-  if (last_block_total(sa, partials, &S->counter, &tot, red)) {
-    S->beta = tot / S->rr;
-    S->rr = tot;
+  double ta, tb;
+  if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
+    if (!precond) {
+      S->beta = ta / S->rz;
+      S->rz = ta;
+    }
+    S->rr = ta;
     S->iters += 1;
-    if (!isfinite(tot)) {
+    if (!isfinite(ta)) {
       S->status = FRLAP_ENAN;
       S->done = 1;
-    } else if (tot <= S->tol2) {
+    } else if (ta <= S->tol2) {
       S->done = 1;
     } else if (S->iters >= maxit) {
       S->status = FRLAP_ENOCONV;
@@ -187,13 +198,44 @@ __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __rest
   }
 }
 
-// p = r + beta p
+// after z = M^-1 r: z from the preconditioner output; rz_new = r.z, zq = z.q;
+// flexible (Polak-Ribiere) beta = z.(r_new - r_old) / rz_old = -alpha zq / rz_old
+template <typename T, typename TP>
+__global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, T* z, const T* __restrict__ q,
+                           size_t n, double* partials, CgState* S) {
+  if (S->done) return;
+  double a = 0.0, b = 0.0;
+  GRID_STRIDE(i, n) {
+    const T zi = (T)zp[i];
+    if ((const void*)zp != (const void*)z) z[i] = zi;
+    a += (double)r[i] * (double)zi;
+    b += (double)zi * (double)q[i];
+  }
+  double ta, tb;
+  if (grid_sum2(a, b, partials, &S->counter, &ta, &tb)) {
+    if (!(ta > 0.0) || !isfinite(ta)) {
+      S->status = isfinite(ta) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
+      S->done = 1;
+    } else {
+      S->beta = -S->alpha * tb / S->rz;
+      S->rz = ta;
+    }
+  }
+}
+
+// p = z + beta p
 template <typename T>
-__global__ void k_cg_dir(const T* __restrict__ r, T* p, size_t n, const CgState* S) {
+__global__ void k_cg_dir(const T* __restrict__ z, T* p, size_t n, const CgState* S) {
   if (S->done) return;
   const double b = S->beta;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = (T)((double)r[i] + b * (double)p[i]);
+  GRID_STRIDE(i, n) p[i] = (T)((double)z[i] + b * (double)p[i]);
+}
+
+// FP32 copy of r for the preconditioner solve
+template <typename T>
+__global__ void k_to32(const T* __restrict__ r, float* r32, size_t n, const CgState* S) {
+  if (S && S->done) return;
+  GRID_STRIDE(i, n) r32[i] = (float)r[i];
 }
 
 __global__ void k_set_state(CgState* S, double sigma, double s) {
@@ -205,41 +247,19 @@ __global__ void k_set_state(CgState* S, double sigma, double s) {
   S->iters = 0;
 }
 
-// true residual norms: out[0] = ||f - (sigma x + s q)||^2, out[1] = ||f||^2 (one block per slice, then last block)
+// true residual norms: out[0] = ||f - (sigma x + s q)||^2, out[1] = ||f||^2
 __global__ void k_resid(const double* __restrict__ f, const double* __restrict__ x, const double* __restrict__ q,
                         size_t n, double sigma, double s, double* partials, unsigned* counter, double* out,
                         double* rvec, double* rnorm_scale) {
-  __shared__ double red[32];
   double a = 0.0, b = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(i, n) {
     const double ri = f[i] - (sigma * x[i] + s * q[i]);
     if (rvec) rvec[i] = ri;
     a += ri * ri;
     b += f[i] * f[i];
   }
-  const double sa = block_sum(a, red);
-  __syncthreads();
-  const double sb = block_sum(b, red);
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = sa;
-    partials[gridDim.x + blockIdx.x] = sb;
-    __threadfence();
-    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  double va = 0.0, vb = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    va += *((volatile double*)&partials[i]);
-    vb += *((volatile double*)&partials[gridDim.x + i]);
-  }
-  __syncthreads();
-  const double ta = block_sum(va, red);
-  __syncthreads();
-  const double tb = block_sum(vb, red);
-  if (threadIdx.x == 0) {
-    *counter = 0u;
+  double ta, tb;
+  if (grid_sum2(a, b, partials, counter, &ta, &tb)) {
     out[0] = ta;
     out[1] = tb;
     if (rnorm_scale) *rnorm_scale = sqrt(ta);
@@ -275,48 +295,115 @@ size_t vec_bytes(const Plan& p, int eb) { return align256(p.M * (size_t)eb); }
 
 }  // namespace
 
-// workspace: [apply work][r][p][q][partials][state]   (vectors of the given precision)
+// workspace of one (P)CG solve in precision T:
+// [apply work T][apply work FP32 (precond, T = double)][r][p][q][z][r32][z32][partials][state]
 size_t cg_work_bytes(const Plan& p, int eb) {
-  return apply_work_bytes(p, eb) + 3 * vec_bytes(p, eb) + align256(2 * kBlocks * sizeof(double)) +
-         align256(sizeof(CgState));
+  size_t b = apply_work_bytes(p, eb) + 4 * vec_bytes(p, eb) + 2 * vec_bytes(p, 4) +
+             align256(2 * kBlocks * sizeof(double)) + align256(sizeof(CgState));
+  if (eb == 8) b += apply_work_bytes(p, 4);
+  return b;
 }
 
-// Runs CG on B x = f with B = sigma I + s A in precision T; x holds x0 on entry.
-// Returns the final device state through *hS (host copy).
+struct CgBufs {
+  void* awork;
+  void* awork32;
+  void* r;
+  void* p;
+  void* q;
+  void* z;
+  float* r32;
+  float* z32;
+  double* partials;
+  CgState* S;
+};
+
+static CgBufs carve(const Plan& p, void* work, int eb) {
+  CgBufs b;
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  b.awork = w;
+  w += apply_work_bytes(p, eb);
+  b.awork32 = nullptr;
+  if (eb == 8) {
+    b.awork32 = w;
+    w += apply_work_bytes(p, 4);
+  }
+  b.r = w;
+  w += vec_bytes(p, eb);
+  b.p = w;
+  w += vec_bytes(p, eb);
+  b.q = w;
+  w += vec_bytes(p, eb);
+  b.z = w;
+  w += vec_bytes(p, eb);
+  b.r32 = reinterpret_cast<float*>(w);
+  w += vec_bytes(p, 4);
+  b.z32 = reinterpret_cast<float*>(w);
+  w += vec_bytes(p, 4);
+  b.partials = reinterpret_cast<double*>(w);
+  w += align256(2 * kBlocks * sizeof(double));
+  b.S = reinterpret_cast<CgState*>(w);
+  return b;
+}
+
+// z32 = M^-1 r: one FP32 apply with the preconditioner symbol mu (skipped once done)
+template <typename T>
+static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu, cudaStream_t st) {
+  const float* src;
+  if constexpr (sizeof(T) == 8) {
+    k_to32<T><<<kBlocks, kThreads, 0, st>>>(reinterpret_cast<const T*>(b.r), b.r32, p.M, b.S);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = b.r32;
+    return apply_launch<float>(p, src, b.z32, b.awork32, st, &b.S->done, nullptr, mu);
+  } else {
+    src = reinterpret_cast<const float*>(b.r);
+    return apply_launch<float>(p, src, b.z32, b.awork, st, &b.S->done, nullptr, mu);
+  }
+}
+
+// (Flexible) PCG on B x = f, B = sigma I + s A, in precision T; x holds x0 on entry.
+// mu = FP32 preconditioner symbol (octant) or nullptr for plain CG.
 template <typename T>
 static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double s, double rtol, int maxit,
-                           int use_x0, void* work, cudaStream_t st, CgState* hS) {
-  unsigned char* w = reinterpret_cast<unsigned char*>(work);
-  void* awork = w;
-  w += apply_work_bytes(p, sizeof(T));
-  T* r = reinterpret_cast<T*>(w);
-  w += vec_bytes(p, sizeof(T));
-  T* pv = reinterpret_cast<T*>(w);
-  w += vec_bytes(p, sizeof(T));
-  T* q = reinterpret_cast<T*>(w);
-  w += vec_bytes(p, sizeof(T));
-  double* partials = reinterpret_cast<double*>(w);
-  w += align256(2 * kBlocks * sizeof(double));
-  CgState* S = reinterpret_cast<CgState*>(w);
+                           int use_x0, const float* mu, void* work, cudaStream_t st, CgState* hS) {
+  const CgBufs b = carve(p, work, sizeof(T));
+  T* r = reinterpret_cast<T*>(b.r);
+  T* pv = reinterpret_cast<T*>(b.p);
+  T* q = reinterpret_cast<T*>(b.q);
+  T* z = mu ? reinterpret_cast<T*>(b.z) : r;
+  CgState* S = b.S;
   const size_t n = p.M;
   k_set_state<<<1, 1, 0, st>>>(S, sigma, s);
   FRLAP_LAUNCH_CHECK("k_set_state");
   if (use_x0) {
-    cudaError_t e = apply_launch<T>(p, x, q, awork, st, nullptr);
+    cudaError_t e = apply_launch<T>(p, x, q, b.awork, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "apply (initial residual)");
   }
-  k_cg_init<T><<<kBlocks, kThreads, 0, st>>>(f, x, q, r, pv, n, partials, S, rtol, use_x0);
+  k_cg_init<T><<<kBlocks, kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
   FRLAP_LAUNCH_CHECK("k_cg_init");
+  if (mu) {
+    cudaError_t e = precondition<T>(p, b, mu, st);
+    if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
+    k_pcg_start<T, float><<<kBlocks, kThreads, 0, st>>>(r, b.z32, z, pv, n, b.partials, S);
+  } else {
+    k_pcg_start<T, T><<<kBlocks, kThreads, 0, st>>>(r, nullptr, z, pv, n, b.partials, S);
+  }
+  FRLAP_LAUNCH_CHECK("k_pcg_start");
   const int* done = &S->done;
   const int chunk = 8;
   int launched = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      cudaError_t e = apply_launch<T>(p, pv, q, awork, st, done);
+      cudaError_t e = apply_launch<T>(p, pv, q, b.awork, st, done);
       if (e != cudaSuccess) return cuda_fail(e, "apply (CG)");
-      k_cg_pq<T><<<kBlocks, kThreads, 0, st>>>(pv, q, n, partials, S);
-      k_cg_update<T><<<kBlocks, kThreads, 0, st>>>(x, r, pv, q, n, partials, S, maxit);
-      k_cg_dir<T><<<kBlocks, kThreads, 0, st>>>(r, pv, n, S);
+      k_cg_pq<T><<<kBlocks, kThreads, 0, st>>>(pv, q, n, b.partials, S);
+      k_cg_update<T><<<kBlocks, kThreads, 0, st>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr);
+      if (mu) {
+        e = precondition<T>(p, b, mu, st);
+        if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
+        k_pcg_beta<T, float><<<kBlocks, kThreads, 0, st>>>(r, b.z32, z, q, n, b.partials, S);
+      }
+      k_cg_dir<T><<<kBlocks, kThreads, 0, st>>>(z, pv, n, S);
       FRLAP_LAUNCH_CHECK("CG iteration kernels");
     }
     launched += chunk;
@@ -332,22 +419,15 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
 static frlap_status true_residual(const Plan& p, const double* f, const double* x, double sigma, double s,
                                   void* work, cudaStream_t st, double* relres, double* rvec,
                                   double* rnorm_dev) {
-  unsigned char* w = reinterpret_cast<unsigned char*>(work);
-  void* awork = w;
-  w += apply_work_bytes(p, 8);
-  w += vec_bytes(p, 8);  // r
-  w += vec_bytes(p, 8);  // p
-  double* q = reinterpret_cast<double*>(w);
-  w += vec_bytes(p, 8);
-  double* partials = reinterpret_cast<double*>(w);
-  w += align256(2 * kBlocks * sizeof(double));
-  CgState* S = reinterpret_cast<CgState*>(w);
+  const CgBufs b = carve(p, work, 8);
+  double* q = reinterpret_cast<double*>(b.q);
+  CgState* S = b.S;
   // the reduction ticket must start at zero (this workspace may not have run a CG yet)
   FRLAP_CUDA_TRY(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), st));
-  cudaError_t e = apply_launch<double>(p, x, q, awork, st, nullptr);
+  cudaError_t e = apply_launch<double>(p, x, q, b.awork, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
   double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
-  k_resid<<<kBlocks, kThreads, 0, st>>>(f, x, q, p.M, sigma, s, partials, &S->counter, out, rvec, rnorm_dev);
+  k_resid<<<kBlocks, kThreads, 0, st>>>(f, x, q, p.M, sigma, s, b.partials, &S->counter, out, rvec, rnorm_dev);
   FRLAP_LAUNCH_CHECK("k_resid");
   double h[2];
   FRLAP_CUDA_TRY(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -364,10 +444,11 @@ size_t ir_work_bytes(const Plan& p) {
 size_t ac_work_bytes(const Plan& p) { return cg_work_bytes(p, 8) + vec_bytes(p, 8); }
 
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
-                            double inner_rtol, int* iters, double* relres, void* work, cudaStream_t st) {
+                            const float* mu, double inner_rtol, int* iters, double* relres, void* work,
+                            cudaStream_t st) {
   CgState hS;
   if (solver == FRLAP_SOLVE_CG) {
-    frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, maxit, 1, work, st, &hS);
+    frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, maxit, 1, mu, work, st, &hS);
     if (rc != FRLAP_OK) return rc;
     double rel = 0.0;
     rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
@@ -400,7 +481,7 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
     if (rel <= rtol || outer == max_outer || total >= maxit) break;
     k_to_f32<<<kBlocks, kThreads, 0, st>>>(r64, rnorm, r32, d32, p.M);
     FRLAP_LAUNCH_CHECK("k_to_f32");
-    rc = run_cg<float>(p, r32, d32, 0.0, 1.0, inner_rtol, maxit - total, 0, work32, st, &hS);
+    rc = run_cg<float>(p, r32, d32, 0.0, 1.0, inner_rtol, maxit - total, 0, mu, work32, st, &hS);
     if (rc != FRLAP_OK) return rc;
     total += hS.iters;
     if (hS.status == FRLAP_ENAN) return fail(FRLAP_ENAN, "non-finite value in the FP32 inner solve");
@@ -424,7 +505,7 @@ frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, i
   for (int step = 0; step < nsteps; ++step) {
     k_ac_rhs<<<kBlocks, kThreads, 0, st>>>(u, rhs, p.M, tau);
     FRLAP_LAUNCH_CHECK("k_ac_rhs");
-    frlap_status rc = run_cg<double>(p, rhs, u, 1.0, tau * eps * eps, rtol, 100000, 1, cgw, st, &hS);
+    frlap_status rc = run_cg<double>(p, rhs, u, 1.0, tau * eps * eps, rtol, 100000, 1, nullptr, cgw, st, &hS);
     if (rc != FRLAP_OK) return rc;
     total += hS.iters;
     if (hS.status != FRLAP_OK) {
