@@ -202,6 +202,43 @@ frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void*
 frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double tau, double eps, int nsteps,
                                    double rtol, int* iters, void* d_work, void* stream);
 
+/* ---- learned preconditioner (spec extension; the paper has no learned part) ----
+ * A per-frequency MLP on the symbol octant: features (alpha, kappa_x, kappa_y,
+ * kappa_z), kappa_r = k_r / (P_r/2) (kappa_z = 0 in 2D), two tanh layers of
+ * FRLAP_MLP_HIDDEN units, scalar output s; multiplier m(k) = exp(s(k)) / lambda(k)
+ * with lambda the symbol of A's embedding (a zero network gives m = 1/lambda).
+ * Parameters: FRLAP_MLP_NPARAM floats, in order W1[64][4], b1[64], W2[64][64]
+ * (out, in), b2[64], w3[64], b3[1]. */
+#define FRLAP_MLP_HIDDEN 64
+#define FRLAP_MLP_NFEAT 4
+#define FRLAP_MLP_NPARAM 4545
+
+/* m on the plan's octant (prod_r (P_r/2+1) doubles, x fastest); pass it to
+ * frlap_precond_set_symbol to use it in frlap_pcg_solve. */
+frlap_status frlap_mlp_multiplier(const frlap_plan* plan, const float* d_params, double* d_m, void* stream);
+
+/* Scratch for frlap_learn_grad with a batch of B pairs. */
+size_t frlap_learn_workspace_bytes(const frlap_plan* plan, int B);
+
+/* Loss L = mean_b ||M^-1 r_b - e_b||^2 / ||e_b||^2 over B pairs (d_r, d_e: B
+ * consecutive grid vectors of doubles, e_b = A^-1 r_b) and its gradient with
+ * respect to the parameters: d_grad (FRLAP_MLP_NPARAM floats, overwritten),
+ * d_loss (one double on the device).  FP64 spectra, FP32 network. */
+frlap_status frlap_learn_grad(const frlap_plan* plan, const float* d_params, const double* d_r, const double* d_e,
+                              int B, float* d_grad, double* d_loss, void* d_work, void* stream);
+
+/* One Adam step (step counter t >= 1) on n parameters, in place. */
+frlap_status frlap_adam_step(float* d_params, const float* d_grad, float* d_m1, float* d_m2, int n, float lr,
+                             float beta1, float beta2, float eps, int t, void* stream);
+
+/* Training pairs from the plain FP64 CG solver: run CG on A x = f from x0 = 0 to
+ * rtol and snapshot the iterates x_0 = 0, x_1, ...; on return d_E[j] = x* - x_j
+ * and d_R[j] = A d_E[j] (= f - A x_j), j < *npairs = min(iterations, K): the
+ * final iterate (zero error) is left out.  Each pair is prod(n_r) doubles.
+ * d_work: frlap_workspace_bytes(plan, FRLAP_OP_PCG).  Synchronises stream. */
+frlap_status frlap_cg_pairs(const frlap_plan* plan, const double* d_f, int K, double rtol, double* d_E, double* d_R,
+                            int* npairs, void* d_work, void* stream);
+
 /* The message for the last error on the calling thread ("" if none). */
 const char* frlap_last_error(void);
 

@@ -13,8 +13,15 @@ maps the features phi(k) = (alpha, kappa_x, kappa_y, kappa_z), kappa_r = k_r/(P_
 multiplier is m(k) = exp(s(k)) / lambda(k), with lambda the real symbol of A's
 circulant embedding, so a zero network gives the inverse-embedding preconditioner.
 M^-1 r = R F^-1 (m . F R^T r) (R: restriction to the interior grid, F: the
-P-point DFT).  Training loss over pairs (r_b, e_b = A^-1 r_b):
-L = mean_b ||M^-1 r_b - e_b||^2 / ||e_b||^2.
+P-point DFT).  Training pairs (r_b, e_b = A^-1 r_b) come from the plain CG
+solver.  Because PCG is unchanged when M is scaled, the loss measures the error of
+the best multiple of z_b = M^-1 r_b in the A-norm:
+  L_b = min_c ||e_b - c z_b||_A^2 / ||e_b||_A^2 = 1 - a_b^2 / (b_b c_b),
+  a_b = r_b . z_b,  b_b = z_b . A z_b,  c_b = r_b . e_b (= ||e_b||_A^2),
+and L = mean_b L_b (the error reduction of one preconditioned steepest-descent step).
+With R^ = F R^T r, W^ = F R^T (A z) and prod(P) the DFT size,
+  d a_b / d m(k) = |R^(k)|^2 / prod(P),   d b_b / d m(k) = 2 Re(conj(W^(k)) R^(k)) / prod(P),
+summed over the mirror images of each octant entry.
 """
 from __future__ import annotations
 
@@ -117,11 +124,12 @@ def precond_apply(m_oct, P, r):
     return z[tuple(slice(0, n) for n in r.shape)].copy()
 
 
-def loss_and_grad(theta, alpha, lam_oct, P, rs, es):
-    """Loss over the batch and its gradient with respect to theta (FP64)."""
+def loss_and_grad(theta, alpha, lam_oct, P, rs, es, apply_A):
+    """Loss over the batch and its gradient with respect to theta (FP64); apply_A(v) = A v."""
     m, s, cache = multiplier(theta, alpha, lam_oct, P)
     Pa = tuple(reversed(P))
     axes = tuple(range(rs[0].ndim))
+    PP = float(np.prod(Pa))
     mfull = _full(m, P)
     B = len(rs)
     L = 0.0
@@ -129,11 +137,13 @@ def loss_and_grad(theta, alpha, lam_oct, P, rs, es):
     for r, e in zip(rs, es):
         R = np.fft.fftn(r, s=Pa, axes=axes)
         z = np.fft.ifftn(mfull * R, axes=axes).real[tuple(slice(0, n) for n in r.shape)]
-        D = z - e
-        w = 1.0 / (B * float(np.sum(e * e)))
-        L += w * float(np.sum(D * D))
-        Dh = np.fft.fftn(D, s=Pa, axes=axes)
-        gfull += 2.0 * w * np.real(np.conj(Dh) * R) / float(np.prod(Pa))
+        w = apply_A(z)
+        a, b, c = float(np.sum(r * z)), float(np.sum(z * w)), float(np.sum(r * e))
+        L += (1.0 - a * a / (b * c)) / B
+        W = np.fft.fftn(w, s=Pa, axes=axes)
+        da = np.abs(R) ** 2 / PP
+        db = 2.0 * np.real(np.conj(W) * R) / PP
+        gfull += (-(2.0 * a / (b * c)) * da + (a * a / (b * b * c)) * db) / B
     g_m = _fold(gfull, P)
     g_s = (g_m * m).reshape(-1)
     return L, mlp_backward(theta, cache, g_s)

@@ -46,6 +46,11 @@ _SIGS = {
     "frlap_precond_strang": (_I, [_P, ctypes.POINTER(_I), _P]),
     "frlap_precond_set_symbol": (_I, [_P, _P, _P]),
     "frlap_precond_apply": (_I, [_P, _I, _P, _P, _P, _P]),
+    "frlap_mlp_multiplier": (_I, [_P, _P, _P, _P]),
+    "frlap_learn_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
+    "frlap_learn_grad": (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _P]),
+    "frlap_adam_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I, _P]),
+    "frlap_cg_pairs": (_I, [_P, _P, _I, _D, _P, _P, ctypes.POINTER(_I), _P, _P]),
     "frlap_allen_cahn_step": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), _P, _P]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
@@ -286,6 +291,55 @@ def frlap_precond_set_symbol(plan: Plan, m: torch.Tensor, stream=None):
     """Install a multiplier octant (float64, shape of plan.symbol()) as the LEARNED preconditioner."""
     _check(lib().frlap_precond_set_symbol(plan.handle, _dev(m, torch.float64, "m"), _stream(stream)),
            "frlap_precond_set_symbol")
+
+
+MLP_NPARAM = 4545
+
+
+def _f32(t, name):
+    return _dev(t, torch.float32, name)
+
+
+def frlap_mlp_multiplier(plan: Plan, params: torch.Tensor, stream=None) -> torch.Tensor:
+    """m = exp(net(alpha, kappa)) / lambda on the plan's octant (float64, shape of plan.symbol())."""
+    shape = tuple(p // 2 + 1 for p in reversed(plan.P))
+    m = torch.empty(shape, dtype=torch.float64, device="cuda")
+    _check(lib().frlap_mlp_multiplier(plan.handle, _f32(params, "params"), _dev(m, torch.float64, "m"),
+                                      _stream(stream)), "frlap_mlp_multiplier")
+    return m
+
+
+def frlap_learn_workspace_bytes(plan: Plan, B: int) -> int:
+    return int(lib().frlap_learn_workspace_bytes(plan.handle, int(B)))
+
+
+def frlap_learn_grad(plan: Plan, params: torch.Tensor, r: torch.Tensor, e: torch.Tensor, grad: torch.Tensor,
+                     loss: torch.Tensor, work: torch.Tensor, stream=None):
+    """Preconditioner loss (into loss, one float64) and its parameter gradient (into grad) over len(r) pairs."""
+    B = r.shape[0]
+    _check(lib().frlap_learn_grad(plan.handle, _f32(params, "params"), _dev(r, torch.float64, "r"),
+                                  _dev(e, torch.float64, "e"), int(B), _f32(grad, "grad"),
+                                  _dev(loss, torch.float64, "loss"), ctypes.c_void_p(work.data_ptr()),
+                                  _stream(stream)), "frlap_learn_grad")
+
+
+def frlap_adam_step(params, grad, m1, m2, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().frlap_adam_step(_f32(params, "params"), _f32(grad, "grad"), _f32(m1, "m1"), _f32(m2, "m2"),
+                                 int(params.numel()), lr, beta1, beta2, eps, int(t), _stream(stream)),
+           "frlap_adam_step")
+
+
+def frlap_cg_pairs(plan: Plan, f: torch.Tensor, K: int, rtol: float = 1e-10, work=None, stream=None):
+    """(E, R, npairs): e_j = x* - x_j and r_j = A e_j from the plain CG iterates x_0 = 0, x_1, ..."""
+    E = torch.empty((K,) + tuple(plan.shape), dtype=torch.float64, device="cuda")
+    R = torch.empty_like(E)
+    if work is None:
+        work = plan.workspace(FRLAP_OP_PCG)
+    npairs = ctypes.c_int(0)
+    _check(lib().frlap_cg_pairs(plan.handle, _dev(f, torch.float64, "f"), int(K), rtol,
+                                _dev(E, torch.float64, "E"), _dev(R, torch.float64, "R"), ctypes.byref(npairs),
+                                ctypes.c_void_p(work.data_ptr()), _stream(stream)), "frlap_cg_pairs")
+    return E, R, npairs.value
 
 
 def frlap_allen_cahn_step(plan: Plan, u: torch.Tensor, tau: float, eps: float, nsteps: int = 1,

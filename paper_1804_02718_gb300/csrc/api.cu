@@ -31,6 +31,14 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
                             const float* mu, double inner_rtol, int* iters, double* relres, void* work,
                             cudaStream_t st);
 size_t strang_scratch_bytes(const Plan& p);
+size_t learn_work_bytes(const Plan& p, int B);
+cudaError_t mlp_multiplier_launch(const Plan& p, const float* params, double* m, cudaStream_t s);
+cudaError_t learn_grad_launch(const Plan& p, const float* params, const double* r, const double* e, int B,
+                              float* grad, double* loss, void* work, cudaStream_t s);
+cudaError_t adam_launch(float* p, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
+                        int t, cudaStream_t s);
+frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, double* E, double* R, int* npairs,
+                           void* work, cudaStream_t st);
 cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host);
 cudaError_t scale_to_f32_launch(const double* src, float* dst, size_t n, double s, cudaStream_t st);
 frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, int nsteps, double rtol,
@@ -338,6 +346,47 @@ frlap_status frlap_precond_apply(const frlap_plan* plan, int precond, const floa
   cudaError_t e = apply_launch<float>(*plan, d_r, d_z, d_work, (cudaStream_t)stream, nullptr, nullptr, mu);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_apply");
   return FRLAP_OK;
+}
+
+frlap_status frlap_mlp_multiplier(const frlap_plan* plan, const float* d_params, double* d_m, void* stream) {
+  if (!plan || !d_params || !d_m) return fail(FRLAP_EINVAL, "plan, d_params or d_m is NULL");
+  cudaError_t e = mlp_multiplier_launch(*plan, d_params, d_m, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_mlp_multiplier");
+  return FRLAP_OK;
+}
+
+size_t frlap_learn_workspace_bytes(const frlap_plan* plan, int B) {
+  if (!plan || B < 1) return 0;
+  return learn_work_bytes(*plan, B);
+}
+
+frlap_status frlap_learn_grad(const frlap_plan* plan, const float* d_params, const double* d_r, const double* d_e,
+                              int B, float* d_grad, double* d_loss, void* d_work, void* stream) {
+  if (!plan || !d_params || !d_r || !d_e || !d_grad || !d_loss) return fail(FRLAP_EINVAL, "NULL argument");
+  if (B < 1) return fail(FRLAP_EINVAL, "B must be >= 1");
+  if (plan->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "training needs an F64 or MIXED plan (FP64 spectra)");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  cudaError_t e = learn_grad_launch(*plan, d_params, d_r, d_e, B, d_grad, d_loss, d_work, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_learn_grad");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_adam_step(float* d_params, const float* d_grad, float* d_m1, float* d_m2, int n, float lr,
+                             float beta1, float beta2, float eps, int t, void* stream) {
+  if (!d_params || !d_grad || !d_m1 || !d_m2 || n < 1 || t < 1) return fail(FRLAP_EINVAL, "bad Adam arguments");
+  cudaError_t e = adam_launch(d_params, d_grad, d_m1, d_m2, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_adam_step");
+  return FRLAP_OK;
+}
+
+frlap_status frlap_cg_pairs(const frlap_plan* plan, const double* d_f, int K, double rtol, double* d_E, double* d_R,
+                            int* npairs, void* d_work, void* stream) {
+  if (!plan || !d_f || !d_E || !d_R || K < 1 || !(rtol > 0.0)) return fail(FRLAP_EINVAL, "bad arguments");
+  if (plan->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "training pairs need an F64 or MIXED plan");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  return cg_pairs_impl(*plan, d_f, K, rtol, d_E, d_R, npairs, d_work, (cudaStream_t)stream);
 }
 
 frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void* stream) {

@@ -218,6 +218,68 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   }
 }
 
+
+// lines of length n (stride ld) -> zero-pad to P, forward FFT, write all P outputs (stride ldo)
+template <typename T>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
+    k_col_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int ncols, int n, size_t ld, size_t ldo,
+              int logP, int TL, const cplx<T>* __restrict__ tw, int logPtab) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  const int P = 1 << logP, G = P >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int col = blockIdx.x * TL + l;
+  const bool valid = col < ncols;
+  C* buf = smem + (size_t)l * sline(P);
+  const C* src = in + (size_t)(valid ? col : 0) * ld;
+  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : mk<C>(0, 0);
+  __syncthreads();
+  fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+  if (valid) {
+    C* dst = out + (size_t)col * ldo;
+    for (int i = lane; i < P; i += G) dst[i] = buf[spad(i)];
+  }
+}
+
+// lines of P spectrum values (stride ld) -> * multiplier, inverse FFT, crop to n, write (stride ldo)
+template <typename T>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
+    k_col_mulinv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int ncols, int n, size_t ld, size_t ldo,
+                 int logP, int TL, const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw,
+                 int logPtab) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  const int P = 1 << logP, G = P >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int col = blockIdx.x * TL + l;
+  const bool valid = col < ncols;
+  C* buf = smem + (size_t)l * sline(P);
+  const C* src = in + (size_t)(valid ? col : 0) * ld;
+  size_t lam_base;
+  int lam_stride;
+  if (map.d == 2) {
+    lam_base = valid ? col : 0;
+    lam_stride = map.Hx1;
+  } else {
+    const int c = valid ? col : 0;
+    const int kx = c >> map.logPy, ky = c & (map.Py - 1);
+    lam_base = (size_t)min(ky, map.Py - ky) * map.Hx1 + kx;
+    lam_stride = map.Hy1 * map.Hx1;
+  }
+  for (int k = lane; k < P; k += G) {
+    const int kf = min(k, P - k);
+    buf[spad(k)] = valid ? lam[lam_base + (size_t)kf * lam_stride] * src[k] : mk<C>(0, 0);
+  }
+  __syncthreads();
+  fft_line<T, 1>(buf, logP, lane, tw, logPtab);
+  if (valid) {
+    C* dst = out + (size_t)col * ldo;
+    for (int i = lane; i < n; i += G) dst[i] = buf[spad(i)];
+  }
+}
+
 // Lines per CTA for a line of `len` complex slots: as many as fit in
 // `budget` bytes of shared memory and 1024 threads (at least one).
 // (every apply kernel is compiled for at most 512 threads per CTA)
@@ -366,5 +428,131 @@ template cudaError_t apply_launch<double>(const Plan&, const double*, double*, v
                                           cudaEvent_t const*, const double*);
 template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
                                          cudaEvent_t const*, const float*);
+
+size_t spectrum_elems(const Plan& p) {
+  const size_t Hx1 = p.P[0] / 2 + 1;
+  return (p.d == 2) ? Hx1 * p.P[1] : Hx1 * p.P[1] * p.P[2];
+}
+
+// SP = F R^T u on the half spectrum: 2D [kx][ky], 3D [kx][ky][kz] (kx <= P_x/2, full ky, kz).
+template <typename T>
+cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work, cudaStream_t s) {
+  using C = cplx<T>;
+  const int eb = sizeof(C);
+  const int budget = 96 * 1024;
+  const C* tw[3];
+  for (int r = 0; r < 3; ++r) {
+    if constexpr (sizeof(T) == 8) tw[r] = reinterpret_cast<const C*>(p.tw64[r]);
+    else tw[r] = reinterpret_cast<const C*>(p.tw32[r]);
+  }
+  C* S1 = reinterpret_cast<C*>(work);
+  C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
+  const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const int Hx = p.P[0] / 2;
+  const int nrows = ny * (p.d == 3 ? nz : 1);
+  cudaError_t e;
+  {
+    const int G = Hx >> 4;
+    const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    if ((e = set_smem(k_r2c_T<T>, sm)) != cudaSuccess) return e;
+    k_r2c_T<T><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(u, S1, nrows, nx, nx, (size_t)nrows, p.logP[0] - 1, tl,
+                                                          tw[0], p.logP[0], nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const C* lines = S1;
+  int ncols = Hx + 1, n = ny, logP = p.logP[1];
+  size_t ld = (size_t)nrows;
+  const C* twl = tw[1];
+  if (p.d == 3) {
+    const int Py = p.P[1];
+    const int G = Py >> 4;
+    const int tl = pick_tl(sline(Py), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(Py) * eb;
+    if ((e = set_smem(k_c2cT_fwd<T>, sm)) != cudaSuccess) return e;
+    const int tiles = (nz + tl - 1) / tl;
+    k_c2cT_fwd<T><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz,
+                                                        nz, p.logP[1], tl, tw[1], p.logP[1], nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    lines = S2;
+    ncols = (Hx + 1) * Py;
+    n = nz;
+    ld = (size_t)nz;
+    logP = p.logP[2];
+    twl = tw[2];
+  }
+  const int P = 1 << logP;
+  const int G = P >> 4;
+  const int tl = pick_tl(sline(P), eb, G, budget, 64);
+  const size_t sm = (size_t)tl * sline(P) * eb;
+  if ((e = set_smem(k_col_fwd<T>, sm)) != cudaSuccess) return e;
+  k_col_fwd<T><<<(ncols + tl - 1) / tl, tl * G, sm, s>>>(lines, SP, ncols, n, ld, (size_t)P, logP, tl, twl, logP);
+  return cudaGetLastError();
+}
+
+// y = R F^-1 (mult * SP), mult = a symbol octant with the 1/prod(P) factor folded in.
+template <typename T>
+cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T* y, void* work, cudaStream_t s) {
+  using C = cplx<T>;
+  const int eb = sizeof(C);
+  const int budget = 96 * 1024;
+  const C* tw[3];
+  for (int r = 0; r < 3; ++r) {
+    if constexpr (sizeof(T) == 8) tw[r] = reinterpret_cast<const C*>(p.tw64[r]);
+    else tw[r] = reinterpret_cast<const C*>(p.tw32[r]);
+  }
+  C* S1 = reinterpret_cast<C*>(work);
+  C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
+  const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const int Hx = p.P[0] / 2;
+  const int nrows = ny * (p.d == 3 ? nz : 1);
+  LamMap map;
+  map.d = p.d;
+  map.Hx1 = Hx + 1;
+  map.logPy = p.logP[1];
+  map.Py = p.P[1];
+  map.Hy1 = p.P[1] / 2 + 1;
+  cudaError_t e;
+  {
+    const int logP = p.d == 2 ? p.logP[1] : p.logP[2];
+    const int P = 1 << logP;
+    const int G = P >> 4;
+    const int tl = pick_tl(sline(P), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(P) * eb;
+    if ((e = set_smem(k_col_mulinv<T>, sm)) != cudaSuccess) return e;
+    const int ncols = p.d == 2 ? Hx + 1 : (Hx + 1) * p.P[1];
+    const int n = p.d == 2 ? ny : nz;
+    C* dst = p.d == 2 ? S1 : S2;
+    const size_t ldo = p.d == 2 ? (size_t)nrows : (size_t)nz;
+    k_col_mulinv<T><<<(ncols + tl - 1) / tl, tl * G, sm, s>>>(SP, dst, ncols, n, (size_t)P, ldo, logP, tl, mult, map,
+                                                               p.d == 2 ? tw[1] : tw[2], logP);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (p.d == 3) {
+    const int Py = p.P[1];
+    const int G = Py >> 4;
+    const int tl = pick_tl(sline(Py), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(Py) * eb;
+    if ((e = set_smem(k_c2cT_inv<T>, sm)) != cudaSuccess) return e;
+    const int tiles = (nz + tl - 1) / tl;
+    k_c2cT_inv<T><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny,
+                                                        p.logP[1], tl, tw[1], p.logP[1], nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    const int G = Hx >> 4;
+    const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    if ((e = set_smem(k_c2r_T<T>, sm)) != cudaSuccess) return e;
+    k_c2r_T<T><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(S1, y, nrows, nx, (size_t)nrows, nx, p.logP[0] - 1, tl,
+                                                          tw[0], p.logP[0], nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template cudaError_t spectrum_forward<double>(const Plan&, const double*, double2*, void*, cudaStream_t);
+template cudaError_t spectrum_inverse<double>(const Plan&, const double2*, const double*, double*, void*,
+                                              cudaStream_t);
 
 }  // namespace frlap

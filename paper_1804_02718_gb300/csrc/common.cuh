@@ -94,6 +94,12 @@ template <typename T>
 cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
                          cudaEvent_t const* ev = nullptr, const T* lam_override = nullptr);
 size_t apply_work_bytes(const Plan& p, int real_bytes);
+// forward half spectrum F R^T u (2D [kx][ky], 3D [kx][ky][kz]) and its multiplied inverse; same workspace as apply
+size_t spectrum_elems(const Plan& p);
+template <typename T>
+cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work, cudaStream_t s);
+template <typename T>
+cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T* y, void* work, cudaStream_t s);
 
 // coefficient / symbol generation (coeffs.cu)
 cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int Nmax, double* coef, void* scratch,

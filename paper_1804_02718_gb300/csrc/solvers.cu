@@ -365,7 +365,8 @@ static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu,
 // mu = FP32 preconditioner symbol (octant) or nullptr for plain CG.
 template <typename T>
 static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double s, double rtol, int maxit,
-                           int use_x0, const float* mu, void* work, cudaStream_t st, CgState* hS) {
+                           int use_x0, const float* mu, void* work, cudaStream_t st, CgState* hS,
+                           T* snap = nullptr, int nsnap = 0) {
   const CgBufs b = carve(p, work, sizeof(T));
   T* r = reinterpret_cast<T*>(b.r);
   T* pv = reinterpret_cast<T*>(b.p);
@@ -389,6 +390,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
     k_pcg_start<T, T><<<kBlocks, kThreads, 0, st>>>(r, nullptr, z, pv, n, b.partials, S);
   }
   FRLAP_LAUNCH_CHECK("k_pcg_start");
+  if (snap && nsnap > 0) FRLAP_CUDA_TRY(cudaMemcpyAsync(snap, x, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
   const int* done = &S->done;
   const int chunk = 8;
   int launched = 0;
@@ -398,6 +400,9 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
       if (e != cudaSuccess) return cuda_fail(e, "apply (CG)");
       k_cg_pq<T><<<kBlocks, kThreads, 0, st>>>(pv, q, n, b.partials, S);
       k_cg_update<T><<<kBlocks, kThreads, 0, st>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr);
+      if (snap && launched + c + 1 < nsnap)
+        FRLAP_CUDA_TRY(cudaMemcpyAsync(snap + (size_t)(launched + c + 1) * n, x, n * sizeof(T),
+                                       cudaMemcpyDeviceToDevice, st));
       if (mu) {
         e = precondition<T>(p, b, mu, st);
         if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
@@ -433,6 +438,34 @@ static frlap_status true_residual(const Plan& p, const double* f, const double* 
   FRLAP_CUDA_TRY(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
   *relres = (h[1] > 0.0) ? sqrt(h[0] / h[1]) : 0.0;
+  return FRLAP_OK;
+}
+
+// E[j] <- xs - E[j]
+__global__ void k_err_from_snap(double* E, const double* __restrict__ xs, size_t n) {
+  GRID_STRIDE(i, n) E[i] = xs[i] - E[i];
+}
+
+frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, double* E, double* R, int* npairs,
+                           void* work, cudaStream_t st) {
+  CgBufs b = carve(p, work, 8);
+  double* x = reinterpret_cast<double*>(b.z);  // the solution lives in the (unused) z buffer
+  FRLAP_CUDA_TRY(cudaMemsetAsync(x, 0, p.M * sizeof(double), st));
+  CgState hS;
+  frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, 1000000, 0, nullptr, work, st, &hS, E, K);
+  if (rc != FRLAP_OK) return rc;
+  if (hS.status != FRLAP_OK) return fail((frlap_status)hS.status, "CG for the training pairs stopped early");
+  // x_0 .. x_{iters-1}: the last iterate is the solution itself (zero error) and is left out
+  const int np = hS.iters < K ? hS.iters : K;
+  for (int j = 0; j < np; ++j) {
+    double* Ej = E + (size_t)j * p.M;
+    k_err_from_snap<<<kBlocks, kThreads, 0, st>>>(Ej, x, p.M);
+    FRLAP_LAUNCH_CHECK("k_err_from_snap");
+    cudaError_t e = apply_launch<double>(p, Ej, R + (size_t)j * p.M, b.awork, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "apply (training pairs)");
+  }
+  FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (npairs) *npairs = np;
   return FRLAP_OK;
 }
 

@@ -1,0 +1,113 @@
+"""GPU parity of the learned preconditioner's kernels against the FP64 oracle, and what training gains.
+
+The network is FP32 on the GPU and FP64 in the oracle; the tolerances below are
+those of FP32 activations (relative 1e-5 for the multiplier, 2e-4 for the loss
+gradient, which sums many FP32 products).
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import frlap_inputs as inp
+from oracle import fast, netprecond as npc, scheme, solvers
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=8)
+def _coef(d, alpha, h, N):
+    return scheme.coefficients(d, alpha, h, N)
+
+
+def _lam_oct(d, alpha, N, P):
+    h = 2.0 / N
+    a, c = _coef(d, alpha, h, N), scheme.c_d_alpha(d, alpha)
+    shape = (N - 1,) * d
+    lam = fast.symbol(a, c, shape, P=tuple(reversed(P)))
+    return lam[tuple(slice(0, p // 2 + 1) for p in reversed(P))], a, c
+
+
+def _theta(seed):
+    rng = np.random.default_rng(seed)
+    return npc.init_params(seed=seed) + 0.05 * rng.standard_normal(npc.NPARAM)
+
+
+@pytest.mark.parametrize("d,N,alpha", [(2, 64, 1.5), (3, 16, 0.9)])
+def test_mlp_multiplier_matches_oracle(frlap, d, N, alpha):
+    plan = frlap.Plan(d, alpha, 2.0 / N, (N,) * d)
+    theta = _theta(1)
+    lam_oct, _, _ = _lam_oct(d, alpha, N, plan.P)
+    m_ref, _, _ = npc.multiplier(theta, alpha, lam_oct, plan.P)
+    m = frlap.frlap_mlp_multiplier(plan, torch.tensor(theta, dtype=torch.float32, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(m, m_ref, rtol=2e-5, atol=0)
+
+
+@pytest.mark.parametrize("d,N,alpha", [(2, 16, 1.3), (3, 8, 1.7)])
+def test_learn_grad_matches_oracle(frlap, d, N, alpha):
+    plan = frlap.Plan(d, alpha, 2.0 / N, (N,) * d)
+    theta = npc.pack(npc.unpack(_theta(2)))
+    theta32 = theta.astype(np.float32).astype(np.float64)  # both sides use the same FP32-rounded weights
+    lam_oct, a, c = _lam_oct(d, alpha, N, plan.P)
+    rng = np.random.default_rng(3)
+    es = [rng.standard_normal(plan.shape) for _ in range(4)]
+    rs = [scheme.apply_dense(a, c, e) for e in es]
+    L_ref, g_ref = npc.loss_and_grad(theta32, alpha, lam_oct, plan.P, rs, es, lambda v: scheme.apply_dense(a, c, v))
+    R = torch.tensor(np.stack(rs), device="cuda")
+    E = torch.tensor(np.stack(es), device="cuda")
+    grad = torch.empty(npc.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    work = torch.empty(frlap.frlap_learn_workspace_bytes(plan, 4) + 256, dtype=torch.uint8, device="cuda")
+    off = (-work.data_ptr()) % 256
+    frlap.frlap_learn_grad(plan, torch.tensor(theta32, dtype=torch.float32, device="cuda"), R, E, grad, loss,
+                           work[off:])
+    assert loss.item() == pytest.approx(L_ref, rel=2e-5)
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - g_ref) <= 2e-4 * np.linalg.norm(g_ref)
+
+
+def test_cg_pairs_are_residual_error_pairs(frlap):
+    """frlap_cg_pairs: e_j = x* - x_j from the plain CG iterates and r_j = A e_j."""
+    N, alpha = 32, 1.2
+    h = 2.0 / N
+    a, c = _coef(2, alpha, h, N), scheme.c_d_alpha(2, alpha)
+    f = inp.gaussian_sum_field((N, N), h, seed=6)
+    plan = frlap.Plan(2, alpha, h, (N, N))
+    E, R, n = frlap.frlap_cg_pairs(plan, torch.from_numpy(f).cuda(), 400, rtol=1e-11)
+    x_ref = np.linalg.solve(scheme.dense_matrix(a, c, f.shape), f.reshape(-1)).reshape(f.shape)
+    _, it_ref, _ = solvers.cg(lambda v: scheme.apply_dense(a, c, v), f, rtol=1e-11)
+    assert abs(n - it_ref) <= 2
+    E, R = E[:n].cpu().numpy(), R[:n].cpu().numpy()
+    np.testing.assert_allclose(E[0], x_ref, rtol=0, atol=1e-9 * np.abs(x_ref).max())  # x_0 = 0
+    for j in (0, n // 2, n - 1):
+        Ae = scheme.apply_dense(a, c, E[j])
+        assert np.linalg.norm(R[j] - Ae) <= 1e-12 * np.linalg.norm(Ae) + 1e-14
+    assert np.linalg.norm(R[0] - f) <= 1e-9 * np.linalg.norm(f)
+
+
+def test_training_lowers_loss_and_beats_plain_cg(frlap):
+    """Train on plain-CG pairs (2D 63^2, three alphas), then use the network on an unseen grid:
+    the loss falls below the untrained network's, and flexible PCG with the learned multiplier reaches
+    1e-10 in far fewer iterations than plain CG (the method without it), at the same solution."""
+    from paper_1804_02718_gb300 import learned
+    sets = [learned.PairSet(2, al, 64, [inp.gaussian_sum_field((64, 64), 2.0 / 64, seed=s) for s in (6, 7)], K=400)
+            for al in (0.7, 1.3, 1.9)]
+    assert sum(s.count for s in sets) > 100
+    p0 = learned.init_params(0)
+    L0 = [learned.loss_and_grad(s, p0, 0, s.count)[0].item() for s in sets]
+    params, hist = learned.train(sets, steps=400, batch=8, lr=2e-3, seed=0)
+    L1 = [learned.loss_and_grad(s, params, 0, s.count)[0].item() for s in sets]
+    print("loss untrained", L0, "trained", L1)
+    assert sum(L1) < 0.95 * sum(L0), (L0, L1)
+    # unseen operator: alpha = 1.5 on 127^2
+    N, alpha = 128, 1.5
+    h = 2.0 / N
+    plan = frlap.Plan(2, alpha, h, (N, N))
+    f = torch.from_numpy(inp.gaussian_sum_field((N, N), h, seed=11)).cuda()
+    learned.install(plan, params)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-10, precond=frlap.FRLAP_PRECOND_LEARNED)
+    x0, it0, rel0, code0 = frlap.frlap_pcg_solve(plan, f, rtol=1e-10)
+    assert code == 0 and code0 == 0 and rel <= 1e-10
+    assert it < 0.35 * it0, (it, it0)
+    assert torch.linalg.norm(x - x0).item() <= 1e-9 * torch.linalg.norm(x0).item()

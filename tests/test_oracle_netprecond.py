@@ -33,14 +33,16 @@ def test_gradient_matches_finite_differences(d):
     theta = npc.init_params(seed=2) + 0.05 * rng.standard_normal(npc.NPARAM)
     es = [rng.standard_normal(shape) for _ in range(3)]
     rs = [scheme.apply_dense(a, c, e) for e in es]
-    L, g = npc.loss_and_grad(theta, 1.3, lam_oct, P, rs, es)
+    A = lambda v: scheme.apply_dense(a, c, v)
+    L, g = npc.loss_and_grad(theta, 1.3, lam_oct, P, rs, es, A)
+    assert 0.0 <= L <= 1.0
     idx = rng.choice(npc.NPARAM, size=24, replace=False).tolist() + [npc.NPARAM - 1, 0]
     for i in idx:
         h = 1e-6
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (npc.loss_and_grad(tp, 1.3, lam_oct, P, rs, es)[0] - npc.loss_and_grad(tm, 1.3, lam_oct, P, rs, es)[0]) / (2 * h)
+        fd = (npc.loss_and_grad(tp, 1.3, lam_oct, P, rs, es, A)[0] - npc.loss_and_grad(tm, 1.3, lam_oct, P, rs, es, A)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(fd)) + 1e-9, (i, fd, g[i])
 
 
