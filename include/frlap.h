@@ -239,6 +239,22 @@ frlap_status frlap_adam_step(float* d_params, const float* d_grad, float* d_m1, 
 frlap_status frlap_cg_pairs(const frlap_plan* plan, const double* d_f, int K, double rtol, double* d_E, double* d_R,
                             int* npairs, void* d_work, void* stream);
 
+/* Batched Allen-Cahn: nbatch instances (each its own plan: alpha and grid; F64 or
+ * MIXED plans) advance nsteps semi-implicit steps each, all in one CUDA-graph
+ * launch with on-device control: one conditional WHILE node whose body runs one CG
+ * iteration for every instance still solving, then moves each instance whose solve
+ * has ended to its next step.  Each step solves (I + tau eps^2 A_i) v =
+ * u + tau (u - u^3) by CG from v = 0 to ||r|| <= rtol ||rhs|| or maxit iterations.
+ * Instances of equal shape share one launch per kernel.  d_u[i]: instance i's
+ * grid vector (doubles), updated in place.  iters[i], status[i] (host arrays, may
+ * be NULL): total CG iterations and frlap_status per instance.  The loop is bounded
+ * (nsteps * (maxit + 2) + 8 passes; FRLAP_ETIMEOUT past that).  d_work:
+ * frlap_allen_cahn_batch_workspace_bytes bytes.  Synchronises stream. */
+size_t frlap_allen_cahn_batch_workspace_bytes(int nbatch, const frlap_plan* const* plans);
+frlap_status frlap_allen_cahn_batch(int nbatch, const frlap_plan* const* plans, double* const* d_u, double tau,
+                                    double eps, int nsteps, double rtol, int maxit, int* iters, int* status,
+                                    void* d_work, void* stream);
+
 /* The message for the last error on the calling thread ("" if none). */
 const char* frlap_last_error(void);
 

@@ -37,6 +37,10 @@ cudaError_t learn_grad_launch(const Plan& p, const float* params, const double* 
                               float* grad, double* loss, void* work, cudaStream_t s);
 cudaError_t adam_launch(float* p, const float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
                         int t, cudaStream_t s);
+size_t ac_batch_work_bytes(int nb, const frlap_plan* const* plans);
+frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const* u, double tau, double eps,
+                           int nsteps, double rtol, int maxit, int* iters_out, int* status_out, void* work,
+                           cudaStream_t user);
 frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, double* E, double* R, int* npairs,
                            void* work, cudaStream_t st);
 cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host);
@@ -387,6 +391,29 @@ frlap_status frlap_cg_pairs(const frlap_plan* plan, const double* d_f, int K, do
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
   return cg_pairs_impl(*plan, d_f, K, rtol, d_E, d_R, npairs, d_work, (cudaStream_t)stream);
+}
+
+size_t frlap_allen_cahn_batch_workspace_bytes(int nbatch, const frlap_plan* const* plans) {
+  if (nbatch < 1 || !plans) return 0;
+  for (int i = 0; i < nbatch; ++i)
+    if (!plans[i]) return 0;
+  return ac_batch_work_bytes(nbatch, plans);
+}
+
+frlap_status frlap_allen_cahn_batch(int nbatch, const frlap_plan* const* plans, double* const* d_u, double tau,
+                                    double eps, int nsteps, double rtol, int maxit, int* iters, int* status,
+                                    void* d_work, void* stream) {
+  if (nbatch < 1 || !plans || !d_u) return fail(FRLAP_EINVAL, "need nbatch >= 1, plans and d_u");
+  for (int i = 0; i < nbatch; ++i) {
+    if (!plans[i] || !d_u[i]) return fail(FRLAP_EINVAL, "NULL plan or d_u entry");
+    if (plans[i]->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "Allen-Cahn batch needs F64 or MIXED plans");
+  }
+  if (!(tau > 0.0) || !(eps > 0.0) || nsteps < 0 || !(rtol > 0.0) || maxit < 1)
+    return fail(FRLAP_EINVAL, "need tau > 0, eps > 0, nsteps >= 0, rtol > 0, maxit >= 1");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  return ac_batch_impl(nbatch, plans, d_u, tau, eps, nsteps, rtol, maxit, iters, status, d_work,
+                       (cudaStream_t)stream);
 }
 
 frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void* stream) {

@@ -20,6 +20,13 @@ namespace frlap {
 
 namespace {
 
+// Batched launches: instance b = blockIdx.y reads and writes at these element offsets
+// (input, output, symbol) times b, and stops early when skip[b * skip_stride] is set.
+struct Batch {
+  size_t in = 0, out = 0, lam = 0;
+  int skip = 0;
+};
+
 struct LamMap {
   int d;       // 2 or 3
   int logPy;   // 3D: log2 P_y (column index = kx * P_y + ky)
@@ -31,7 +38,13 @@ struct LamMap {
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
-                        const int* __restrict__ skip) {
+                        const int* __restrict__ skip, Batch bt) {
+  {
+    const size_t bi = blockIdx.y;
+    in += bi * bt.in;
+    out += bi * bt.out;
+    if (skip) skip += bi * bt.skip;
+  }
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
@@ -79,7 +92,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* 
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
-                        const int* __restrict__ skip) {
+                        const int* __restrict__ skip, Batch bt) {
+  {
+    const size_t bi = blockIdx.y;
+    in += bi * bt.in;
+    out += bi * bt.out;
+    if (skip) skip += bi * bt.skip;
+  }
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
@@ -123,7 +142,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
-                         const int* __restrict__ skip) {
+                         const int* __restrict__ skip, Batch bt) {
+  {
+    const size_t bi = blockIdx.y;
+    data += bi * bt.in;
+    lam += bi * bt.lam;
+    if (skip) skip += bi * bt.skip;
+  }
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
@@ -163,7 +188,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
-                           const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
+                           const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
+  {
+    const size_t bi = blockIdx.y;
+    in += bi * bt.in;
+    out += bi * bt.out;
+    if (skip) skip += bi * bt.skip;
+  }
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
@@ -192,7 +223,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
-                           const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip) {
+                           const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
+  {
+    const size_t bi = blockIdx.y;
+    in += bi * bt.in;
+    out += bi * bt.out;
+    if (skip) skip += bi * bt.skip;
+  }
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
@@ -305,9 +342,13 @@ size_t apply_work_bytes(const Plan& p, int real_bytes) {
   return b;
 }
 
+// B instances of the same shape: u, y at stride `vstride` elements, workspace at stride
+// apply_work_bytes(p), symbols at stride lam_stride (0: all share one), skip flags at
+// stride skip_stride ints.
 template <typename T>
-cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
-                         cudaEvent_t const* ev, const T* lam_override) {
+static cudaError_t apply_launch_b(const Plan& p, int B, const T* u, T* y, size_t vstride, void* work, cudaStream_t s,
+                                  const int* skip, int skip_stride, cudaEvent_t const* ev, const T* lam_override,
+                                  size_t lam_stride) {
   int stage = 0;
   auto mark = [&]() -> cudaError_t {
     if (ev && ev[stage]) {
@@ -335,6 +376,22 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
   const int Hx = p.P[0] / 2;
   const int nrows = ny * (p.d == 3 ? nz : 1);
   const size_t ld1 = (size_t)nrows;  // S1 k-stride: all (z, y) rows
+  // per-instance workspace: S1 and S2 of one apply, in complex elements
+  const size_t wstride = apply_work_bytes(p, sizeof(T)) / eb;
+  if (B > 1) S2 = S1 + align256(p.s1_elems * eb) / eb;
+  Batch b_in;   // u -> S1
+  b_in.in = vstride;
+  b_in.out = wstride;
+  b_in.skip = skip_stride;
+  Batch b_ws;   // workspace-only stages (+ symbol)
+  b_ws.in = wstride;
+  b_ws.out = wstride;
+  b_ws.lam = lam_stride;
+  b_ws.skip = skip_stride;
+  Batch b_out;  // S1 -> y
+  b_out.in = wstride;
+  b_out.out = vstride;
+  b_out.skip = skip_stride;
 
   // ---- stage 1: rows of u -> S1[kx][row]
   {
@@ -345,7 +402,7 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
     if (e != cudaSuccess) return e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    k_r2c_T<T><<<grid, tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip);
+    k_r2c_T<T><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   LamMap map;
@@ -363,7 +420,7 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
     const int ncols = Hx + 1;
     const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    k_colmul<T><<<grid, tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip);
+    k_colmul<T><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
     const int Py = p.P[1], Pz = p.P[2];
@@ -377,8 +434,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
       if ((e = mark()) != cudaSuccess) return e;
-      k_c2cT_fwd<T><<<grid, tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz, nz,
-                                              logPy, tl, tw[1], logPy, skip);
+      k_c2cT_fwd<T><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz,
+                                                       nz, logPy, tl, tw[1], logPy, skip, b_ws);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // ---- stage 3: S2[kx][ky][:] -> FFT_z, * lambda, IFFT_z
@@ -391,7 +448,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
       const int ncols = (Hx + 1) * Py;
       const int grid = (ncols + tl - 1) / tl;
       if ((e = mark()) != cudaSuccess) return e;
-      k_colmul<T><<<grid, tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz, skip);
+      k_colmul<T><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz,
+                                                     skip, b_ws);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
@@ -404,8 +462,8 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
       if ((e = mark()) != cudaSuccess) return e;
-      k_c2cT_inv<T><<<grid, tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny,
-                                              logPy, tl, tw[1], logPy, skip);
+      k_c2cT_inv<T><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny,
+                                                       ny, logPy, tl, tw[1], logPy, skip, b_ws);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
@@ -418,11 +476,28 @@ cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream
     if (e != cudaSuccess) return e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    k_c2r_T<T><<<grid, tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip);
+    k_c2r_T<T><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return mark();
 }
+
+template <typename T>
+cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
+                         cudaEvent_t const* ev, const T* lam_override) {
+  return apply_launch_b<T>(p, 1, u, y, 0, work, s, skip, 0, ev, lam_override, 0);
+}
+
+template <typename T>
+cudaError_t apply_batch_launch(const Plan& p, int B, const T* u, T* y, size_t vstride, void* work, cudaStream_t s,
+                               const int* skip, int skip_stride, const T* lam, size_t lam_stride) {
+  return apply_launch_b<T>(p, B, u, y, vstride, work, s, skip, skip_stride, nullptr, lam, lam_stride);
+}
+
+template cudaError_t apply_batch_launch<double>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
+                                                const int*, int, const double*, size_t);
+template cudaError_t apply_batch_launch<float>(const Plan&, int, const float*, float*, size_t, void*, cudaStream_t,
+                                               const int*, int, const float*, size_t);
 
 template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
                                           cudaEvent_t const*, const double*);
@@ -457,7 +532,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     if ((e = set_smem(k_r2c_T<T>, sm)) != cudaSuccess) return e;
     k_r2c_T<T><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(u, S1, nrows, nx, nx, (size_t)nrows, p.logP[0] - 1, tl,
-                                                          tw[0], p.logP[0], nullptr);
+                                                          tw[0], p.logP[0], nullptr, Batch{});
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const C* lines = S1;
@@ -472,7 +547,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
     if ((e = set_smem(k_c2cT_fwd<T>, sm)) != cudaSuccess) return e;
     const int tiles = (nz + tl - 1) / tl;
     k_c2cT_fwd<T><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz,
-                                                        nz, p.logP[1], tl, tw[1], p.logP[1], nullptr);
+                                                        nz, p.logP[1], tl, tw[1], p.logP[1], nullptr, Batch{});
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     lines = S2;
     ncols = (Hx + 1) * Py;
@@ -536,7 +611,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
     if ((e = set_smem(k_c2cT_inv<T>, sm)) != cudaSuccess) return e;
     const int tiles = (nz + tl - 1) / tl;
     k_c2cT_inv<T><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny,
-                                                        p.logP[1], tl, tw[1], p.logP[1], nullptr);
+                                                        p.logP[1], tl, tw[1], p.logP[1], nullptr, Batch{});
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -545,7 +620,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     if ((e = set_smem(k_c2r_T<T>, sm)) != cudaSuccess) return e;
     k_c2r_T<T><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(S1, y, nrows, nx, (size_t)nrows, nx, p.logP[0] - 1, tl,
-                                                          tw[0], p.logP[0], nullptr);
+                                                          tw[0], p.logP[0], nullptr, Batch{});
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
