@@ -56,8 +56,12 @@ typedef enum {
 /* Arithmetic of the FFT apply.  F64: IEEE double everywhere.  F32: single
  * precision FFT stages and symbol.  MIXED: a plan that holds both, so
  * that the iterative-refinement solver can run FP32 inner applies and FP64
- * outer residuals (coefficients and symbol are always generated in FP64). */
-typedef enum { FRLAP_F64 = 0, FRLAP_F32 = 1, FRLAP_MIXED = 2 } frlap_prec;
+ * outer residuals (coefficients and symbol are always generated in FP64).
+ * DF64: FP64 vectors in memory, FFT stages in double-float arithmetic (pairs
+ * of FP32 numbers, about 48 significant bits), which GB300 runs several times
+ * faster than FP64 at an accuracy within the FP64 tolerance of the apply.
+ * MIXED_DF64: MIXED with the FP64 side computed as in DF64. */
+typedef enum { FRLAP_F64 = 0, FRLAP_F32 = 1, FRLAP_MIXED = 2, FRLAP_DF64 = 3, FRLAP_MIXED_DF64 = 4 } frlap_prec;
 
 /* Which scratch size frlap_workspace_bytes reports. */
 typedef enum { FRLAP_OP_APPLY = 0, FRLAP_OP_PCG = 1, FRLAP_OP_AC = 2 } frlap_op;
@@ -119,7 +123,7 @@ frlap_status frlap_plan_symbol(const frlap_plan* plan, double* d_lambda, void* s
  * the circulant embedding: zero-pad u to P_r per axis, forward real-to-complex
  * FFT along x, complex FFTs along y (and z), multiply by lambda, inverse FFTs,
  * keep the first n_r entries per axis.  d_u, d_y: prod(n_r) elements of double
- * (F64 and MIXED plans) or float (F32 plans); they must not overlap. */
+ * (F64, MIXED, DF64 and MIXED_DF64 plans) or float (F32 plans); they must not overlap. */
 frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream);
 
 /* Number of kernel stages of one apply (2D: 3, 3D: 5): pad + real FFT along x,

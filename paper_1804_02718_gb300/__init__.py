@@ -6,7 +6,7 @@ package is its thin Python binding.  Build the library with
 is missing -- there is no CPU fallback.
 """
 from ._binding import (  # noqa: F401
-    FRLAP_F32, FRLAP_F64, FRLAP_MIXED, FRLAP_OP_AC, FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_SOLVE_CG,
+    FRLAP_F32, FRLAP_F64, FRLAP_MIXED, FRLAP_DF64, FRLAP_MIXED_DF64, FRLAP_OP_AC, FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_SOLVE_CG,
     FRLAP_SOLVE_IR, FRLAP_PRECOND_NONE, FRLAP_PRECOND_STRANG, FRLAP_PRECOND_LEARNED, LIB_PATH, STATUS, FrlapError, Plan, frlap_allen_cahn_step, frlap_apply, frlap_apply_f32,
     frlap_apply_nstages, frlap_apply_profiled, frlap_apply_noalloc, NOALLOC_MAX_BYTES,
     frlap_c_dalpha, frlap_coeffs, frlap_pcg_solve, frlap_precond_strang, frlap_precond_set_symbol, frlap_precond_apply,

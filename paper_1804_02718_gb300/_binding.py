@@ -15,7 +15,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfrlap.so")
 
-FRLAP_F64, FRLAP_F32, FRLAP_MIXED = 0, 1, 2
+FRLAP_F64, FRLAP_F32, FRLAP_MIXED, FRLAP_DF64, FRLAP_MIXED_DF64 = 0, 1, 2, 3, 4
 FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_OP_AC = 0, 1, 2
 FRLAP_SOLVE_CG, FRLAP_SOLVE_IR = 0, 1
 FRLAP_PRECOND_NONE, FRLAP_PRECOND_STRANG, FRLAP_PRECOND_LEARNED = 0, 1, 2

@@ -243,7 +243,7 @@ struct Group {
 };
 
 bool same_shape(const Plan& a, const Plan& b) {
-  if (a.d != b.d) return false;
+  if (a.d != b.d || a.df64 != b.df64) return false;
   for (int r = 0; r < a.d; ++r)
     if (a.n[r] != b.n[r] || a.P[r] != b.P[r]) return false;
   return true;
@@ -267,6 +267,15 @@ std::vector<Group> make_groups(int nb, const frlap_plan* const* plans) {
     }
   }
   return g;
+}
+
+// the group's batched apply through its FP64 engine; lam holds the stacked symbols in that engine's type
+cudaError_t batch_apply(const Plan& p, int B, const double* u, double* y, size_t vs, void* work, cudaStream_t s,
+                        const int* skip, int skip_stride, const double* lam, size_t lam_stride) {
+  if (p.df64)
+    return apply_batch_launch<dfl>(p, B, u, y, vs, work, s, skip, skip_stride, reinterpret_cast<const dfl*>(lam),
+                                   lam_stride);
+  return apply_batch_launch<double>(p, B, u, y, vs, work, s, skip, skip_stride, lam, lam_stride);
 }
 
 size_t group_bytes(const Group& g) {
@@ -347,8 +356,9 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
         const frlap_plan* pi = plans[g.idx[k]];
         e = cudaMemcpyAsync(g.u + k * g.vs, u[g.idx[k]], p.M * 8, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
-          e = cudaMemcpyAsync(g.lam + k * (align256(p.lam_count * 8) / 8), pi->lam64, p.lam_count * 8,
-                              cudaMemcpyDeviceToDevice, s);
+          e = cudaMemcpyAsync(g.lam + k * (align256(p.lam_count * 8) / 8),
+                              p.df64 ? static_cast<const void*>(pi->lamdf) : static_cast<const void*>(pi->lam64),
+                              p.lam_count * 8, cudaMemcpyDeviceToDevice, s);
       }
     }
     if (e != cudaSuccess) {
@@ -363,8 +373,8 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
     // set the kernel attributes before capture (the first apply does it)
     for (auto& g : groups) {
       const Plan& p = *g.plan;
-      e = apply_batch_launch<double>(p, (int)g.idx.size(), g.p, g.q, g.vs, g.awork, s, &g.S[0].done,
-                                     (int)(sizeof(AcState) / sizeof(int)), g.lam, align256(p.lam_count * 8) / 8);
+      e = batch_apply(p, (int)g.idx.size(), g.p, g.q, g.vs, g.awork, s, &g.S[0].done,
+                      (int)(sizeof(AcState) / sizeof(int)), g.lam, align256(p.lam_count * 8) / 8);
       if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) {
@@ -399,8 +409,7 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
     for (auto& g : groups) {
       const Plan& p = *g.plan;
       const int B = (int)g.idx.size();
-      apply_batch_launch<double>(p, B, g.p, g.q, g.vs, g.awork, s, &g.S[0].done, sstride, g.lam,
-                                 align256(p.lam_count * 8) / 8);
+      batch_apply(p, B, g.p, g.q, g.vs, g.awork, s, &g.S[0].done, sstride, g.lam, align256(p.lam_count * 8) / 8);
       const dim3 grid(kAcBlocks, B);
       k_ac_pq<<<grid, kAcThreads, 0, s>>>(g.p, g.q, g.M, g.vs, g.S, g.partials, sc);
       k_ac_update<<<grid, kAcThreads, 0, s>>>(g.x, g.r, g.p, g.q, g.M, g.vs, g.S, g.partials, maxit);

@@ -112,9 +112,11 @@ frlap_status frlap_plan_destroy(frlap_plan* plan) {
   cudaFree(plan->lam32);
   cudaFree(plan->mu_strang);
   cudaFree(plan->mu_learned);
+  cudaFree(plan->lamdf);
   for (int r = 0; r < 3; ++r) {
     cudaFree(plan->tw64[r]);
     cudaFree(plan->tw32[r]);
+    cudaFree(plan->twdf[r]);
   }
   if (plan->side) cudaStreamDestroy(plan->side);
   delete plan;
@@ -126,7 +128,7 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   frlap_status rc = check_params(d, alpha, gamma, h, N);
   if (rc != FRLAP_OK) return rc;
   if (!out) return fail(FRLAP_EINVAL, "out is NULL");
-  if (prec != FRLAP_F64 && prec != FRLAP_F32 && prec != FRLAP_MIXED) return fail(FRLAP_EINVAL, "unknown precision");
+  if (prec < FRLAP_F64 || prec > FRLAP_MIXED_DF64) return fail(FRLAP_EINVAL, "unknown precision");
   *out = nullptr;
   frlap_plan* p = new (std::nothrow) frlap_plan();
   if (!p) return fail(FRLAP_ENOMEM, "host allocation failed");
@@ -135,6 +137,7 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   p->gamma = gamma;
   p->h = h;
   p->prec = prec;
+  p->df64 = (prec == FRLAP_DF64 || prec == FRLAP_MIXED_DF64);
   p->c = c_dalpha_host(d, alpha);
   p->Nmax = 0;
   p->M = 1;
@@ -186,6 +189,13 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
       return cleanup(FRLAP_ENOMEM, "plan allocation failed");
     cudaError_t e = twiddle_launch(p->P[r], p->tw64[r], p->tw32[r], s);
     if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));
+    if (p->df64) {
+      if (cudaMalloc(&p->twdf[r], p->P[r] * sizeof(cdf)) != cudaSuccess)
+        return cleanup(FRLAP_ENOMEM, "plan allocation failed");
+      e = to_df_launch(reinterpret_cast<const double*>(p->tw64[r]), reinterpret_cast<dfl*>(p->twdf[r]),
+                       2 * (size_t)p->P[r], s);
+      if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));
+    }
   }
   cudaError_t e = coeffs_launch(d, alpha, gamma, h, p->Nmax, coef, scratch, s);
   if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("coefficients: ") + cudaGetErrorString(e));
@@ -195,6 +205,12 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   for (int r = 0; r < d; ++r) scale /= (double)p->P[r];
   e = scale_symbol_launch(p->lam64, p->lam32, p->lam_count, scale, s);
   if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol scale: ") + cudaGetErrorString(e));
+  if (p->df64) {
+    if (cudaMalloc(&p->lamdf, p->lam_count * sizeof(dfl)) != cudaSuccess)
+      return cleanup(FRLAP_ENOMEM, "plan allocation failed");
+    e = to_df_launch(p->lam64, p->lamdf, p->lam_count, s);
+    if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol copy: ") + cudaGetErrorString(e));
+  }
   e = cudaStreamSynchronize(s);
   cudaFree(coef);
   cudaFree(scratch);
@@ -214,11 +230,11 @@ size_t frlap_workspace_bytes(const frlap_plan* plan, int op) {
   switch (op) {
     case FRLAP_OP_APPLY: {
       size_t b = apply_work_bytes(*plan, eb);
-      if (plan->prec == FRLAP_MIXED) b = apply_work_bytes(*plan, 8);
+      if (plan->prec != FRLAP_F32) b = apply_work_bytes(*plan, 8);
       return b;
     }
     case FRLAP_OP_PCG:
-      if (plan->prec == FRLAP_MIXED) return ir_work_bytes(*plan);
+      if (plan->prec == FRLAP_MIXED || plan->prec == FRLAP_MIXED_DF64) return ir_work_bytes(*plan);
       return cg_work_bytes(*plan, eb);
     case FRLAP_OP_AC:
       return ac_work_bytes(*plan);
@@ -258,7 +274,7 @@ frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, voi
   if (plan->prec == FRLAP_F32)
     e = apply_launch<float>(*plan, (const float*)d_u, (float*)d_y, d_work, (cudaStream_t)stream, nullptr);
   else
-    e = apply_launch<double>(*plan, (const double*)d_u, (double*)d_y, d_work, (cudaStream_t)stream, nullptr);
+    e = apply64(*plan, (const double*)d_u, (double*)d_y, d_work, (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_apply");
   return FRLAP_OK;
 }
@@ -276,7 +292,7 @@ frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void*
   if (plan->prec == FRLAP_F32)
     e = apply_launch<float>(*plan, (const float*)d_u, (float*)d_y, d_work, (cudaStream_t)stream, nullptr, ev);
   else
-    e = apply_launch<double>(*plan, (const double*)d_u, (double*)d_y, d_work, (cudaStream_t)stream, nullptr, ev);
+    e = apply64(*plan, (const double*)d_u, (double*)d_y, d_work, (cudaStream_t)stream, nullptr, ev);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_profiled");
   return FRLAP_OK;
 }
@@ -309,8 +325,8 @@ frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* 
   if (!(rtol > 0.0) || maxit < 1) return fail(FRLAP_EINVAL, "need rtol > 0 and maxit >= 1");
   if (solver == FRLAP_SOLVE_CG && plan->prec == FRLAP_F32)
     return fail(FRLAP_EINVAL, "FP64 CG needs an F64 or MIXED plan");
-  if (solver == FRLAP_SOLVE_IR && plan->prec != FRLAP_MIXED)
-    return fail(FRLAP_EINVAL, "iterative refinement needs a MIXED plan");
+  if (solver == FRLAP_SOLVE_IR && plan->prec != FRLAP_MIXED && plan->prec != FRLAP_MIXED_DF64)
+    return fail(FRLAP_EINVAL, "iterative refinement needs a MIXED or MIXED_DF64 plan");
   if (solver != FRLAP_SOLVE_CG && solver != FRLAP_SOLVE_IR) return fail(FRLAP_EINVAL, "unknown solver");
   if (solver == FRLAP_SOLVE_IR && !(inner_rtol > 0.0 && inner_rtol < 1.0))
     return fail(FRLAP_EINVAL, "inner_rtol must lie in (0, 1)");

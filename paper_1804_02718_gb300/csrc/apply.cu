@@ -13,6 +13,8 @@
 //       c2r_T  : S1[kx][(z,y)]              -> rows of y
 // Every stage reads and writes whole contiguous lines or TL-wide contiguous
 // tiles; every global index below is bounded by the line/tile validity tests.
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -36,7 +38,7 @@ struct LamMap {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
   {
@@ -57,9 +59,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* 
   const int LS = sline(H);
   C* buf = smem + (size_t)l * LS;
   T* rb = reinterpret_cast<T*>(buf);
-  const T* src = in + (size_t)(valid ? line : 0) * ldi;
+  const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // real sample i is component (i & 1) of complex element i / 2 (even/odd packing)
-  for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? src[i] : (T)0;
+  for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(src[i]) : T(0.0);
   __syncthreads();
   fft_line<T, -1>(buf, logH, lane, tw, logP);
   // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* 
     const int km = H - k;
     const C zk = buf[spad(k)];
     const C zm = buf[spad(km & (H - 1))];
-    const T half = (T)0.5;
+    const T half = T(0.5);
     {
       const C a = zk, b = conjg(zm);
       const C xe = half * (a + b);
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const T* 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, T* __restrict__ out, int nlines, int n, size_t ldi,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, io_t<T>* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
   {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   const int total = TL * (H + 1);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l2 = idx % TL, k = idx / TL;
-    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? in[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
+    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? in[(size_t)k * ldi + line0 + l2] : czero<C>();
   }
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
@@ -133,8 +135,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   fft_line<T, 1>(buf, logH, lane, tw, logP);
   if (line < nlines) {
     const T* rb = reinterpret_cast<const T*>(buf);
-    T* dst = out + (size_t)line * ldo;
-    for (int i = lane; i < n; i += G) dst[i] = rb[2 * spad(i >> 1) + (i & 1)];
+    io_t<T>* dst = out + (size_t)line * ldo;
+    for (int i = lane; i < n; i += G) dst[i] = to_io<T>(rb[2 * spad(i >> 1) + (i & 1)]);
   }
 }
 
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   C* line = data + (size_t)(valid ? col : 0) * ld;
-  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? line[i] : mk<C>(0, 0);
+  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? line[i] : czero<C>();
   __syncthreads();
   fft_line<T, -1>(buf, logP, lane, tw, logPtab);
   size_t lam_base;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   const int LS = sline(P);
   C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
-  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : mk<C>(0, 0);
+  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : czero<C>();
   __syncthreads();
   fft_line<T, -1>(buf, logP, lane, tw, logPtab);
   C* dst = out + g * gout;
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   const int total = TL * P;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int l2 = idx % TL, k = idx / TL;
-    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? src[(size_t)k * ldi + line0 + l2] : mk<C>(0, 0);
+    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? src[(size_t)k * ldi + line0 + l2] : czero<C>();
   }
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   const C* src = in + (size_t)(valid ? col : 0) * ld;
-  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : mk<C>(0, 0);
+  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : czero<C>();
   __syncthreads();
   fft_line<T, -1>(buf, logP, lane, tw, logPtab);
   if (valid) {
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
   }
   for (int k = lane; k < P; k += G) {
     const int kf = min(k, P - k);
-    buf[spad(k)] = valid ? lam[lam_base + (size_t)kf * lam_stride] * src[k] : mk<C>(0, 0);
+    buf[spad(k)] = valid ? lam[lam_base + (size_t)kf * lam_stride] * src[k] : czero<C>();
   }
   __syncthreads();
   fft_line<T, 1>(buf, logP, lane, tw, logPtab);
@@ -346,9 +348,23 @@ size_t apply_work_bytes(const Plan& p, int real_bytes) {
 // apply_work_bytes(p), symbols at stride lam_stride (0: all share one), skip flags at
 // stride skip_stride ints.
 template <typename T>
-static cudaError_t apply_launch_b(const Plan& p, int B, const T* u, T* y, size_t vstride, void* work, cudaStream_t s,
-                                  const int* skip, int skip_stride, cudaEvent_t const* ev, const T* lam_override,
-                                  size_t lam_stride) {
+static const cplx<T>* twiddle_table(const Plan& p, int r) {
+  if constexpr (std::is_same<T, double>::value) return p.tw64[r];
+  else if constexpr (std::is_same<T, float>::value) return p.tw32[r];
+  else return p.twdf[r];
+}
+
+template <typename T>
+static const T* symbol_table(const Plan& p) {
+  if constexpr (std::is_same<T, double>::value) return p.lam64;
+  else if constexpr (std::is_same<T, float>::value) return p.lam32;
+  else return p.lamdf;
+}
+
+template <typename T>
+static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
+                                  cudaStream_t s, const int* skip, int skip_stride, cudaEvent_t const* ev,
+                                  const T* lam_override, size_t lam_stride) {
   int stage = 0;
   auto mark = [&]() -> cudaError_t {
     if (ev && ev[stage]) {
@@ -362,13 +378,8 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const T* u, T* y, size_t
   const int eb = sizeof(C);
   const int budget = 96 * 1024;
   const C* tw[3];
-  for (int r = 0; r < 3; ++r) {
-    if constexpr (sizeof(T) == 8) tw[r] = reinterpret_cast<const C*>(p.tw64[r]);
-    else tw[r] = reinterpret_cast<const C*>(p.tw32[r]);
-  }
-  const T* lam;
-  if constexpr (sizeof(T) == 8) lam = p.lam64; else lam = p.lam32;
-  if (lam_override) lam = lam_override;
+  for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
+  const T* lam = lam_override ? lam_override : symbol_table<T>(p);
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -483,26 +494,36 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const T* u, T* y, size_t
 }
 
 template <typename T>
-cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
+cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s, const int* skip,
                          cudaEvent_t const* ev, const T* lam_override) {
   return apply_launch_b<T>(p, 1, u, y, 0, work, s, skip, 0, ev, lam_override, 0);
 }
 
 template <typename T>
-cudaError_t apply_batch_launch(const Plan& p, int B, const T* u, T* y, size_t vstride, void* work, cudaStream_t s,
-                               const int* skip, int skip_stride, const T* lam, size_t lam_stride) {
+cudaError_t apply_batch_launch(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
+                               cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride) {
   return apply_launch_b<T>(p, B, u, y, vstride, work, s, skip, skip_stride, nullptr, lam, lam_stride);
+}
+
+cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
+                    cudaEvent_t const* ev) {
+  if (p.df64) return apply_launch<dfl>(p, u, y, work, s, skip, ev, nullptr);
+  return apply_launch<double>(p, u, y, work, s, skip, ev, nullptr);
 }
 
 template cudaError_t apply_batch_launch<double>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
                                                 const int*, int, const double*, size_t);
 template cudaError_t apply_batch_launch<float>(const Plan&, int, const float*, float*, size_t, void*, cudaStream_t,
                                                const int*, int, const float*, size_t);
+template cudaError_t apply_batch_launch<dfl>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
+                                             const int*, int, const dfl*, size_t);
 
 template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
                                           cudaEvent_t const*, const double*);
 template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
                                          cudaEvent_t const*, const float*);
+template cudaError_t apply_launch<dfl>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
+                                       cudaEvent_t const*, const dfl*);
 
 size_t spectrum_elems(const Plan& p) {
   const size_t Hx1 = p.P[0] / 2 + 1;
@@ -516,10 +537,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
   const int eb = sizeof(C);
   const int budget = 96 * 1024;
   const C* tw[3];
-  for (int r = 0; r < 3; ++r) {
-    if constexpr (sizeof(T) == 8) tw[r] = reinterpret_cast<const C*>(p.tw64[r]);
-    else tw[r] = reinterpret_cast<const C*>(p.tw32[r]);
-  }
+  for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -572,10 +590,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
   const int eb = sizeof(C);
   const int budget = 96 * 1024;
   const C* tw[3];
-  for (int r = 0; r < 3; ++r) {
-    if constexpr (sizeof(T) == 8) tw[r] = reinterpret_cast<const C*>(p.tw64[r]);
-    else tw[r] = reinterpret_cast<const C*>(p.tw32[r]);
-  }
+  for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];

@@ -378,6 +378,19 @@ cudaError_t symbol_axes_launch(const Plan& p, double* lam, cudaStream_t s) {
 }  // namespace frlap
 
 namespace frlap {
+namespace {
+__global__ void k_to_df(const double* __restrict__ src, dfl* dst, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = df_from(src[i]);
+}
+}  // namespace
+
+// double-float copies of a symbol (n values) or of a twiddle table (n complex values = 2n doubles)
+cudaError_t to_df_launch(const double* src, dfl* dst, size_t n, cudaStream_t st) {
+  k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
 cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st) {
   k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lam64, lam32, n, s);
   return cudaGetLastError();

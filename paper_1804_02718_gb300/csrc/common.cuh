@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/frlap.h"
+#include "dfloat.cuh"
 
 namespace frlap {
 
@@ -31,10 +32,27 @@ frlap_status cuda_fail(cudaError_t e, const char* where);
 template <typename T> struct cplx_t;
 template <> struct cplx_t<float> { using type = float2; };
 template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<dfl> { using type = cdf; };
 template <typename T> using cplx = typename cplx_t<T>::type;
+
+// storage type of the real grid vectors and of the symbol for each compute type:
+// FP32 and FP64 compute and store in their own type; double-float computes in
+// dfl, reads and writes FP64 vectors, and keeps its symbol/twiddles as dfl.
+template <typename T> struct io_t_ { using type = T; };
+template <> struct io_t_<dfl> { using type = double; };
+template <typename T> using io_t = typename io_t_<T>::type;
+
+template <typename T> __device__ __forceinline__ T from_io(io_t<T> v) { return v; }
+template <> __device__ __forceinline__ dfl from_io<dfl>(double v) { return df_from(v); }
+template <typename T> __device__ __forceinline__ io_t<T> to_io(T v) { return v; }
+template <> __device__ __forceinline__ double to_io<dfl>(dfl v) { return df_to(v); }
 
 template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
   C c; c.x = a; c.y = b; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C czero() {
+  using T = decltype(C::x);
+  return mk<C>(T(0), T(0));
 }
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -81,6 +99,9 @@ struct Plan {
   float* lam32 = nullptr;      // symbol octant, FP32 (F32 and MIXED plans)
   double2* tw64[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i m / P_r), m < P_r
   float2* tw32[3] = {nullptr, nullptr, nullptr};
+  cdf* twdf[3] = {nullptr, nullptr, nullptr};      // the same twiddles as double-floats
+  dfl* lamdf = nullptr;        // symbol octant as double-floats (DF64 plans)
+  bool df64 = false;           // FP64-precision vectors are applied with double-float FFTs
   // workspace layout of one apply, in complex elements of the apply precision
   size_t s1_elems = 0, s2_elems = 0;
   cudaStream_t side = nullptr;  // internal stream for captured solver graphs
@@ -90,14 +111,18 @@ struct Plan {
 };
 
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
+// T = compute type (float, double or dfl); vectors are io_t<T>, symbol overrides are T
 template <typename T>
-cudaError_t apply_launch(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip,
+cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s, const int* skip,
                          cudaEvent_t const* ev = nullptr, const T* lam_override = nullptr);
+// FP64 vectors through the plan's FP64 engine (native double or double-float)
+cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
+                    cudaEvent_t const* ev = nullptr);
 size_t apply_work_bytes(const Plan& p, int real_bytes);
 // B same-shape instances in one launch per stage (see apply.cu)
 template <typename T>
-cudaError_t apply_batch_launch(const Plan& p, int B, const T* u, T* y, size_t vstride, void* work, cudaStream_t s,
-                               const int* skip, int skip_stride, const T* lam, size_t lam_stride);
+cudaError_t apply_batch_launch(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
+                               cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride);
 // forward half spectrum F R^T u (2D [kx][ky], 3D [kx][ky][kz]) and its multiplied inverse; same workspace as apply
 size_t spectrum_elems(const Plan& p);
 template <typename T>
@@ -112,6 +137,7 @@ size_t coeffs_scratch_bytes(int d, int Nmax);
 cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
 cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s);
 cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st);
+cudaError_t to_df_launch(const double* src, dfl* dst, size_t n, cudaStream_t st);
 // even DFT of the octant along every axis (used for both the operator and preconditioner symbols)
 cudaError_t symbol_axes_launch(const Plan& p, double* lam_oct, cudaStream_t s);
 

@@ -1,0 +1,66 @@
+// Double-float ("df64") arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant bits.  GB300 runs
+// FP32 at 62x its FP64 rate, so FFT stages in this format reach FP64-class
+// accuracy (about 1e-14 relative per operation) much faster than in FP64.
+// Error-free transformations (Knuth's two-sum, Dekker's fast two-sum, and the
+// FMA-based exact product) build the arithmetic:
+//   two_sum(a, b):      s = a + b, e = (a - (s - v)) + (b - v) with v = s - a
+//   fast_two_sum(a, b): s = a + b, e = b - (s - a)                (|a| >= |b|)
+//   two_prod(a, b):     p = a * b, e = fma(a, b, -p)
+// Addition is the "sloppy" variant (error bounded by eps (|a| + |b|)), which is
+// the bound that FFT error analysis uses anyway.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace frlap {
+
+struct dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+  // from a double (compile-time constants fold; at run time this costs FP64 ops)
+  __host__ __device__ explicit dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ explicit dfl(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+struct cdf {
+  dfl x, y;  // real, imaginary
+};
+
+__device__ __forceinline__ dfl df_from(double d) {
+  const float h = __double2float_rn(d);
+  return dfl(h, __double2float_rn(d - (double)h));
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return dfl(s, e);
+}
+
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return cdf{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return cdf{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cdf operator*(dfl s, cdf a) { return cdf{s * a.x, s * a.y}; }
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) { return cdf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cdf cmulc(cdf a, cdf b) { return cdf{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+
+}  // namespace frlap

@@ -46,19 +46,20 @@ __device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
 // exp(SIGN * 2 pi i m / 16) for the small set of m used inside the radix-16 kernel
 template <int SIGN, typename T>
 __device__ __forceinline__ cplx<T> w16(int m) {
-  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, r2 = (T)0.70710678118654752440;
-  T re, im;
+  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r2 = T(0.70710678118654752440);
+  const T one = T(1.0), zero = T(0.0);
+  T re = zero, im = zero;
   switch (m) {
-    case 0: re = 1; im = 0; break;
+    case 0: re = one; im = zero; break;
     case 1: re = c1; im = s1; break;
     case 2: re = r2; im = r2; break;
     case 3: re = s1; im = c1; break;
-    case 4: re = 0; im = 1; break;
+    case 4: re = zero; im = one; break;
     case 6: re = -r2; im = r2; break;
     case 9: re = -c1; im = -s1; break;
-    default: re = 0; im = 0; break;
+    default: break;
   }
-  return mk<cplx<T>>(re, (T)SIGN * im);
+  return mk<cplx<T>>(re, SIGN < 0 ? -im : im);
 }
 
 template <int SIGN, typename C>
@@ -67,12 +68,18 @@ __device__ __forceinline__ void dft8(C* v) {
   // even / odd halves
   dft4<SIGN>(v[0], v[2], v[4], v[6]);
   dft4<SIGN>(v[1], v[3], v[5], v[7]);
-  const T r2 = (T)0.70710678118654752440;
+  const T r2 = T(0.70710678118654752440);
   C o1 = v[3], o2 = v[5], o3 = v[7];
   // W8^1 = (1 + SIGN i)/sqrt2, W8^2 = SIGN i, W8^3 = (-1 + SIGN i)/sqrt2
-  C t1 = mk<C>(r2 * (o1.x - (T)SIGN * o1.y), r2 * (o1.y + (T)SIGN * o1.x));
+  C t1, t3;
+  if (SIGN < 0) {
+    t1 = mk<C>(r2 * (o1.x + o1.y), r2 * (o1.y - o1.x));
+    t3 = mk<C>(r2 * (o3.y - o3.x), -(r2 * (o3.y + o3.x)));
+  } else {
+    t1 = mk<C>(r2 * (o1.x - o1.y), r2 * (o1.y + o1.x));
+    t3 = mk<C>(-(r2 * (o3.x + o3.y)), r2 * (o3.x - o3.y));
+  }
   C t2 = mul_i<SIGN>(o2);
-  C t3 = mk<C>(r2 * (-o3.x - (T)SIGN * o3.y), r2 * (-o3.y + (T)SIGN * o3.x));
   C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
   v[0] = e0 + o0; v[4] = e0 - o0;
   v[1] = e1 + t1; v[5] = e1 - t1;

@@ -52,7 +52,7 @@ extern "C" frlap_status frlap_apply_noalloc(const frlap_plan* plan, const void* 
   if (f32)
     e = apply_launch<float>(*plan, (const float*)d_u, (float*)d_y, scratch, (cudaStream_t)stream, nullptr);
   else
-    e = apply_launch<double>(*plan, (const double*)d_u, (double*)d_y, scratch, (cudaStream_t)stream, nullptr);
+    e = apply64(*plan, (const double*)d_u, (double*)d_y, scratch, (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_noalloc");
   return FRLAP_OK;
 }

@@ -295,6 +295,14 @@ size_t vec_bytes(const Plan& p, int eb) { return align256(p.M * (size_t)eb); }
 
 }  // namespace
 
+// the apply of a CG in precision T: FP32 vectors through the FP32 engine, FP64
+// vectors through the plan's FP64 engine (native or double-float)
+template <typename T>
+static cudaError_t apply_T(const Plan& p, const T* u, T* y, void* work, cudaStream_t s, const int* skip) {
+  if constexpr (sizeof(T) == 8) return apply64(p, u, y, work, s, skip);
+  else return apply_launch<float>(p, u, y, work, s, skip);
+}
+
 // workspace of one (P)CG solve in precision T:
 // [apply work T][apply work FP32 (precond, T = double)][r][p][q][z][r32][z32][partials][state]
 size_t cg_work_bytes(const Plan& p, int eb) {
@@ -377,7 +385,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   k_set_state<<<1, 1, 0, st>>>(S, sigma, s);
   FRLAP_LAUNCH_CHECK("k_set_state");
   if (use_x0) {
-    cudaError_t e = apply_launch<T>(p, x, q, b.awork, st, nullptr);
+    cudaError_t e = apply_T<T>(p, x, q, b.awork, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "apply (initial residual)");
   }
   k_cg_init<T><<<kBlocks, kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
@@ -396,7 +404,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   int launched = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      cudaError_t e = apply_launch<T>(p, pv, q, b.awork, st, done);
+      cudaError_t e = apply_T<T>(p, pv, q, b.awork, st, done);
       if (e != cudaSuccess) return cuda_fail(e, "apply (CG)");
       k_cg_pq<T><<<kBlocks, kThreads, 0, st>>>(pv, q, n, b.partials, S);
       k_cg_update<T><<<kBlocks, kThreads, 0, st>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr);
@@ -429,7 +437,7 @@ static frlap_status true_residual(const Plan& p, const double* f, const double* 
   CgState* S = b.S;
   // the reduction ticket must start at zero (this workspace may not have run a CG yet)
   FRLAP_CUDA_TRY(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), st));
-  cudaError_t e = apply_launch<double>(p, x, q, b.awork, st, nullptr);
+  cudaError_t e = apply64(p, x, q, b.awork, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
   double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
   k_resid<<<kBlocks, kThreads, 0, st>>>(f, x, q, p.M, sigma, s, b.partials, &S->counter, out, rvec, rnorm_dev);
@@ -461,7 +469,7 @@ frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, d
     double* Ej = E + (size_t)j * p.M;
     k_err_from_snap<<<kBlocks, kThreads, 0, st>>>(Ej, x, p.M);
     FRLAP_LAUNCH_CHECK("k_err_from_snap");
-    cudaError_t e = apply_launch<double>(p, Ej, R + (size_t)j * p.M, b.awork, st, nullptr);
+    cudaError_t e = apply64(p, Ej, R + (size_t)j * p.M, b.awork, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "apply (training pairs)");
   }
   FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -481,14 +489,23 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
                             cudaStream_t st) {
   CgState hS;
   if (solver == FRLAP_SOLVE_CG) {
-    frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, maxit, 1, mu, work, st, &hS);
-    if (rc != FRLAP_OK) return rc;
+    // CG, then the true residual; if rounding left the true residual above rtol while the
+    // recursive one met it, restart from the current x (at most 4 restarts, within maxit)
+    int total = 0;
     double rel = 0.0;
-    rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
-    if (rc != FRLAP_OK) return rc;
-    if (iters) *iters = hS.iters;
+    frlap_status rc = FRLAP_OK;
+    for (int restart = 0; restart < 5; ++restart) {
+      rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, maxit - total, 1, mu, work, st, &hS);
+      if (rc != FRLAP_OK) return rc;
+      total += hS.iters;
+      rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
+      if (rc != FRLAP_OK) return rc;
+      if (hS.status != FRLAP_OK || rel <= rtol || total >= maxit || hS.iters == 0) break;
+    }
+    if (iters) *iters = total;
     if (relres) *relres = rel;
     if (hS.status != FRLAP_OK) return fail((frlap_status)hS.status, "CG stopped early (see status code)");
+    if (!(rel <= rtol)) return fail(FRLAP_ENOCONV, "true residual above rtol (rounding floor of the apply)");
     return FRLAP_OK;
   }
   // iterative refinement: x <- x + ||r|| * CG32(A, r/||r||)

@@ -97,6 +97,14 @@ def test_apply_fp64_matches_oracle(frlap, d, Ns, alpha):
 
 
 @pytest.mark.parametrize("d,Ns,alpha", APPLY_CASES)
+def test_apply_df64_matches_oracle(frlap, d, Ns, alpha):
+    """Double-float FFT stages (FRLAP_DF64): same FP64 tolerance as the native FP64 apply."""
+    u = inp.normal_field(Ns, seed=3)
+    err, *_ = _apply_case(frlap, d, Ns, alpha, u, frlap.FRLAP_DF64)
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("d,Ns,alpha", APPLY_CASES)
 def test_apply_fp32_matches_oracle(frlap, d, Ns, alpha):
     u = inp.normal_field(Ns, seed=1)
     err, *_ = _apply_case(frlap, d, Ns, alpha, u, frlap.FRLAP_F32)
@@ -131,7 +139,7 @@ def test_apply_linear_and_symmetric(frlap):
     assert torch.dot(Au.flatten(), u.flatten()).item() > 0
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (3, 1e-12)])
 def test_apply_2047_full_size(frlap, prec, tol):
     """2D 2047^2, alpha = 1.5 (the throughput workload): against the NumPy-FFT oracle, plus sampled rows
     of the dense definition."""
@@ -151,7 +159,7 @@ def test_apply_2047_full_size(frlap, prec, tol):
         assert abs(y[r] - v) <= tol * op.lam_max * np.linalg.norm(u) / math.sqrt(u.size) * 50
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (3, 1e-12)])
 def test_apply_255_cubed_sampled_rows(frlap, prec, tol):
     """3D 255^3, alpha = 1.0: sampled rows of the dense definition (each row is a full 255^3 sum)."""
     Ns, alpha = (256, 256, 256), 1.0

@@ -39,28 +39,30 @@ def test_cg_config0_poisson_f_equals_one(frlap):
     assert abs(it - it_ref) <= 2
 
 
-@pytest.mark.parametrize("d,Ns,alpha", [(2, (48, 40), 0.7), (3, (16, 16, 16), 1.9), (3, (12, 10, 8), 1.0)])
-def test_cg_gaussian_sum(frlap, d, Ns, alpha):
+@pytest.mark.parametrize("d,Ns,alpha,prec", [(2, (48, 40), 0.7, 0), (3, (16, 16, 16), 1.9, 0),
+                                              (3, (12, 10, 8), 1.0, 0), (2, (96, 64), 1.6, 3), (3, (20, 20, 20), 1.4, 3)])
+def test_cg_gaussian_sum(frlap, d, Ns, alpha, prec):
     h = 2.0 / max(Ns)
     a, c = _coef(d, alpha, h, max(Ns)), scheme.c_d_alpha(d, alpha)
     f = inp.gaussian_sum_field(Ns, h, seed=1)
     op = fast.FastOperator(a, c, f.shape)
     x_ref, _, rel_ref = solvers.cg(op, f, rtol=1e-13)
-    plan = frlap.Plan(d, alpha, h, Ns)
+    plan = frlap.Plan(d, alpha, h, Ns, prec=prec)
     x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f), rtol=1e-12)
     assert code == 0 and rel <= 1e-12
     assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
 
 
-@pytest.mark.parametrize("d,Ns,alpha", [(2, (128, 128), 1.8), (3, (24, 24, 24), 1.2)])
-def test_iterative_refinement_reaches_fp64_solution(frlap, d, Ns, alpha):
+@pytest.mark.parametrize("d,Ns,alpha,prec", [(2, (128, 128), 1.8, 2), (3, (24, 24, 24), 1.2, 2),
+                                              (2, (128, 128), 1.5, 4)])
+def test_iterative_refinement_reaches_fp64_solution(frlap, d, Ns, alpha, prec):
     """FP32 inner CG inside FP64 refinement: the final solution is within 1e-10 of the FP64 solution."""
     h = 2.0 / max(Ns)
     a, c = _coef(d, alpha, h, max(Ns)), scheme.c_d_alpha(d, alpha)
     f = inp.gaussian_sum_field(Ns, h, seed=3)
     op = fast.FastOperator(a, c, f.shape)
     x_ref, _, _ = solvers.cg(op, f, rtol=1e-13)
-    plan = frlap.Plan(d, alpha, h, Ns, prec=frlap.FRLAP_MIXED)
+    plan = frlap.Plan(d, alpha, h, Ns, prec=prec)
     x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f), rtol=1e-11, solver=frlap.FRLAP_SOLVE_IR,
                                              inner_rtol=1e-4)
     assert code == 0 and rel <= 1e-11
