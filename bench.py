@@ -2,15 +2,19 @@
 """Throughput of the FFT Toeplitz apply of the fractional-Laplacian scheme on one GB300.
 
 Default workload: 2D, alpha = 1.5, Omega = (-1,1)^2, h = 2/2048 (2047 x 2047 interior
-unknowns), FP64 apply y = A u through libfrlap (the 2D throughput case of the 3D
-FP64 CG configuration).  One step = a batch of 8 applies to 8 distinct seeded
+unknowns), an FP64-precision apply y = A u through libfrlap (the 2D throughput case
+of the 3D FP64 CG configuration), computed by the double-float FFT engine
+(FP64 vectors; FFT stages in FP32 pairs, parity 1e-12 normwise against the FP64
+oracle, like native FP64).  One step = a batch of 8 applies to 8 distinct seeded
 N(0,1) vectors (268 MB of inputs, more than the 129 MB L2).  Reported: apply
 unknowns/s over all ranks, the per-kernel roofline of the dominant kernel, the
 same metric end to end through host buffers, and the CPU oracle timed on the
-host cores.  Extra lines (FP32 apply, 3D 255^3 applies, CG solve times) are
-measured after the timed region.
+host cores.  Extra lines (native FP64 and FP32 applies, 3D 255^3 applies, CG
+solve times) are measured after the timed region.  `--suite solvers` instead runs
+the solver configurations (time to 1e-10 for plain CG, refinement, Strang and
+learned preconditioning; the batched Allen-Cahn launch) and prints them.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl frlap|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl frlap|reference] [--prec df64|f64|f32]
 """
 from __future__ import annotations
 
@@ -50,6 +54,9 @@ def peaks():
 # FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+# double-float: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the FP32
+# instructions one FP64-equivalent FFT flop costs (add 11, mul 7; FFT mix 2 adds : 1 mul -> 29/3)
+DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / (29.0 / 3.0) / 1e12
 
 
 class ClockSampler:
@@ -243,7 +250,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="frlap", choices=["frlap", "reference"])
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "df64"])
+    ap.add_argument("--prec", default="df64", choices=["f64", "f32", "df64"])
+    ap.add_argument("--suite", default="apply", choices=["apply", "solvers"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -254,6 +262,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.suite == "solvers":
+        run_solver_suite(args)
         return
 
     import torch
@@ -305,12 +316,12 @@ def main():
                 "peak_source": "FP64 pipe from unit count x max clock (DESIGN.md)",
                 "flops_per_launch": sf[dom]}
     elif args.prec == "df64":
-        # FFT flops counted as FP64-equivalent operations, each executed as a double-float
-        # sequence on the FP32 pipes; peak = the FP32 pipe (no double-float op is a single FP32 op)
+        # FFT flops counted as FP64-equivalent operations, each executed as a double-float sequence
+        # on the FP32 pipes; peak = FP32 issue rate / FP32 instructions per FP64-equivalent flop
         ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe from unit count x max clock (DESIGN.md); double-float runs on FP32 pipes",
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": DF64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / DF64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP32 issue rate from unit counts x max clock / double-float cost (DESIGN.md)",
                 "flops_per_launch": sf[dom]}
     else:
         ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
@@ -425,6 +436,76 @@ def run_extras(fl, torch, args):
         del plan
         torch.cuda.empty_cache()
     return out
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out
+
+
+def run_solver_suite(args):
+    """Time to 1e-10 (true relative residual) for the solver configurations, one GPU."""
+    import torch
+    import paper_1804_02718_gb300 as fl
+    from paper_1804_02718_gb300 import build as _build, learned
+    _build.build()
+    out = {"suite": "solvers", "rtol": 1e-10}
+    # learned network: trained once on plain-CG pairs (2D 63^2 and 3D 15^3, alpha 0.5..1.9)
+    t_train, params2 = _timed(lambda: learned.train(
+        [learned.PairSet(2, al, 64, [inp.gaussian_sum_field((64, 64), 2 / 64, seed=s) for s in (6, 7)], K=400)
+         for al in (0.5, 0.9, 1.3, 1.7, 1.9)], steps=400, batch=8, lr=2e-3, seed=0)[0])
+    t_train3, params3 = _timed(lambda: learned.train(
+        [learned.PairSet(3, al, 16, [inp.gaussian_sum_field((16, 16, 16), 2 / 16, seed=s) for s in (6, 7)], K=300)
+         for al in (0.5, 0.9, 1.3, 1.7, 1.9)], steps=300, batch=8, lr=2e-3, seed=0)[0])
+    out["train_s"] = {"2d": t_train, "3d": t_train3}
+
+    def solve_row(d, N, alpha, seed, variants):
+        h = 2.0 / N
+        f = torch.from_numpy(inp.gaussian_sum_field((N,) * d, h, seed=seed)).cuda()
+        row = {}
+        for name, prec, solver, pre in variants:
+            plan = fl.Plan(d, alpha, h, (N,) * d, prec=prec)
+            if pre == fl.FRLAP_PRECOND_STRANG:
+                fl.frlap_precond_strang(plan)
+            elif pre == fl.FRLAP_PRECOND_LEARNED:
+                learned.install(plan, params2 if d == 2 else params3)
+            plan.workspace(fl.FRLAP_OP_PCG)
+            dt, (x, it, rel, code) = _timed(lambda: fl.frlap_pcg_solve(plan, f, rtol=1e-10, solver=solver,
+                                                                     precond=pre, inner_rtol=1e-4,
+                                                                     raise_on_error=False))
+            row[name] = {"s": dt, "iters": it, "relres": rel, "status": code}
+            del plan
+            torch.cuda.empty_cache()
+        return row
+
+    F64, DF, MX = fl.FRLAP_F64, fl.FRLAP_DF64, fl.FRLAP_MIXED_DF64
+    CG, IR = fl.FRLAP_SOLVE_CG, fl.FRLAP_SOLVE_IR
+    NONE, STR, LRN = fl.FRLAP_PRECOND_NONE, fl.FRLAP_PRECOND_STRANG, fl.FRLAP_PRECOND_LEARNED
+    full = [("plain_cg_fp64", F64, CG, NONE), ("plain_cg_df64", DF, CG, NONE), ("pcg_strang_df64", DF, CG, STR),
+            ("pcg_learned_df64", DF, CG, LRN), ("ir_learned_fp32inner", MX, IR, LRN)]
+    fast = [("pcg_strang_df64", DF, CG, STR), ("pcg_learned_df64", DF, CG, LRN), ("ir_strang_fp32inner", MX, IR, STR),
+            ("ir_learned_fp32inner", MX, IR, LRN)]
+    out["2d_2047_alpha1.5"] = solve_row(2, 2048, 1.5, 1, full)
+    for al in (0.5, 1.0, 1.5, 1.9):
+        out[f"3d_255_alpha{al}"] = solve_row(3, 256, al, 1, full if al in (1.0, 1.9) else fast)
+    for al in (1.2, 1.8):
+        out[f"2d_4095_alpha{al}"] = solve_row(2, 4096, al, 3, fast + [("plain_cg_df64", DF, CG, NONE)])
+        out[f"3d_511_alpha{al}"] = solve_row(3, 512, al, 3, fast)
+    # batched Allen-Cahn: 64 instances, alpha ~ U[1.2,1.9], grids 255/511/1023, 200 steps, one graph launch
+    batch = inp.allen_cahn_batch()
+    plans = [fl.Plan(2, al, 2.0 / (n + 1), (n + 1, n + 1), prec=fl.FRLAP_DF64) for al, n, _ in batch]
+    us = [torch.from_numpy(u0).cuda() for _, _, u0 in batch]
+    dt, (its, st, code) = _timed(lambda: fl.frlap_allen_cahn_batch(plans, us, 1e-3, 0.05, 200, rtol=1e-10,
+                                                                   raise_on_error=False))
+    unknown_steps = sum(u.numel() for u in us) * 200
+    out["allen_cahn_batch_64x200"] = {"s": dt, "status": code, "total_cg_iters": int(sum(its)),
+                                     "unknown_steps_per_s": unknown_steps / dt,
+                                     "max_abs_u": max(float(u.abs().max().item()) for u in us)}
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

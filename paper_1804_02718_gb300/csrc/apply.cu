@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   // real sample i is component (i & 1) of complex element i / 2 (even/odd packing)
   for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(src[i]) : T(0.0);
   __syncthreads();
-  fft_line<T, -1>(buf, logH, lane, tw, logP);
+  fft_line<T, -1, true, false>(buf, logH, lane, tw, logP);
   // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
   for (int k = lane; k <= H / 2; k += G) {
     const int km = H - k;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
     }
   }
   __syncthreads();
-  fft_line<T, 1>(buf, logH, lane, tw, logP);
+  fft_line<T, 1, false, true>(buf, logH, lane, tw, logP);
   if (line < nlines) {
     const T* rb = reinterpret_cast<const T*>(buf);
     io_t<T>* dst = out + (size_t)line * ldo;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
   C* line = data + (size_t)(valid ? col : 0) * ld;
   for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? line[i] : czero<C>();
   __syncthreads();
-  fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+  fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
   size_t lam_base;
   int lam_stride;
   if (map.d == 2) {
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
     buf[spad(k)] = lam[lam_base + (size_t)kf * lam_stride] * buf[spad(k)];
   }
   __syncthreads();
-  fft_line<T, 1>(buf, logP, lane, tw, logPtab);
+  fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
   if (valid)
     for (int i = lane; i < n; i += G) line[i] = buf[spad(i)];
 }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
   for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : czero<C>();
   __syncthreads();
-  fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+  fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
   C* dst = out + g * gout;
   const int total = TL * P;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   }
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
-  fft_line<T, 1>(buf, logP, lane, tw, logPtab);
+  fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
   if (line < nlines) {
     C* dst = out + g * gout + (size_t)line * ldo;
     for (int i = lane; i < n; i += G) dst[i] = buf[spad(i)];
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
   const C* src = in + (size_t)(valid ? col : 0) * ld;
   for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : czero<C>();
   __syncthreads();
-  fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+  fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
   if (valid) {
     C* dst = out + (size_t)col * ldo;
     for (int i = lane; i < P; i += G) dst[i] = buf[spad(i)];
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
     buf[spad(k)] = valid ? lam[lam_base + (size_t)kf * lam_stride] * src[k] : czero<C>();
   }
   __syncthreads();
-  fft_line<T, 1>(buf, logP, lane, tw, logPtab);
+  fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
   if (valid) {
     C* dst = out + (size_t)col * ldo;
     for (int i = lane; i < n; i += G) dst[i] = buf[spad(i)];

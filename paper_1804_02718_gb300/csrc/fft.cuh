@@ -16,6 +16,8 @@
 // Ptab / L.  SIGN = -1 is the forward transform, +1 the (unnormalised) inverse.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace frlap {
@@ -62,12 +64,10 @@ __device__ __forceinline__ cplx<T> w16(int m) {
   return mk<cplx<T>>(re, SIGN < 0 ? -im : im);
 }
 
+// radix-2 combine of dft8 after the even (v[0,2,4,6]) and odd (v[1,3,5,7]) length-4 DFTs
 template <int SIGN, typename C>
-__device__ __forceinline__ void dft8(C* v) {
+__device__ __forceinline__ void dft8_combine(C* v) {
   using T = decltype(C::x);
-  // even / odd halves
-  dft4<SIGN>(v[0], v[2], v[4], v[6]);
-  dft4<SIGN>(v[1], v[3], v[5], v[7]);
   const T r2 = T(0.70710678118654752440);
   C o1 = v[3], o2 = v[5], o3 = v[7];
   // W8^1 = (1 + SIGN i)/sqrt2, W8^2 = SIGN i, W8^3 = (-1 + SIGN i)/sqrt2
@@ -88,16 +88,26 @@ __device__ __forceinline__ void dft8(C* v) {
 }
 
 template <int SIGN, typename C>
-__device__ __forceinline__ void dft16(C* v) {
+__device__ __forceinline__ void dft8(C* v) {
+  // even / odd halves
+  dft4<SIGN>(v[0], v[2], v[4], v[6]);
+  dft4<SIGN>(v[1], v[3], v[5], v[7]);
+  dft8_combine<SIGN>(v);
+}
+
+// twiddles by W16^{j2 k1} and the length-4 DFTs over j2 (second half of dft16)
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft16_tail(C* v) {
   using T = decltype(C::x);
-  // x[4 j1 + j2]: length-4 DFTs over j1 for each j2
-#pragma unroll
-  for (int j2 = 0; j2 < 4; ++j2) dft4<SIGN>(v[j2], v[4 + j2], v[8 + j2], v[12 + j2]);
-  // now v[4 k1 + j2] = A_{j2}[k1]; twiddle by W16^{j2 k1}
+  // v[4 k1 + j2] = A_{j2}[k1]; twiddle by W16^{j2 k1}
 #pragma unroll
   for (int k1 = 1; k1 < 4; ++k1)
 #pragma unroll
-    for (int j2 = 1; j2 < 4; ++j2) v[4 * k1 + j2] = cmul(v[4 * k1 + j2], w16<SIGN, T>(j2 * k1));
+    for (int j2 = 1; j2 < 4; ++j2) {
+      const int m = j2 * k1;
+      if (m == 4) v[4 * k1 + j2] = mul_i<SIGN>(v[4 * k1 + j2]);  // W16^4 = SIGN i
+      else v[4 * k1 + j2] = cmul(v[4 * k1 + j2], w16<SIGN, T>(m));
+    }
   // length-4 DFTs over j2 for each k1: X[k1 + 4 k2]
   C out[16];
 #pragma unroll
@@ -110,20 +120,59 @@ __device__ __forceinline__ void dft16(C* v) {
   for (int i = 0; i < 16; ++i) v[i] = out[i];
 }
 
-template <int R, int SIGN, typename C>
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft16(C* v) {
+  // x[4 j1 + j2]: length-4 DFTs over j1 for each j2
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) dft4<SIGN>(v[j2], v[4 + j2], v[8 + j2], v[12 + j2]);
+  dft16_tail<SIGN>(v);
+}
+
+// dft16 of an input whose upper half x[8..15] is zero (the zero-padded first stage)
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft16_zin(C* v) {
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) {
+    const C a = v[j2], b = v[4 + j2];
+    const C bi = mul_i<SIGN>(b);
+    v[j2] = a + b;
+    v[4 + j2] = a + bi;
+    v[8 + j2] = a - b;
+    v[12 + j2] = a - bi;
+  }
+  dft16_tail<SIGN>(v);
+}
+
+// dft8 of an input whose upper half x[4..7] is zero
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft8_zin(C* v) {
+  // even and odd quarter-length DFTs with two nonzero inputs each, then the radix-2 combine of dft8
+  const C e0 = v[0], e1 = v[2], o0 = v[1], o1 = v[3];
+  const C e1i = mul_i<SIGN>(e1), o1i = mul_i<SIGN>(o1);
+  v[0] = e0 + e1; v[2] = e0 + e1i; v[4] = e0 - e1; v[6] = e0 - e1i;
+  v[1] = o0 + o1; v[3] = o0 + o1i; v[5] = o0 - o1; v[7] = o0 - o1i;
+  dft8_combine<SIGN>(v);
+}
+
+template <int R, int SIGN, bool ZIN, typename C>
 __device__ __forceinline__ void dftR(C* v) {
   if constexpr (R == 2) dft2<SIGN>(v[0], v[1]);
   else if constexpr (R == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
-  else if constexpr (R == 8) dft8<SIGN>(v);
-  else dft16<SIGN>(v);
+  else if constexpr (R == 8) {
+    if constexpr (ZIN) dft8_zin<SIGN>(v); else dft8<SIGN>(v);
+  } else {
+    if constexpr (ZIN) dft16_zin<SIGN>(v); else dft16<SIGN>(v);
+  }
 }
 
-// The 15 twiddles W^r, r = 1..15, of one radix-16 butterfly (W = tw[idx1]).  FP64 loads
-// every power from the table (the FP64 pipe is the bottleneck there); FP32 loads
-// W, W^4 and W^8 and forms the rest with at most three chained products.
+// Twiddles W^r, r = 1..15, of one radix-16 butterfly (W = tw[k << sh]), loaded after the
+// stage barrier.  FP64 and double-float load every power from the table (products would
+// cost more than the loads there); FP32 loads W, W^4 and W^8 and forms the rest with at
+// most three chained products.  (Issuing these loads before the barrier was measured
+// slower: the extra live registers cost more than the hidden latency.)
 template <typename T>
 __device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict__ tw, int k, int sh) {
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (!std::is_same<T, float>::value) {
 #pragma unroll
     for (int r = 1; r < 16; ++r) w[r] = tw[(r * k) << sh];
   } else {
@@ -146,8 +195,10 @@ __device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict
 }
 
 // One Stockham stage of radix R on a line of length L = 2^logL held in `buf`
-// (padded layout, see spad).
-template <typename T, int R, int SIGN>
+// (padded layout, see spad).  ZIN: the input's upper half is zero (first stage of a
+// zero-padded forward transform; those elements are not read).  HOUT: only the lower
+// half of the output is used later (last stage of a cropped inverse transform).
+template <typename T, int R, int SIGN, bool ZIN, bool HOUT>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int logNs, int lane,
                                           const cplx<T>* __restrict__ tw, int logPtab) {
   using C = cplx<T>;
@@ -155,12 +206,15 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
   constexpr int LOGR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
   const int G = 1 << (logL - 4);
   const int LR = 1 << (logL - LOGR);
+  // W_{Ns R}^{r k} = tw[r k Ptab / (Ns R)]
+  const int sh = logPtab - logNs - LOGR;
   C v[E];
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int j = lane + b * G;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b * R + r] = buf[spad(j + r * LR)];
+    for (int r = 0; r < R; ++r)
+      v[b * R + r] = (ZIN && 2 * r >= R) ? czero<C>() : buf[spad(j + r * LR)];
   }
   __syncthreads();
 #pragma unroll
@@ -168,8 +222,6 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
     const int j = lane + b * G;
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      // W_{Ns R}^{r k} = tw[r k Ptab / (Ns R)]
-      const int sh = logPtab - logNs - LOGR;
       if constexpr (R == 16) {
         C w[16];
         twiddles16<T>(w, tw, k, sh);
@@ -178,32 +230,59 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
       } else {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C w = tw[(r * k) << sh];
-          v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], w) : cmulc(v[b * R + r], w);
+          const C wr = tw[(r * k) << sh];
+          v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], wr) : cmulc(v[b * R + r], wr);
         }
       }
     }
-    dftR<R, SIGN>(&v[b * R]);
+    dftR<R, SIGN, ZIN>(&v[b * R]);
     const int o = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[spad(o + r * Ns)] = v[b * R + r];
+    for (int r = 0; r < R; ++r)
+      if (!HOUT || 2 * r < R) buf[spad(o + r * Ns)] = v[b * R + r];
   }
   __syncthreads();
 }
 
 // Full transform of the line in `buf` (length 2^logL >= 16).  Every thread of the
 // CTA must call this with the same logL (the stages contain CTA barriers).
-template <typename T, int SIGN>
+// ZIN: the upper half of the input line is zero (its slots are neither read nor
+// needed); HOUT: only the lower half of the output is read afterwards (the upper
+// half of the buffer is left stale).  The last stage is always radix 16.
+template <typename T, int SIGN, bool ZIN_ = false, bool HOUT_ = false>
 __device__ __forceinline__ void fft_line(cplx<T>* buf, int logL, int lane, const cplx<T>* __restrict__ tw,
                                          int logPtab) {
+  // The pruned first/last stages pay off where arithmetic is the bottleneck (FP64); for
+  // FP32 and double-float they only add code (three copies of the radix-16 stage instead
+  // of one loop body), which measured slower, so they are used for FP64 only.
+  constexpr bool ZIN = ZIN_ && std::is_same<T, double>::value;
+  constexpr bool HOUT = HOUT_ && std::is_same<T, double>::value;
   const int rem = logL & 3;
   int logNs = 0;
-  if (rem == 1) { fft_stage<T, 2, SIGN>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 1; }
-  else if (rem == 2) { fft_stage<T, 4, SIGN>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 2; }
-  else if (rem == 3) { fft_stage<T, 8, SIGN>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 3; }
-  while (logNs < logL) {
-    fft_stage<T, 16, SIGN>(buf, logL, 1 << logNs, logNs, lane, tw, logPtab);
-    logNs += 4;
+  if (rem == 1) { fft_stage<T, 2, SIGN, ZIN, false>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 1; }
+  else if (rem == 2) { fft_stage<T, 4, SIGN, ZIN, false>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 2; }
+  else if (rem == 3) { fft_stage<T, 8, SIGN, ZIN, false>(buf, logL, 1, 0, lane, tw, logPtab); logNs = 3; }
+  if constexpr (!ZIN && !HOUT) {
+    while (logNs < logL) {
+      fft_stage<T, 16, SIGN, false, false>(buf, logL, 1 << logNs, logNs, lane, tw, logPtab);
+      logNs += 4;
+    }
+    return;
+  } else {
+    if (logNs == 0) {
+      // the first stage is radix 16
+      if (logL == 4) {
+        fft_stage<T, 16, SIGN, ZIN, HOUT>(buf, logL, 1, 0, lane, tw, logPtab);
+        return;
+      }
+      fft_stage<T, 16, SIGN, ZIN, false>(buf, logL, 1, 0, lane, tw, logPtab);
+      logNs = 4;
+    }
+    while (logNs + 4 < logL) {
+      fft_stage<T, 16, SIGN, false, false>(buf, logL, 1 << logNs, logNs, lane, tw, logPtab);
+      logNs += 4;
+    }
+    fft_stage<T, 16, SIGN, false, HOUT>(buf, logL, 1 << logNs, logNs, lane, tw, logPtab);
   }
 }
 
