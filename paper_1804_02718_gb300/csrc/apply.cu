@@ -321,11 +321,12 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
 
 // Lines per CTA for a line of `len` complex slots: as many as fit in
 // `budget` bytes of shared memory and 1024 threads (at least one).
-// (every apply kernel is compiled for at most 512 threads per CTA)
+// (every apply kernel is compiled for at most 512 threads per CTA; CTAs of at most 256
+// threads measured fastest: more independent CTAs per SM overlap their phases)
 int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
   int tl = budget / (len * elem_bytes);
   tl = tl < 1 ? 1 : tl;
-  while (tl > 1 && tl * G > 512) --tl;
+  while (tl > 1 && tl * G > 256) --tl;
   if (tl > max_lines) tl = max_lines;
   return tl < 1 ? 1 : tl;
 }

@@ -209,14 +209,21 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
   // W_{Ns R}^{r k} = tw[r k Ptab / (Ns R)]
   const int sh = logPtab - logNs - LOGR;
   C v[E];
+  // padded addresses: element i sits at i + i/16.  A stride that is a multiple of 16
+  // elements keeps the same in-group offset, so address = base + r * (stride * 17/16).
+  const bool lr16 = (LR & 15) == 0;
+  const int lstep = LR + (LR >> 4);
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int j = lane + b * G;
+    const int base = spad(j);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      v[b * R + r] = (ZIN && 2 * r >= R) ? czero<C>() : buf[spad(j + r * LR)];
+      v[b * R + r] = (ZIN && 2 * r >= R) ? czero<C>() : buf[lr16 ? base + r * lstep : spad(j + r * LR)];
   }
   __syncthreads();
+  const bool ns16 = (Ns & 15) == 0;
+  const int sstep = Ns + (Ns >> 4);
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int j = lane + b * G;
@@ -237,9 +244,12 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
     }
     dftR<R, SIGN, ZIN>(&v[b * R]);
     const int o = (j - k) * R + k;
+    const int obase = spad(o);
+    // Ns = 1: o is a multiple of R and o + r never crosses a 16-element group (R divides 16)
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (!HOUT || 2 * r < R) buf[spad(o + r * Ns)] = v[b * R + r];
+      if (!HOUT || 2 * r < R)
+        buf[Ns == 1 ? obase + r : (ns16 ? obase + r * sstep : spad(o + r * Ns))] = v[b * R + r];
   }
   __syncthreads();
 }
