@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   T* rb = reinterpret_cast<T*>(buf);
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // real sample i is component (i & 1) of complex element i / 2 (even/odd packing)
-  for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(src[i]) : T(0.0);
+  for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(src[i]) : T(0);
   __syncthreads();
   fft_line<T, -1, true, false>(buf, logH, lane, tw, logP);
   // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
     const int km = H - k;
     const C zk = buf[spad(k)];
     const C zm = buf[spad(km & (H - 1))];
-    const T half = T(0.5);
+    constexpr T half = T(0.5);
     {
       const C a = zk, b = conjg(zm);
       const C xe = half * (a + b);

@@ -19,9 +19,9 @@ struct dfl {
   float hi, lo;
   dfl() = default;
   __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
-  // from a double (compile-time constants fold; at run time this costs FP64 ops)
-  __host__ __device__ explicit dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
-  __host__ __device__ explicit dfl(int v) : hi((float)v), lo(0.0f) {}
+  // from a double: for constants only (constexpr, folded at compile time)
+  __host__ __device__ constexpr explicit dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr explicit dfl(int v) : hi((float)v), lo(0.0f) {}
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
@@ -29,10 +29,26 @@ struct cdf {
   dfl x, y;  // real, imaginary
 };
 
+// Split a double into hi + lo with integer operations only (GB300's FP64 and conversion
+// pipes are narrow): hi keeps the sign, exponent and top 23 fraction bits (truncated),
+// lo is the remaining 29 fraction bits rounded to a float, so hi + lo equals d to about
+// 2^-47 relative.  Zero, subnormal, huge and non-finite values take the conversion path.
 __device__ __forceinline__ dfl df_from(double d) {
-  const float h = __double2float_rn(d);
-  return dfl(h, __double2float_rn(d - (double)h));
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ffu);  // biased exponent
+  if (e < 1023 - 70 || e > 1023 + 120) {  // fast path keeps both parts normal floats
+    const float h = __double2float_rn(d);
+    return dfl(h, __double2float_rn(d - (double)h));
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long frac = b & 0xfffffffffffffull;
+  const unsigned hb = sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(frac >> 29);
+  const unsigned low = (unsigned)(frac & 0x1fffffffu);                    // weight 2^(e - 1023 - 52)
+  const float scale = __int_as_float((e - 1023 - 52 + 127) << 23);         // 2^(e - 1075), normal here
+  const float lo = __uint2float_rn(low) * scale;
+  return dfl(__int_as_float((int)hb), sign ? -lo : lo);
 }
+// hi + lo as a double (widening on the bits measured slower than the conversion instructions here)
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
 
 __device__ __forceinline__ dfl fast_two_sum(float a, float b) {

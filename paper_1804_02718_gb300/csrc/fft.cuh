@@ -48,8 +48,8 @@ __device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
 // exp(SIGN * 2 pi i m / 16) for the small set of m used inside the radix-16 kernel
 template <int SIGN, typename T>
 __device__ __forceinline__ cplx<T> w16(int m) {
-  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r2 = T(0.70710678118654752440);
-  const T one = T(1.0), zero = T(0.0);
+  constexpr T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r2 = T(0.70710678118654752440);
+  constexpr T one = T(1.0), zero = T(0.0);
   T re = zero, im = zero;
   switch (m) {
     case 0: re = one; im = zero; break;
@@ -68,7 +68,7 @@ __device__ __forceinline__ cplx<T> w16(int m) {
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft8_combine(C* v) {
   using T = decltype(C::x);
-  const T r2 = T(0.70710678118654752440);
+  constexpr T r2 = T(0.70710678118654752440);
   C o1 = v[3], o2 = v[5], o3 = v[7];
   // W8^1 = (1 + SIGN i)/sqrt2, W8^2 = SIGN i, W8^3 = (-1 + SIGN i)/sqrt2
   C t1, t3;
