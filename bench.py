@@ -54,6 +54,10 @@ def peaks():
 # FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+# DRAM traffic per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised in profiles/k_colmul_2d_2047.md; None where the kernel changed since
+MEASURED_TRAFFIC = {("colmul", "df64"): 116.4e6, ("colmul", "f32"): 50.5e6}
+
 # double-float: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the FP32
 # instructions one FP64-equivalent FFT flop costs (add 11, mul 7; FFT mix 2 adds : 1 mul -> 29/3)
 DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / (29.0 / 3.0) / 1e12
@@ -320,13 +324,15 @@ def main():
         # on the FP32 pipes; peak = FP32 issue rate / FP32 instructions per FP64-equivalent flop
         ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
         roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": DF64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / DF64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / DF64_PEAK_TFLOPS,
+                "traffic": MEASURED_TRAFFIC.get((names[dom], args.prec)),
                 "peak_source": "FP32 issue rate from unit counts x max clock / double-float cost (DESIGN.md)",
                 "flops_per_launch": sf[dom]}
     else:
         ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom]}
+                "frac": ach / hbm, "traffic": MEASURED_TRAFFIC.get((names[dom], args.prec)),
+                "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom]}
     apply_ms = sum(stage_ms)
     model_bytes = sum(sb)
     kernels = {nm: {"ms": round(ms, 5), "model_GBps": round(b / (ms / 1e3) / 1e9, 1),
