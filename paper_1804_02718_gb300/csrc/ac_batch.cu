@@ -357,7 +357,7 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
         e = cudaMemcpyAsync(g.u + k * g.vs, u[g.idx[k]], p.M * 8, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(g.lam + k * (align256(p.lam_count * 8) / 8),
-                              p.df64 ? static_cast<const void*>(pi->lamdf) : static_cast<const void*>(pi->lam64),
+                              p.df64 ? static_cast<const void*>(pi->lamdf) : static_cast<const void*>(pi->lamL64),
                               p.lam_count * 8, cudaMemcpyDeviceToDevice, s);
       }
     }

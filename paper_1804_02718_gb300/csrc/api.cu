@@ -109,6 +109,7 @@ frlap_status frlap_coeffs(int d, double alpha, double gamma, double h, const int
 frlap_status frlap_plan_destroy(frlap_plan* plan) {
   if (!plan) return FRLAP_OK;
   cudaFree(plan->lam64);
+  cudaFree(plan->lamL64);
   cudaFree(plan->lam32);
   cudaFree(plan->mu_strang);
   cudaFree(plan->mu_learned);
@@ -179,7 +180,8 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   };
   if (cudaMalloc(&coef, ncoef * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&scratch, coeffs_scratch_bytes(d, p->Nmax)) != cudaSuccess ||
-      cudaMalloc(&p->lam64, p->lam_count * sizeof(double)) != cudaSuccess)
+      cudaMalloc(&p->lam64, p->lam_count * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&p->lamL64, p->lam_count * sizeof(double)) != cudaSuccess)
     return cleanup(FRLAP_ENOMEM, "plan allocation failed");
   if (prec != FRLAP_F64 && cudaMalloc(&p->lam32, p->lam_count * sizeof(float)) != cudaSuccess)
     return cleanup(FRLAP_ENOMEM, "plan allocation failed");
@@ -203,12 +205,15 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol: ") + cudaGetErrorString(e));
   double scale = 1.0;
   for (int r = 0; r < d; ++r) scale /= (double)p->P[r];
-  e = scale_symbol_launch(p->lam64, p->lam32, p->lam_count, scale, s);
+  e = scale_symbol_launch(p->lam64, nullptr, p->lam_count, scale, s);
   if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol scale: ") + cudaGetErrorString(e));
+  e = line_symbol_launch<double>(*p, p->lam64, p->lamL64, 1.0, s);
+  if (e == cudaSuccess && p->lam32) e = line_symbol_launch<float>(*p, p->lam64, p->lam32, 1.0, s);
+  if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol copy: ") + cudaGetErrorString(e));
   if (p->df64) {
     if (cudaMalloc(&p->lamdf, p->lam_count * sizeof(dfl)) != cudaSuccess)
       return cleanup(FRLAP_ENOMEM, "plan allocation failed");
-    e = to_df_launch(p->lam64, p->lamdf, p->lam_count, s);
+    e = line_symbol_launch<dfl>(*p, p->lam64, p->lamdf, 1.0, s);
     if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("symbol copy: ") + cudaGetErrorString(e));
   }
   e = cudaStreamSynchronize(s);
@@ -438,7 +443,7 @@ frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void*
     return fail(FRLAP_ENOMEM, "multiplier allocation failed");
   double scale = 1.0;
   for (int r = 0; r < plan->d; ++r) scale /= (double)plan->P[r];
-  cudaError_t e = scale_to_f32_launch(d_m, plan->mu_learned, plan->lam_count, scale, (cudaStream_t)stream);
+  cudaError_t e = line_symbol_launch<float>(*plan, d_m, plan->mu_learned, scale, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_set_symbol");
   return FRLAP_OK;
 }

@@ -29,13 +29,58 @@ struct Batch {
   int skip = 0;
 };
 
+// Where a middle-stage column finds its multiplier line.  Column index: 2D kx, 3D kx * P_y + ky.
 struct LamMap {
   int d;       // 2 or 3
-  int logPy;   // 3D: log2 P_y (column index = kx * P_y + ky)
+  int logPy;   // 3D: log2 P_y
   int Py;
   int Hx1;     // P_x/2 + 1
   int Hy1;     // P_y/2 + 1
+  int Hz1;     // P_z/2 + 1 (3D)
 };
+
+// Global loads are issued in unrolled batches before their shared-memory stores, so that
+// each thread keeps many loads in flight (the kernels are latency-bound otherwise).
+
+// One line of P = 16 G elements, zero beyond n (or all zero if !valid): lane loads lane + j G.
+template <typename C>
+__device__ __forceinline__ void load_line(C* buf, const C* __restrict__ src, int lane, int G, int n, bool valid) {
+  constexpr int U = sizeof(C) <= 8 ? 16 : 8;
+#pragma unroll 1
+  for (int j0 = 0; j0 < 16; j0 += U) {
+    C t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = lane + (j0 + u) * G;
+      t[u] = (valid && i < n) ? src[i] : czero<C>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) buf[spad(lane + (j0 + u) * G)] = t[u];
+  }
+}
+
+// smem[l][spad(k)] = src[k * ld + line0 + l] for l < TL, k < total / TL (zero past nlines)
+template <typename C>
+__device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ src, int total, int TL, int LS,
+                                                size_t ld, int line0, int nlines) {
+  constexpr int U = sizeof(C) <= 8 ? 8 : 4;
+  const int step = blockDim.x;
+#pragma unroll 1
+  for (int idx0 = threadIdx.x; idx0 < total; idx0 += U * step) {
+    C t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = idx0 + u * step;
+      const int l2 = idx % TL, k = idx / TL;
+      t[u] = (idx < total && line0 + l2 < nlines) ? src[(size_t)k * ld + line0 + l2] : czero<C>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = idx0 + u * step;
+      if (idx < total) smem[(size_t)(idx % TL) * LS + spad(idx / TL)] = t[u];
+    }
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
@@ -60,8 +105,25 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   C* buf = smem + (size_t)l * LS;
   T* rb = reinterpret_cast<T*>(buf);
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
-  // real sample i is component (i & 1) of complex element i / 2 (even/odd packing)
-  for (int i = lane; i < 2 * H; i += G) rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(src[i]) : T(0);
+  // real sample i is component (i & 1) of complex element i / 2 (even/odd packing).  Each
+  // lane loads 2H / G = 32 samples, in batches of U issued before their stores.
+  {
+    constexpr int U = sizeof(io_t<T>) == 4 ? 32 : 16;
+#pragma unroll 1
+    for (int j0 = 0; j0 < 32; j0 += U) {
+      io_t<T> t[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = lane + (j0 + u) * G;
+        t[u] = (valid && i < n) ? src[i] : io_t<T>(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = lane + (j0 + u) * G;
+        rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(t[u]) : T(0);
+      }
+    }
+  }
   __syncthreads();
   fft_line<T, -1, true, false>(buf, logH, lane, tw, logP);
   // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
@@ -111,10 +173,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   const int line = line0 + l;
   const int LS = sline(H);
   const int total = TL * (H + 1);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx % TL, k = idx / TL;
-    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? in[(size_t)k * ldi + line0 + l2] : czero<C>();
-  }
+  load_transposed<C>(smem, in, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
   // repack: Z[k] = (X[k] + conj X[H-k]) + i W^{-k} (X[k] - conj X[H-k]), so that the
@@ -161,24 +220,25 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   C* line = data + (size_t)(valid ? col : 0) * ld;
-  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? line[i] : czero<C>();
+  load_line<C>(buf, line, lane, G, n, valid);
   __syncthreads();
   fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
+  // line-major symbol: the folded line of this column is contiguous
   size_t lam_base;
-  int lam_stride;
-  if (map.d == 2) {
-    lam_base = valid ? col : 0;
-    lam_stride = map.Hx1;
-  } else {
+  {
     const int c = valid ? col : 0;
-    const int kx = c >> map.logPy, ky = c & (map.Py - 1);
-    const int kyf = min(ky, map.Py - ky);
-    lam_base = (size_t)kyf * map.Hx1 + kx;
-    lam_stride = map.Hy1 * map.Hx1;
+    if (map.d == 2) {
+      lam_base = (size_t)c * map.Hy1;
+    } else {
+      const int kx = c >> map.logPy, ky = c & (map.Py - 1);
+      lam_base = ((size_t)kx * map.Hy1 + min(ky, map.Py - ky)) * map.Hz1;
+    }
   }
-  for (int k = lane; k < P; k += G) {
-    const int kf = min(k, P - k);
-    buf[spad(k)] = lam[lam_base + (size_t)kf * lam_stride] * buf[spad(k)];
+  const T* __restrict__ lrow = lam + lam_base;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k = lane + j * G;
+    buf[spad(k)] = lrow[min(k, P - k)] * buf[spad(k)];
   }
   __syncthreads();
   fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
@@ -210,9 +270,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   const int LS = sline(P);
   C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
-  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : czero<C>();
+  load_line<C>(buf, src, lane, G, n, valid);
   __syncthreads();
   fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
+  __syncthreads();
   C* dst = out + g * gout;
   const int total = TL * P;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -244,10 +305,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   const C* src = in + g * gin;
   const int LS = sline(P);
   const int total = TL * P;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx % TL, k = idx / TL;
-    smem[(size_t)l2 * LS + spad(k)] = (line0 + l2 < nlines) ? src[(size_t)k * ldi + line0 + l2] : czero<C>();
-  }
+  load_transposed<C>(smem, src, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
   fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
@@ -272,7 +330,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   const C* src = in + (size_t)(valid ? col : 0) * ld;
-  for (int i = lane; i < P; i += G) buf[spad(i)] = (valid && i < n) ? src[i] : czero<C>();
+  load_line<C>(buf, src, lane, G, n, valid);
   __syncthreads();
   fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
   if (valid) {
@@ -296,6 +354,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   const C* src = in + (size_t)(valid ? col : 0) * ld;
+  // the multiplier is in natural octant order here (it comes from the learning kernels)
   size_t lam_base;
   int lam_stride;
   if (map.d == 2) {
@@ -320,7 +379,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
 }
 
 // Lines per CTA for a line of `len` complex slots: as many as fit in
-// `budget` bytes of shared memory and 1024 threads (at least one).
+// `budget` bytes of shared memory and 256 threads (at least one), in whole warps.
 // (every apply kernel is compiled for at most 512 threads per CTA; CTAs of at most 256
 // threads measured fastest: more independent CTAs per SM overlap their phases)
 int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
@@ -328,6 +387,11 @@ int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
   tl = tl < 1 ? 1 : tl;
   while (tl > 1 && tl * G > 256) --tl;
   if (tl > max_lines) tl = max_lines;
+  // whole warps (the FFT stages of lines shorter than 32 lanes end with a warp barrier)
+  if (G < 32) {
+    const int q = 32 / G;
+    tl = tl < q ? q : tl - tl % q;
+  }
   return tl < 1 ? 1 : tl;
 }
 
@@ -357,7 +421,7 @@ static const cplx<T>* twiddle_table(const Plan& p, int r) {
 
 template <typename T>
 static const T* symbol_table(const Plan& p) {
-  if constexpr (std::is_same<T, double>::value) return p.lam64;
+  if constexpr (std::is_same<T, double>::value) return p.lamL64;
   else if constexpr (std::is_same<T, float>::value) return p.lam32;
   else return p.lamdf;
 }
@@ -423,6 +487,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   map.logPy = logPy;
   map.Py = p.P[1];
   map.Hy1 = p.P[1] / 2 + 1;
+  map.Hz1 = p.d == 3 ? p.P[2] / 2 + 1 : 1;
   if (p.d == 2) {
     const int G = p.P[1] >> 4;
     const int tl = pick_tl(sline(p.P[1]), eb, G, budget, 64);
@@ -603,6 +668,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
   map.logPy = p.logP[1];
   map.Py = p.P[1];
   map.Hy1 = p.P[1] / 2 + 1;
+  map.Hz1 = p.d == 3 ? p.P[2] / 2 + 1 : 1;
   cudaError_t e;
   {
     const int logP = p.d == 2 ? p.logP[1] : p.logP[2];

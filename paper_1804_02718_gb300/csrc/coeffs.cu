@@ -12,6 +12,8 @@
 // Newton's method on the three-term Legendre recurrence.
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -360,6 +362,7 @@ cudaError_t symbol_axes_launch(const Plan& p, double* lam, cudaStream_t s) {
     int tl = (48 * 1024) / (sline(P) * 16);
     if (tl < 1) tl = 1;
     while (tl > 1 && tl * G > 512) --tl;
+    if (G < 32) tl = tl < 32 / G ? 32 / G : tl - tl % (32 / G);  // whole warps (see line_sync)
     // lines along axis r: stride = product of H1 of faster axes; inner = that same product
     size_t stride = 1;
     for (int q = 0; q < r; ++q) stride *= H1[q];
@@ -395,4 +398,36 @@ cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s,
   k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lam64, lam32, n, s);
   return cudaGetLastError();
 }
+
+namespace {
+template <typename To>
+__device__ __forceinline__ To from_double(double v) {
+  if constexpr (std::is_same<To, dfl>::value) return df_from(v);
+  else return (To)v;
+}
+
+// natural octant [A][Bm][Cx] (Cx fastest) -> line-major [Cx][Bm][A] (A fastest), times s
+template <typename To>
+__global__ void k_oct_to_line(const double* __restrict__ oct, To* __restrict__ dst, size_t n, int A, int Bm, int Cx,
+                              double s) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int a = (int)(i % A);
+  const size_t r = i / A;
+  const int b = (int)(r % Bm), c = (int)(r / Bm);
+  dst[i] = from_double<To>(oct[((size_t)a * Bm + b) * Cx + c] * s);
+}
+}  // namespace
+
+template <typename To>
+cudaError_t line_symbol_launch(const Plan& p, const double* oct, To* dst, double s, cudaStream_t st) {
+  const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1;
+  const int A = (p.d == 3) ? p.P[2] / 2 + 1 : Hy1, Bm = (p.d == 3) ? Hy1 : 1;
+  const size_t n = p.lam_count;
+  k_oct_to_line<To><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(oct, dst, n, A, Bm, Hx1, s);
+  return cudaGetLastError();
+}
+template cudaError_t line_symbol_launch<double>(const Plan&, const double*, double*, double, cudaStream_t);
+template cudaError_t line_symbol_launch<float>(const Plan&, const double*, float*, double, cudaStream_t);
+template cudaError_t line_symbol_launch<dfl>(const Plan&, const double*, dfl*, double, cudaStream_t);
 }  // namespace frlap

@@ -95,17 +95,23 @@ struct Plan {
   int prec;        // frlap_prec
   size_t M;        // number of unknowns
   size_t lam_count;            // prod (P_r/2 + 1) over the used axes
-  double* lam64 = nullptr;     // symbol octant, FP64 (always built)
-  float* lam32 = nullptr;      // symbol octant, FP32 (F32 and MIXED plans)
+  // The symbol octant lambda(kx, ky[, kz]), k_r = 0..P_r/2, with 1/prod(P) folded in.
+  // lam64 is in natural order ([ky][kx] / [kz][ky][kx], kx fastest).  The tables the
+  // apply's middle stage reads (lamL64, lam32, lamdf and the preconditioner multipliers)
+  // are line-major: axes reversed ([kx][ky] / [kx][ky][kz]), so that the folded line of
+  // one column is contiguous.
+  double* lam64 = nullptr;     // natural order, FP64 (always built)
+  double* lamL64 = nullptr;    // line-major, FP64 (always built)
+  float* lam32 = nullptr;      // line-major, FP32 (all plans but F64)
   double2* tw64[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i m / P_r), m < P_r
   float2* tw32[3] = {nullptr, nullptr, nullptr};
   cdf* twdf[3] = {nullptr, nullptr, nullptr};      // the same twiddles as double-floats
-  dfl* lamdf = nullptr;        // symbol octant as double-floats (DF64 plans)
+  dfl* lamdf = nullptr;        // line-major, as double-floats (DF64 plans)
   bool df64 = false;           // FP64-precision vectors are applied with double-float FFTs
   // workspace layout of one apply, in complex elements of the apply precision
   size_t s1_elems = 0, s2_elems = 0;
   cudaStream_t side = nullptr;  // internal stream for captured solver graphs
-  // preconditioner symbols (octant layout of lam, FP32; nullptr until built)
+  // preconditioner multipliers (line-major like lam32, FP32; nullptr until built)
   float* mu_strang = nullptr;   // inverse of the multilevel Strang circulant, embedded like A
   float* mu_learned = nullptr;  // learned Fourier multiplier
 };
@@ -137,6 +143,9 @@ size_t coeffs_scratch_bytes(int d, int Nmax);
 cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
 cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s);
 cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st);
+// dst (line-major, converted to To) = s * oct (natural order); To = double, float or dfl
+template <typename To>
+cudaError_t line_symbol_launch(const Plan& p, const double* oct, To* dst, double s, cudaStream_t st);
 cudaError_t to_df_launch(const double* src, dfl* dst, size_t n, cudaStream_t st);
 // even DFT of the octant along every axis (used for both the operator and preconditioner symbols)
 cudaError_t symbol_axes_launch(const Plan& p, double* lam_oct, cudaStream_t s);

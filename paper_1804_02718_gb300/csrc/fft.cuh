@@ -8,7 +8,7 @@
 // reads x[j + r L/R], multiplies by the twiddles W_{Ns R}^{r k} (k = j mod Ns),
 // does a radix-R DFT in registers and writes to (j - k) R + k + r Ns; the
 // result is in natural order with no bit reversal.  All reads of a stage
-// happen before a CTA barrier and all writes after it, so one buffer suffices.
+// happen before a barrier and all writes after it, so one buffer suffices.
 // Radices: one 2/4/8 stage for the leftover log2 factor, then radix-16 stages.
 //
 // Twiddles come from a table tw[m] = exp(-2 pi i m / Ptab), m < Ptab, of the
@@ -194,6 +194,17 @@ __device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict
   }
 }
 
+// Barrier between the read and write halves of a stage.  The G = L/16 lanes of a line
+// are consecutive threads starting at a multiple of G, so a line of at most 512 points
+// (G <= 32) lies inside one warp, and a warp barrier suffices: the other warps of the CTA
+// proceed independently.  Longer lines span several warps.  CTAs are whole warps (the
+// launchers round their size to a multiple of 32 threads) and every thread calls the
+// transform, so the full-warp barrier is well defined.
+__device__ __forceinline__ void line_sync(int logL) {
+  if (logL <= 9) __syncwarp();
+  else __syncthreads();
+}
+
 // One Stockham stage of radix R on a line of length L = 2^logL held in `buf`
 // (padded layout, see spad).  ZIN: the input's upper half is zero (first stage of a
 // zero-padded forward transform; those elements are not read).  HOUT: only the lower
@@ -221,7 +232,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
     for (int r = 0; r < R; ++r)
       v[b * R + r] = (ZIN && 2 * r >= R) ? czero<C>() : buf[lr16 ? base + r * lstep : spad(j + r * LR)];
   }
-  __syncthreads();
+  line_sync(logL);
   const bool ns16 = (Ns & 15) == 0;
   const int sstep = Ns + (Ns >> 4);
 #pragma unroll
@@ -251,11 +262,13 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
       if (!HOUT || 2 * r < R)
         buf[Ns == 1 ? obase + r : (ns16 ? obase + r * sstep : spad(o + r * Ns))] = v[b * R + r];
   }
-  __syncthreads();
+  line_sync(logL);
 }
 
 // Full transform of the line in `buf` (length 2^logL >= 16).  Every thread of the
-// CTA must call this with the same logL (the stages contain CTA barriers).
+// CTA must call this with the same logL (the stages contain barriers, over the CTA for
+// logL > 9, else over the warp: a caller that then reads other lines synchronises the
+// CTA itself).
 // ZIN: the upper half of the input line is zero (its slots are neither read nor
 // needed); HOUT: only the lower half of the output is read afterwards (the upper
 // half of the buffer is left stale).  The last stage is always radix 16.

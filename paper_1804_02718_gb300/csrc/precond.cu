@@ -156,7 +156,7 @@ cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_h
   if ((e = symbol_axes_launch(p, oct, s)) != cudaSuccess) return e;
   double scale = 1.0;
   for (int r = 0; r < p.d; ++r) scale /= (double)p.P[r];
-  if ((e = scale_symbol_launch(oct, p.mu_strang, p.lam_count, scale, s)) != cudaSuccess) return e;
+  if ((e = line_symbol_launch<float>(p, oct, p.mu_strang, scale, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }
