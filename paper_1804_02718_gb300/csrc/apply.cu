@@ -59,25 +59,27 @@ __device__ __forceinline__ void load_line(C* buf, const C* __restrict__ src, int
   }
 }
 
-// smem[l][spad(k)] = src[k * ld + line0 + l] for l < TL, k < total / TL (zero past nlines)
+// smem[l][spad(k)] = src[k * ld + line0 + l] for l < TL, k < total / TL (zero past nlines);
+// TL is a power of two
 template <typename C>
 __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ src, int total, int TL, int LS,
                                                 size_t ld, int line0, int nlines) {
   constexpr int U = sizeof(C) <= 8 ? 8 : 4;
   const int step = blockDim.x;
+  const int logTL = __ffs(TL) - 1;
 #pragma unroll 1
   for (int idx0 = threadIdx.x; idx0 < total; idx0 += U * step) {
     C t[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int idx = idx0 + u * step;
-      const int l2 = idx % TL, k = idx / TL;
+      const int l2 = idx & (TL - 1), k = idx >> logTL;
       t[u] = (idx < total && line0 + l2 < nlines) ? src[(size_t)k * ld + line0 + l2] : czero<C>();
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int idx = idx0 + u * step;
-      if (idx < total) smem[(size_t)(idx % TL) * LS + spad(idx / TL)] = t[u];
+      if (idx < total) smem[(size_t)(idx & (TL - 1)) * LS + spad(idx >> logTL)] = t[u];
     }
   }
 }
@@ -147,8 +149,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   }
   __syncthreads();
   const int total = TL * (H + 1);
+  const int logTL = __ffs(TL) - 1;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx % TL, k = idx / TL;
+    const int l2 = idx & (TL - 1), k = idx >> logTL;
     if (line0 + l2 < nlines) out[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * LS + spad(k)];
   }
 }
@@ -276,8 +279,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   __syncthreads();
   C* dst = out + g * gout;
   const int total = TL * P;
+  const int logTL = __ffs(TL) - 1;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx % TL, k = idx / TL;
+    const int l2 = idx & (TL - 1), k = idx >> logTL;
     if (line0 + l2 < nlines) dst[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * LS + spad(k)];
   }
 }
@@ -379,7 +383,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
 }
 
 // Lines per CTA for a line of `len` complex slots: as many as fit in
-// `budget` bytes of shared memory and 256 threads (at least one), in whole warps.
+// `budget` bytes of shared memory and 256 threads (at least one), rounded down to a
+// power of two, in whole warps.
 // (every apply kernel is compiled for at most 512 threads per CTA; CTAs of at most 256
 // threads measured fastest: more independent CTAs per SM overlap their phases)
 int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
@@ -387,12 +392,13 @@ int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
   tl = tl < 1 ? 1 : tl;
   while (tl > 1 && tl * G > 256) --tl;
   if (tl > max_lines) tl = max_lines;
+  // a power of two (the transposed loads and stores index lines by shifts)
+  int p2 = 1;
+  while (2 * p2 <= tl) p2 *= 2;
+  tl = p2;
   // whole warps (the FFT stages of lines shorter than 32 lanes end with a warp barrier)
-  if (G < 32) {
-    const int q = 32 / G;
-    tl = tl < q ? q : tl - tl % q;
-  }
-  return tl < 1 ? 1 : tl;
+  if (G < 32 && tl < 32 / G) tl = 32 / G;
+  return tl;
 }
 
 template <typename Kern>
