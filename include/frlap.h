@@ -130,6 +130,21 @@ frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, voi
  * the FFT/multiply stages along y (and z), inverse real FFT along x + crop. */
 int frlap_apply_nstages(const frlap_plan* plan);
 
+/* nbatch products y_b = A u_b (b = 0..nbatch-1) of the same plan, each as in
+ * frlap_apply, with one kernel launch per stage for the whole batch: the
+ * instances fill the GPU together instead of one after another.  Many
+ * right-hand sides or time levels of one operator are the use (the paper applies
+ * A once per CG iteration and time step, Secs. 5.3-5.4).
+ * d_u, d_y: nbatch vectors of prod(n_r) elements each, back to back, of the
+ * element type frlap_apply takes for the plan; the two ranges must not overlap.
+ * d_work: frlap_apply_batch_workspace_bytes(plan, nbatch) bytes, 256-byte aligned.
+ * events: NULL, or frlap_apply_nstages(plan) + 1 cudaEvent_t recorded on `stream`
+ * before each stage and after the last (NULL entries are skipped).
+ * 1 <= nbatch <= 65535, else FRLAP_EINVAL. */
+size_t frlap_apply_batch_workspace_bytes(const frlap_plan* plan, int nbatch);
+frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d_u, void* d_y, void* d_work,
+                               void* stream, void* const* events);
+
 /* frlap_apply with timing marks: events[i] (a cudaEvent_t, or NULL to skip) is
  * recorded on `stream` just before stage i, events[nstages] after the last
  * stage.  The caller creates the events; the array must hold nstages+1 entries. */

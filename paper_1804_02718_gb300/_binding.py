@@ -42,6 +42,8 @@ _SIGS = {
     "frlap_apply_noalloc": (_I, [_P, _P, _P, _P]),
     "frlap_apply_nstages": (_I, [_P]),
     "frlap_apply_profiled": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "frlap_apply_batch_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
+    "frlap_apply_batch": (_I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
     "frlap_precond_strang": (_I, [_P, ctypes.POINTER(_I), _P]),
     "frlap_precond_set_symbol": (_I, [_P, _P, _P]),
@@ -242,6 +244,41 @@ def frlap_apply_profiled(plan: Plan, u: torch.Tensor, y: torch.Tensor, work: tor
                                       ctypes.c_void_p(work.data_ptr()), _stream(stream), arr),
            "frlap_apply_profiled")
     return y
+
+
+def frlap_apply_batch_workspace_bytes(plan: Plan, nbatch: int) -> int:
+    return int(lib().frlap_apply_batch_workspace_bytes(plan.handle, int(nbatch)))
+
+
+def frlap_apply_batch(plan: Plan, U: torch.Tensor, Y: torch.Tensor = None, work: torch.Tensor = None, stream=None,
+                      events=None):
+    """Y[b] = A U[b] for every b in one launch per stage; U holds nbatch vectors back to back
+    (shape (nbatch, *plan.shape) or any contiguous tensor of nbatch * M entries).  `work`: at least
+    frlap_apply_batch_workspace_bytes(plan, nbatch) bytes, 256-byte aligned (allocated if None).
+    `events`: None, or nstages + 1 torch.cuda.Event recorded before each stage and after the last."""
+    dt = _apply_dtype(plan)
+    if U.numel() % plan.M != 0 or U.numel() == 0:
+        raise ValueError(f"U has {U.numel()} entries, not a positive multiple of the plan's {plan.M} unknowns")
+    nb = U.numel() // plan.M
+    if Y is None:
+        Y = torch.empty_like(U)
+    if Y.numel() != U.numel():
+        raise ValueError("Y and U differ in size")
+    if work is None:
+        nbytes = frlap_apply_batch_workspace_bytes(plan, nb)
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        off = (-raw.data_ptr()) % 256
+        work = raw[off:off + nbytes]
+    arr = None
+    if events is not None:
+        ns = frlap_apply_nstages(plan)
+        if len(events) != ns + 1:
+            raise ValueError(f"need {ns + 1} events")
+        arr = (ctypes.c_void_p * (ns + 1))(*[ctypes.c_void_p(e.cuda_event) if e is not None else None
+                                             for e in events])
+    _check(lib().frlap_apply_batch(plan.handle, nb, _dev(U, dt, "U"), _dev(Y, dt, "Y"),
+                                   ctypes.c_void_p(work.data_ptr()), _stream(stream), arr), "frlap_apply_batch")
+    return Y
 
 
 def frlap_apply_f32(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch.Tensor = None, stream=None):

@@ -286,6 +286,36 @@ frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, voi
 
 int frlap_apply_nstages(const frlap_plan* plan) { return plan ? (plan->d == 2 ? 3 : 5) : 0; }
 
+size_t frlap_apply_batch_workspace_bytes(const frlap_plan* plan, int nbatch) {
+  if (!plan || nbatch < 1) return 0;
+  return (size_t)nbatch * frlap_workspace_bytes(plan, FRLAP_OP_APPLY);
+}
+
+frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d_u, void* d_y, void* d_work,
+                               void* stream, void* const* events) {
+  if (!plan || !d_u || !d_y) return fail(FRLAP_EINVAL, "plan, d_u or d_y is NULL");
+  if (nbatch < 1 || nbatch > 65535) return fail(FRLAP_EINVAL, "nbatch must be in 1..65535");
+  const size_t bytes = (size_t)nbatch * plan->M * (plan->prec == FRLAP_F32 ? 4 : 8);
+  const uintptr_t u0 = reinterpret_cast<uintptr_t>(d_u), y0 = reinterpret_cast<uintptr_t>(d_y);
+  if (u0 < y0 + bytes && y0 < u0 + bytes) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  cudaEvent_t const* ev = reinterpret_cast<cudaEvent_t const*>(events);
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (plan->prec == FRLAP_F32)
+    e = apply_batch_launch<float>(*plan, nbatch, (const float*)d_u, (float*)d_y, plan->M, d_work, s, nullptr, 0,
+                                  nullptr, 0, ev);
+  else if (plan->df64)
+    e = apply_batch_launch<dfl>(*plan, nbatch, (const double*)d_u, (double*)d_y, plan->M, d_work, s, nullptr, 0,
+                                nullptr, 0, ev);
+  else
+    e = apply_batch_launch<double>(*plan, nbatch, (const double*)d_u, (double*)d_y, plan->M, d_work, s, nullptr, 0,
+                                   nullptr, 0, ev);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_batch");
+  return FRLAP_OK;
+}
+
 frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream,
                                   void* const* events) {
   if (!plan || !d_u || !d_y || !events) return fail(FRLAP_EINVAL, "plan, d_u, d_y or events is NULL");

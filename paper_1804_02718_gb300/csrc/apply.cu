@@ -224,29 +224,47 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
   C* buf = smem + (size_t)l * sline(P);
   C* line = data + (size_t)(valid ? col : 0) * ld;
   load_line<C>(buf, line, lane, G, n, valid);
-  __syncthreads();
-  fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
   // line-major symbol: the folded line of this column is contiguous
-  size_t lam_base;
-  {
+  auto symbol_row = [&]() -> const T* {
     const int c = valid ? col : 0;
-    if (map.d == 2) {
-      lam_base = (size_t)c * map.Hy1;
-    } else {
-      const int kx = c >> map.logPy, ky = c & (map.Py - 1);
-      lam_base = ((size_t)kx * map.Hy1 + min(ky, map.Py - ky)) * map.Hz1;
-    }
-  }
-  const T* __restrict__ lrow = lam + lam_base;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int k = lane + j * G;
-    buf[spad(k)] = lrow[min(k, P - k)] * buf[spad(k)];
-  }
+    if (map.d == 2) return lam + (size_t)c * map.Hy1;
+    const int kx = c >> map.logPy, ky = c & (map.Py - 1);
+    return lam + ((size_t)kx * map.Hy1 + min(ky, map.Py - ky)) * map.Hz1;
+  };
   __syncthreads();
-  fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
-  if (valid)
-    for (int i = lane; i < n; i += G) line[i] = buf[spad(i)];
+  if constexpr (!std::is_same<T, dfl>::value) {
+    // FP64 prunes the first stage (zero upper half) and the last (cropped output)
+    fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
+    const T* __restrict__ lrow = symbol_row();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = lane + j * G;
+      buf[spad(k)] = lrow[min(k, P - k)] * buf[spad(k)];
+    }
+    __syncthreads();
+    fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
+    if (valid)
+      for (int i = lane; i < n; i += G) line[i] = buf[spad(i)];
+  } else {
+    // Double-float: the inverse transform runs as conj(FFT(conj(.))), so both transforms
+    // execute one copy of the forward code.  The double-float stages are long enough that
+    // two copies miss in the instruction cache (measured 6% slower); for FP32 the loop
+    // costs more in register spills than it saves.
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+      if (pass == 1) break;
+      const T* __restrict__ lrow = symbol_row();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int k = lane + j * G;
+        buf[spad(k)] = conjg(lrow[min(k, P - k)] * buf[spad(k)]);
+      }
+      __syncthreads();
+    }
+    if (valid)
+      for (int i = lane; i < n; i += G) line[i] = conjg(buf[spad(i)]);
+  }
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
@@ -573,8 +591,9 @@ cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work
 
 template <typename T>
 cudaError_t apply_batch_launch(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
-                               cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride) {
-  return apply_launch_b<T>(p, B, u, y, vstride, work, s, skip, skip_stride, nullptr, lam, lam_stride);
+                               cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride,
+                               cudaEvent_t const* ev) {
+  return apply_launch_b<T>(p, B, u, y, vstride, work, s, skip, skip_stride, ev, lam, lam_stride);
 }
 
 cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
@@ -584,11 +603,11 @@ cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaS
 }
 
 template cudaError_t apply_batch_launch<double>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
-                                                const int*, int, const double*, size_t);
+                                                const int*, int, const double*, size_t, cudaEvent_t const*);
 template cudaError_t apply_batch_launch<float>(const Plan&, int, const float*, float*, size_t, void*, cudaStream_t,
-                                               const int*, int, const float*, size_t);
+                                               const int*, int, const float*, size_t, cudaEvent_t const*);
 template cudaError_t apply_batch_launch<dfl>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
-                                             const int*, int, const dfl*, size_t);
+                                             const int*, int, const dfl*, size_t, cudaEvent_t const*);
 
 template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
                                           cudaEvent_t const*, const double*);

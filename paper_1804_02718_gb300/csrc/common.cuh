@@ -128,7 +128,8 @@ size_t apply_work_bytes(const Plan& p, int real_bytes);
 // B same-shape instances in one launch per stage (see apply.cu)
 template <typename T>
 cudaError_t apply_batch_launch(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
-                               cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride);
+                               cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride,
+                               cudaEvent_t const* ev = nullptr);
 // forward half spectrum F R^T u (2D [kx][ky], 3D [kx][ky][kz]) and its multiplied inverse; same workspace as apply
 size_t spectrum_elems(const Plan& p);
 template <typename T>

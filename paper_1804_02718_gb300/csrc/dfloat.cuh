@@ -73,10 +73,33 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) {
   return fast_two_sum(p, e);
 }
 
+// a b + c d with one normalisation: the two leading products are split exactly (FMA), summed
+// with two_sum, and the error terms and cross products gathered in one FP32 accumulator
+// (19 instructions against 25 for two products and a sum; error about eps^2 (|ab| + |cd|)).
+__device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float q = __fmul_rn(c.hi, d.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  float f = __fmaf_rn(c.hi, d.hi, -q);
+  const float s = __fadd_rn(p, q);
+  const float v = __fsub_rn(s, p);
+  const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(q, v));
+  e = __fmaf_rn(a.hi, b.lo, e);
+  f = __fmaf_rn(c.hi, d.lo, f);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  f = __fmaf_rn(c.lo, d.hi, f);
+  return fast_two_sum(s, __fadd_rn(t, __fadd_rn(e, f)));
+}
+
 __device__ __forceinline__ cdf operator+(cdf a, cdf b) { return cdf{a.x + b.x, a.y + b.y}; }
 __device__ __forceinline__ cdf operator-(cdf a, cdf b) { return cdf{a.x - b.x, a.y - b.y}; }
 __device__ __forceinline__ cdf operator*(dfl s, cdf a) { return cdf{s * a.x, s * a.y}; }
-__device__ __forceinline__ cdf cmul(cdf a, cdf b) { return cdf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ cdf cmulc(cdf a, cdf b) { return cdf{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) {
+  return cdf{df_dot2(a.x, b.x, -a.y, b.y), df_dot2(a.x, b.y, a.y, b.x)};
+}
+// a * conj(b)
+__device__ __forceinline__ cdf cmulc(cdf a, cdf b) {
+  return cdf{df_dot2(a.x, b.x, a.y, b.y), df_dot2(a.y, b.x, -a.x, b.y)};
+}
 
 }  // namespace frlap

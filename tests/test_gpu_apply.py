@@ -174,3 +174,48 @@ def test_apply_255_cubed_sampled_rows(frlap, prec, tol):
     lam_max = float(plan.symbol().abs().max().item() * np.prod(plan.P))
     for r, v in zip(rows, yr):
         assert abs(y[r] - v) <= tol * lam_max * np.linalg.norm(u) / math.sqrt(u.size) * 50, (r, y[r], v)
+
+
+@pytest.mark.parametrize("d,Ns,alpha,prec,tol", [
+    (2, (64, 40), 1.3, 0, 1e-12), (2, (64, 40), 1.3, 1, 1e-5), (2, (64, 40), 1.3, 3, 1e-12),
+    (3, (12, 20, 9), 0.7, 0, 1e-12), (3, (12, 20, 9), 0.7, 1, 1e-5), (3, (12, 20, 9), 0.7, 3, 1e-12)])
+def test_apply_batch_matches_oracle(frlap, d, Ns, alpha, prec, tol):
+    """frlap_apply_batch: every instance of the batch against the oracle, and bit for bit equal to
+    frlap_apply of that instance (the batch only adds a grid dimension)."""
+    h = 2.0 / max(Ns)
+    a_ref, c = _oracle(d, alpha, h, Ns)
+    us = [inp.normal_field(Ns, seed=20 + b) for b in range(5)]
+    op = fast.FastOperator(a_ref, c, us[0].shape)
+    plan = frlap.Plan(d, alpha, h, Ns, prec=prec)
+    dt = torch.float32 if prec == 1 else torch.float64
+    U = _t(np.stack(us), dt)
+    Y = frlap.frlap_apply_batch(plan, U)
+    for b, u in enumerate(us):
+        y = Y[b].double().cpu().numpy()
+        assert np.linalg.norm(y - op(u)) <= tol * op.lam_max * np.linalg.norm(u), b
+        assert torch.equal(Y[b], frlap.frlap_apply(plan, U[b].clone()))
+
+
+def test_apply_batch_full_size_and_errors(frlap):
+    """The throughput launch: 8 x 2047^2 double-float instances in one batched apply; two checked
+    against the oracle, all eight bit for bit against single applies.  Bad arguments are refused."""
+    Ns, alpha = (2048, 2048), 1.5
+    h = 2.0 / 2048
+    plan = frlap.Plan(2, alpha, h, Ns, prec=frlap.FRLAP_DF64)
+    U = torch.stack([_t(inp.normal_field(Ns, seed=100 + b)) for b in range(8)])
+    Y = frlap.frlap_apply_batch(plan, U)
+    a_ref, c = _oracle(2, alpha, h, Ns)
+    op = fast.FastOperator(a_ref, c, plan.shape)
+    for b in (0, 7):
+        u = U[b].cpu().numpy()
+        assert np.linalg.norm(Y[b].cpu().numpy() - op(u)) <= 1e-12 * op.lam_max * np.linalg.norm(u)
+    for b in range(8):
+        assert torch.equal(Y[b], frlap.frlap_apply(plan, U[b].clone()))
+    import ctypes
+    lib = frlap.lib()
+    work = torch.empty(frlap.frlap_apply_batch_workspace_bytes(plan, 8) + 256, dtype=torch.uint8, device="cuda")
+    w = ctypes.c_void_p(work.data_ptr() + (-work.data_ptr()) % 256)
+    p = ctypes.c_void_p
+    assert lib.frlap_apply_batch(plan.handle, 0, p(U.data_ptr()), p(Y.data_ptr()), w, None, None) == 1
+    assert lib.frlap_apply_batch(plan.handle, 8, p(U.data_ptr()), p(U[4].data_ptr()), w, None, None) == 1  # overlap
+    assert frlap.frlap_apply_batch_workspace_bytes(plan, 8) == 8 * plan.workspace_bytes(frlap.FRLAP_OP_APPLY)
