@@ -5,8 +5,9 @@ Default workload: 2D, alpha = 1.5, Omega = (-1,1)^2, h = 2/2048 (2047 x 2047 int
 unknowns), an FP64-precision apply y = A u through libfrlap (the 2D throughput case
 of the 3D FP64 CG configuration), computed by the double-float FFT engine
 (FP64 vectors; FFT stages in FP32 pairs, parity 1e-12 normwise against the FP64
-oracle, like native FP64).  One step = a batch of 8 applies to 8 distinct seeded
-N(0,1) vectors (268 MB of inputs, more than the 129 MB L2).  Reported: apply
+oracle, like native FP64).  One step = one batched apply (frlap_apply_batch, one
+launch per stage) to 8 distinct seeded N(0,1) vectors (268 MB of inputs, more than
+the 129 MB L2).  Reported: apply
 unknowns/s over all ranks, the per-kernel roofline of the dominant kernel, the
 same metric end to end through host buffers, and the CPU oracle timed on the
 host cores.  Extra lines (native FP64 and FP32 applies, 3D 255^3 applies, CG
@@ -51,12 +52,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz (see DESIGN.md)
+# FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
-# DRAM traffic per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu captures summarised in profiles/k_colmul_2d_2047.md; None where the kernel changed since
-MEASURED_TRAFFIC = {("colmul", "df64"): 116.4e6, ("colmul", "f32"): 50.5e6}
+# DRAM traffic of one batched launch (8 instances) of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) from the ncu captures summarised under profiles/; absent where the kernel
+# changed since the capture
+MEASURED_TRAFFIC = {("colmul", "df64"): 1241.9e6, ("colmul", "f32"): 501.5e6}
 
 # double-float: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the FP32
 # instructions one FP64-equivalent FFT flop costs (add 11, mul 7; FFT mix 2 adds : 1 mul -> 29/3)
@@ -218,17 +220,17 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- GPU arm
 def time_applies(fl, torch, plan, U, Y, work, steps, warmup, d, barrier=None):
-    """Time `steps` steps of len(U) applies; returns (total_ms, per-stage mean ms, launches)."""
+    """Time `steps` steps, each one batched apply of all of U (shape (batch, *plan.shape)) with one
+    launch per stage.  Returns (total_ms, per-stage ms per instance (launch time / batch), launches)."""
     ns = fl.frlap_apply_nstages(plan)
+    B = U.shape[0]
     stream = torch.cuda.current_stream()
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)] for _ in U] for _ in range(steps)]
-    for step in evs:  # create the events
-        for row in step:
-            for e in row:
-                e.record(stream)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)] for _ in range(steps)]
+    for row in evs:  # create the events
+        for e in row:
+            e.record(stream)
     for _ in range(warmup):
-        for u, y in zip(U, Y):
-            fl.frlap_apply(plan, u, y, work)
+        fl.frlap_apply_batch(plan, U, Y, work)
     torch.cuda.synchronize()
     if barrier:
         barrier()
@@ -236,16 +238,21 @@ def time_applies(fl, torch, plan, U, Y, work, steps, warmup, d, barrier=None):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(steps):
-        for b, (u, y) in enumerate(zip(U, Y)):
-            fl.frlap_apply_profiled(plan, u, y, work, evs[k][b])
+        fl.frlap_apply_batch(plan, U, Y, work, events=evs[k])
     e1.record(stream)
     torch.cuda.synchronize()
     if barrier:
         barrier()
     total = e0.elapsed_time(e1)
-    st = [statistics.mean(evs[k][b][s].elapsed_time(evs[k][b][s + 1]) for k in range(steps) for b in range(len(U)))
-          for s in range(ns)]
-    return total, st, steps * len(U) * ns
+    st = [statistics.mean(evs[k][s].elapsed_time(evs[k][s + 1]) for k in range(steps)) / B for s in range(ns)]
+    return total, st, steps * ns
+
+
+def batch_workspace(fl, torch, plan, B):
+    nb = fl.frlap_apply_batch_workspace_bytes(plan, B)
+    raw = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    off = (-raw.data_ptr()) % 256
+    return raw[off:off + nb]
 
 
 def main():
@@ -292,9 +299,9 @@ def main():
     h = 2.0 / NGRID
     Ns = (NGRID, NGRID)
     plan = fl.Plan(2, ALPHA, h, Ns, prec=prec)
-    U = [torch.from_numpy(inp.normal_field(Ns, seed=100 + b)).to("cuda", dt) for b in range(BATCH)]
-    Y = [torch.empty_like(u) for u in U]
-    work = plan.workspace(fl.FRLAP_OP_APPLY)
+    U = torch.stack([torch.from_numpy(inp.normal_field(Ns, seed=100 + b)) for b in range(BATCH)]).to("cuda", dt)
+    Y = torch.empty_like(U)
+    work = batch_workspace(fl, torch, plan, BATCH)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -317,8 +324,8 @@ def main():
         ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
         roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe from unit count x max clock (DESIGN.md)",
-                "flops_per_launch": sf[dom]}
+                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
+                "flops_per_launch": sf[dom] * BATCH}
     elif args.prec == "df64":
         # FFT flops counted as FP64-equivalent operations, each executed as a double-float sequence
         # on the FP32 pipes; peak = FP32 issue rate / FP32 instructions per FP64-equivalent flop
@@ -326,13 +333,15 @@ def main():
         roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": DF64_PEAK_TFLOPS,
                 "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / DF64_PEAK_TFLOPS,
                 "traffic": MEASURED_TRAFFIC.get((names[dom], args.prec)),
-                "peak_source": "FP32 issue rate from unit counts x max clock / double-float cost (DESIGN.md)",
-                "flops_per_launch": sf[dom]}
+                "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / 29/3 FP32 instructions per FP64-equivalent flop",
+                "flops_per_launch": sf[dom] * BATCH}
     else:
         ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": MEASURED_TRAFFIC.get((names[dom], args.prec)),
-                "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom]}
+                "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom] * BATCH}
+    roof["instances_per_launch"] = BATCH
+    roof["launch_ms"] = stage_ms[dom] * BATCH
     apply_ms = sum(stage_ms)
     model_bytes = sum(sb)
     kernels = {nm: {"ms": round(ms, 5), "model_GBps": round(b / (ms / 1e3) / 1e9, 1),
@@ -341,23 +350,21 @@ def main():
     # end to end through host buffers (pinned), same batch, H2D + applies + D2H each step
     e2e = None
     if rank == 0 or world > 1:
-        Uh = [u.cpu().pin_memory() for u in U]
-        Yh = [torch.empty_like(u).pin_memory() for u in Uh]
-        Ud = [torch.empty_like(u) for u in U]
+        Uh = U.cpu().pin_memory()
+        Yh = torch.empty_like(Uh).pin_memory()
+        Ud = torch.empty_like(U)
         ksteps = max(2, min(args.steps, 10))
         for _ in range(2):
-            for b in range(BATCH):
-                Ud[b].copy_(Uh[b], non_blocking=True)
-                fl.frlap_apply(plan, Ud[b], Y[b], work)
-                Yh[b].copy_(Y[b], non_blocking=True)
+            Ud.copy_(Uh, non_blocking=True)
+            fl.frlap_apply_batch(plan, Ud, Y, work)
+            Yh.copy_(Y, non_blocking=True)
         torch.cuda.synchronize()
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(ksteps):
-            for b in range(BATCH):
-                Ud[b].copy_(Uh[b], non_blocking=True)
-                fl.frlap_apply(plan, Ud[b], Y[b], work)
-                Yh[b].copy_(Y[b], non_blocking=True)
+            Ud.copy_(Uh, non_blocking=True)
+            fl.frlap_apply_batch(plan, Ud, Y, work)
+            Yh.copy_(Y, non_blocking=True)
         z.record()
         torch.cuda.synchronize()
         ems = a.elapsed_time(z)
@@ -379,7 +386,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": {"df64": "f32x2"}.get(args.prec, args.prec),
             "data": "synthetic",
             "config": {"workload": f"2D {NGRID - 1}x{NGRID - 1} alpha={ALPHA} {args.prec.upper()} FFT Toeplitz apply",
-                       "batch_per_step": BATCH, "embedding": list(plan.P),
+                       "batch_per_step": BATCH, "launch": "frlap_apply_batch (one launch per stage for the batch)",
+                       "embedding": list(plan.P),
                        "l2": "inputs larger than L2 (8 distinct 2047^2 vectors per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
@@ -410,9 +418,9 @@ def run_extras(fl, torch, args):
         dt = torch.float32 if prec == fl.FRLAP_F32 else torch.float64
         eb = 4 if prec == fl.FRLAP_F32 else 8
         plan = fl.Plan(d, ALPHA if d == 2 else 1.0, 2.0 / N, (N,) * d, prec=prec)
-        U = [torch.randn(plan.shape, dtype=dt, device="cuda") for _ in range(batch)]
-        Y = [torch.empty_like(u) for u in U]
-        work = plan.workspace(fl.FRLAP_OP_APPLY)
+        U = torch.randn((batch,) + plan.shape, dtype=dt, device="cuda")
+        Y = torch.empty_like(U)
+        work = batch_workspace(fl, torch, plan, batch)
         steps = 5 if (d == 3 and prec != fl.FRLAP_F32) else 10
         total, st, _ = time_applies(fl, torch, plan, U, Y, work, steps, 2, d)
         sb = stage_bytes(d, plan.n, plan.P, eb)
