@@ -430,6 +430,10 @@ def run_extras(fl, torch, args):
                      "kernels_ms": [round(v, 5) for v in st]}
         del plan, U, Y, work
         torch.cuda.empty_cache()
+    # cuFFT (torch.fft) on the same embedding, as a timed comparison (not on the product path)
+    for name, prec in (("cufft_2047^2_f64", fl.FRLAP_F64), ("cufft_2047^2_f32", fl.FRLAP_F32)):
+        out[name] = cufft_compare(fl, torch, prec, 8)
+        torch.cuda.empty_cache()
     # CG: 63^2, f = 1 (configs[0]) and 2047^2 Gaussian-sum f, plain FP64 CG vs FP32-inner refinement
     for name, N, f_kind, solver in [("cg_63^2_f1_fp64", 64, "one", fl.FRLAP_SOLVE_CG),
                                     ("cg_2047^2_gauss_fp64", 2048, "gauss", fl.FRLAP_SOLVE_CG),
@@ -450,6 +454,43 @@ def run_extras(fl, torch, args):
         del plan
         torch.cuda.empty_cache()
     return out
+
+
+def cufft_compare(fl, torch, prec, batch, steps=10):
+    """The 2047^2 apply of the bench computed with cuFFT through torch.fft: zero-pad each vector to
+    P x P, real-to-complex 2D FFT, multiply by the symbol (the plan's own, 1/P^2 folded in), inverse,
+    crop.  Returns its time per vector and its normwise difference from frlap_apply_batch."""
+    dt = torch.float32 if prec == fl.FRLAP_F32 else torch.float64
+    plan = fl.Plan(2, ALPHA, 2.0 / NGRID, (NGRID, NGRID), prec=prec)
+    ny, nx = plan.shape
+    Py, Px = plan.P[1], plan.P[0]
+    oct_ = plan.symbol()  # (Py/2+1, Px/2+1), natural order
+    ky = torch.arange(Py, device="cuda")
+    lam = oct_[torch.minimum(ky, Py - ky)].to(dt)  # (Py, Px/2+1)
+    U = torch.randn((batch, ny, nx), dtype=dt, device="cuda")
+    Z = torch.zeros((batch, Py, Px), dtype=dt, device="cuda")
+    Y = torch.empty_like(U)
+
+    def run():
+        Z[:, :ny, :nx].copy_(U)
+        X = torch.fft.rfft2(Z)
+        X.mul_(lam)
+        Y.copy_(torch.fft.irfft2(X, s=(Py, Px), norm="forward")[:, :ny, :nx])
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        run()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps / batch
+    Yf = fl.frlap_apply_batch(plan, U)
+    diff = (torch.linalg.norm((Y - Yf).double()) / torch.linalg.norm(Yf.double())).item()
+    return {"ms_per_vector": ms, "unknowns_per_s": plan.M / (ms / 1e3), "rel_diff_vs_frlap": diff,
+            "what": "torch.fft rfft2/irfft2 on the zero-padded P x P grid + symbol multiply + crop"}
 
 
 def _timed(fn):

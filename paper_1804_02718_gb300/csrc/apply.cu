@@ -107,27 +107,24 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   C* buf = smem + (size_t)l * LS;
   T* rb = reinterpret_cast<T*>(buf);
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
-  // real sample i is component (i & 1) of complex element i / 2 (even/odd packing).  Each
-  // lane loads 2H / G = 32 samples, in batches of U issued before their stores.
-  {
-    constexpr int U = sizeof(io_t<T>) == 4 ? 32 : 16;
-#pragma unroll 1
-    for (int j0 = 0; j0 < 32; j0 += U) {
-      io_t<T> t[U];
+  // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
+  // for q >= H/2 (m >= 8): the upper half of the transform input.
+  C v[16];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = lane + (j0 + u) * G;
-        t[u] = (valid && i < n) ? src[i] : io_t<T>(0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = lane + (j0 + u) * G;
-        rb[2 * spad(i >> 1) + (i & 1)] = (valid && i < n) ? from_io<T>(t[u]) : T(0);
-      }
+  for (int m = 0; m < 16; ++m) {
+    const int q = lane + m * G;
+    io_t<T> re = io_t<T>(0), im = io_t<T>(0);
+    if (m < 8 && valid) {
+      if (2 * q < n) re = src[2 * q];
+      if (2 * q + 1 < n) im = src[2 * q + 1];
     }
+    v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
   }
-  __syncthreads();
-  fft_line<T, -1, true, false>(buf, logH, lane, tw, logP);
+  fft_regs<T, -1, true>(v, buf, logH, lane, tw, logP, false);
+  line_sync(logH);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
+  line_sync(logH);
   // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
   for (int k = lane; k <= H / 2; k += G) {
     const int km = H - k;
@@ -193,12 +190,40 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
       buf[spad(km)] = (a + b) + mul_i<1>(cmulc(a - b, tw[km]));
     }
   }
-  __syncthreads();
-  fft_line<T, 1, false, true>(buf, logH, lane, tw, logP);
+  line_sync(logH);
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
+  fft_regs<T, 1, false>(v, buf, logH, lane, tw, logP, true);
+  // v[m] = y[2q] + i y[2q+1] (times P), q = lane + m G; n <= H keeps only m < 8
   if (line < nlines) {
-    const T* rb = reinterpret_cast<const T*>(buf);
     io_t<T>* dst = out + (size_t)line * ldo;
-    for (int i = lane; i < n; i += G) dst[i] = to_io<T>(rb[2 * spad(i >> 1) + (i & 1)]);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int q = lane + m * G;
+      if (2 * q < n) dst[2 * q] = to_io<T>(v[m].x);
+      if (2 * q + 1 < n) dst[2 * q + 1] = to_io<T>(v[m].y);
+    }
+  }
+}
+
+// The cropped output of k_colmul: column blockIdx.x * TL + tid / G, elements lane + m G < n
+// (m < 8; n <= P/2), conjugated if CONJ.  The thread's column and lane are re-derived from
+// the special registers here, not kept live across both transforms (that spilled).
+template <bool CONJ, typename C>
+__device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int ncols, int n, size_t ld, int logP,
+                                           int TL) {
+  unsigned tid;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+  const int G = 1 << (logP - 4);
+  const int lane = (int)tid & (G - 1);
+  const int col = (int)blockIdx.x * TL + ((int)tid >> (logP - 4));
+  if (col >= ncols) return;
+  C* out = data + (size_t)col * ld;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = lane + m * G;
+    if (i < n) out[i] = CONJ ? conjg(v[m]) : v[m];
   }
 }
 
@@ -223,7 +248,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   C* line = data + (size_t)(valid ? col : 0) * ld;
-  load_line<C>(buf, line, lane, G, n, valid);
+  // lane holds elements lane + m G; n <= P/2, so m >= 8 is the zero padding
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int i = lane + m * G;
+    v[m] = (m < 8 && valid && i < n) ? line[i] : czero<C>();
+  }
   // line-major symbol: the folded line of this column is contiguous
   auto symbol_row = [&]() -> const T* {
     const int c = valid ? col : 0;
@@ -231,20 +262,16 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
     const int kx = c >> map.logPy, ky = c & (map.Py - 1);
     return lam + ((size_t)kx * map.Hy1 + min(ky, map.Py - ky)) * map.Hz1;
   };
-  __syncthreads();
   if constexpr (!std::is_same<T, dfl>::value) {
-    // FP64 prunes the first stage (zero upper half) and the last (cropped output)
-    fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
+    fft_regs<T, -1, true>(v, buf, logP, lane, tw, logPtab, false);
     const T* __restrict__ lrow = symbol_row();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int k = lane + j * G;
-      buf[spad(k)] = lrow[min(k, P - k)] * buf[spad(k)];
+    for (int m = 0; m < 16; ++m) {
+      const int k = lane + m * G;
+      v[m] = lrow[min(k, P - k)] * v[m];
     }
-    __syncthreads();
-    fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
-    if (valid)
-      for (int i = lane; i < n; i += G) line[i] = buf[spad(i)];
+    fft_regs<T, 1, false>(v, buf, logP, lane, tw, logPtab, true);
+    store_line<false>(v, data, ncols, n, ld, logP, TL);
   } else {
     // Double-float: the inverse transform runs as conj(FFT(conj(.))), so both transforms
     // execute one copy of the forward code.  The double-float stages are long enough that
@@ -252,18 +279,16 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
     // costs more in register spills than it saves.
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-      fft_line<T, -1>(buf, logP, lane, tw, logPtab);
+      fft_regs<T, -1, false>(v, buf, logP, lane, tw, logPtab, pass == 1);
       if (pass == 1) break;
       const T* __restrict__ lrow = symbol_row();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int k = lane + j * G;
-        buf[spad(k)] = conjg(lrow[min(k, P - k)] * buf[spad(k)]);
+      for (int m = 0; m < 16; ++m) {
+        const int k = lane + m * G;
+        v[m] = conjg(lrow[min(k, P - k)] * v[m]);
       }
-      __syncthreads();
     }
-    if (valid)
-      for (int i = lane; i < n; i += G) line[i] = conjg(buf[spad(i)]);
+    store_line<true>(v, data, ncols, n, ld, logP, TL);
   }
 }
 
@@ -291,9 +316,16 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   const int LS = sline(P);
   C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
-  load_line<C>(buf, src, lane, G, n, valid);
-  __syncthreads();
-  fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int i = lane + m * G;
+    v[m] = (m < 8 && valid && i < n) ? src[i] : czero<C>();
+  }
+  fft_regs<T, -1, true>(v, buf, logP, lane, tw, logPtab, false);
+  line_sync(logP);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
   __syncthreads();
   C* dst = out + g * gout;
   const int total = TL * P;
@@ -330,10 +362,17 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   load_transposed<C>(smem, src, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
-  fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
+  fft_regs<T, 1, false>(v, buf, logP, lane, tw, logPtab, true);
   if (line < nlines) {
     C* dst = out + g * gout + (size_t)line * ldo;
-    for (int i = lane; i < n; i += G) dst[i] = buf[spad(i)];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = lane + m * G;
+      if (i < n) dst[i] = v[m];
+    }
   }
 }
 
