@@ -1,0 +1,11 @@
+// FP32 instances of the FFT apply (kernels and launchers in apply_impl.cuh).
+#include "apply_impl.cuh"
+
+namespace frlap {
+
+template cudaError_t apply_batch_launch<float>(const Plan&, int, const float*, float*, size_t, void*, cudaStream_t,
+                                               const int*, int, const float*, size_t, cudaEvent_t const*);
+template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
+                                         cudaEvent_t const*, const float*);
+
+}  // namespace frlap

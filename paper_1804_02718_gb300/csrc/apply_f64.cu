@@ -1,0 +1,39 @@
+// FP64 instances of the FFT apply and of the spectrum transforms used by the learned
+// preconditioner (kernels and launchers in apply_impl.cuh), plus the engine-independent
+// entry points.
+#include "apply_impl.cuh"
+
+namespace frlap {
+
+// instantiated in apply_dfl.cu
+extern template cudaError_t apply_launch<dfl>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
+                                              cudaEvent_t const*, const dfl*);
+
+size_t apply_work_bytes(const Plan& p, int real_bytes) {
+  const size_t cb = 2 * (size_t)real_bytes;
+  size_t b = align256(p.s1_elems * cb);
+  if (p.d == 3) b += align256(p.s2_elems * cb);
+  return b;
+}
+
+cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
+                    cudaEvent_t const* ev) {
+  if (p.df64) return apply_launch<dfl>(p, u, y, work, s, skip, ev, nullptr);
+  return apply_launch<double>(p, u, y, work, s, skip, ev, nullptr);
+}
+
+template cudaError_t apply_batch_launch<double>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
+                                                const int*, int, const double*, size_t, cudaEvent_t const*);
+template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
+                                          cudaEvent_t const*, const double*);
+
+size_t spectrum_elems(const Plan& p) {
+  const size_t Hx1 = p.P[0] / 2 + 1;
+  return (p.d == 2) ? Hx1 * p.P[1] : Hx1 * p.P[1] * p.P[2];
+}
+
+template cudaError_t spectrum_forward<double>(const Plan&, const double*, double2*, void*, cudaStream_t);
+template cudaError_t spectrum_inverse<double>(const Plan&, const double2*, const double*, double*, void*,
+                                              cudaStream_t);
+
+}  // namespace frlap

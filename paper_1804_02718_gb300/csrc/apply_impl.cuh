@@ -13,6 +13,11 @@
 //       c2r_T  : S1[kx][(z,y)]              -> rows of y
 // Every stage reads and writes whole contiguous lines or TL-wide contiguous
 // tiles; every global index below is bounded by the line/tile validity tests.
+//
+// This header holds the kernel and launcher templates; apply_f32.cu, apply_f64.cu and
+// apply_dfl.cu instantiate them per engine (three translation units, built in parallel).
+#pragma once
+
 #include <type_traits>
 
 #include "common.cuh"
@@ -84,7 +89,7 @@ __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ s
   }
 }
 
-template <typename T>
+template <typename T, int REM>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
     }
     v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
   }
-  fft_regs<T, -1, true>(v, buf, logH, lane, tw, logP, false);
+  fft_regs<T, -1, true, REM>(v, buf, logH, lane, tw, logP, false);
   line_sync(logH);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   }
 }
 
-template <typename T>
+template <typename T, int REM>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, io_t<T>* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   C v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
-  fft_regs<T, 1, false>(v, buf, logH, lane, tw, logP, true);
+  fft_regs<T, 1, false, REM>(v, buf, logH, lane, tw, logP, true);
   // v[m] = y[2q] + i y[2q+1] (times P), q = lane + m G; n <= H keeps only m < 8
   if (line < nlines) {
     io_t<T>* dst = out + (size_t)line * ldo;
@@ -228,7 +233,7 @@ __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int
 }
 
 // lines of length n (contiguous, stride ld) -> zero-pad to P, FFT, * lambda, IFFT, crop, in place
-template <typename T>
+template <typename T, int REM>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
                          const int* __restrict__ skip, Batch bt) {
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
     const int i = lane + m * G;
-    v[m] = (m < 8 && valid && i < n) ? line[i] : czero<C>();
+    v[m] = (m < 8 && valid && i < n) ? ld_stream(&line[i]) : czero<C>();
   }
   // line-major symbol: the folded line of this column is contiguous
   auto symbol_row = [&]() -> const T* {
@@ -263,14 +268,14 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
     return lam + ((size_t)kx * map.Hy1 + min(ky, map.Py - ky)) * map.Hz1;
   };
   if constexpr (!std::is_same<T, dfl>::value) {
-    fft_regs<T, -1, true>(v, buf, logP, lane, tw, logPtab, false);
+    fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
     const T* __restrict__ lrow = symbol_row();
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int k = lane + m * G;
-      v[m] = lrow[min(k, P - k)] * v[m];
+      v[m] = ld_stream(&lrow[min(k, P - k)]) * v[m];
     }
-    fft_regs<T, 1, false>(v, buf, logP, lane, tw, logPtab, true);
+    fft_regs<T, 1, false, REM>(v, buf, logP, lane, tw, logPtab, true);
     store_line<false>(v, data, ncols, n, ld, logP, TL);
   } else {
     // Double-float: the inverse transform runs as conj(FFT(conj(.))), so both transforms
@@ -279,13 +284,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
     // costs more in register spills than it saves.
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-      fft_regs<T, -1, false>(v, buf, logP, lane, tw, logPtab, pass == 1);
+      fft_regs<T, -1, false, REM>(v, buf, logP, lane, tw, logPtab, pass == 1);
       if (pass == 1) break;
       const T* __restrict__ lrow = symbol_row();
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int k = lane + m * G;
-        v[m] = conjg(lrow[min(k, P - k)] * v[m]);
+        v[m] = conjg(ld_stream(&lrow[min(k, P - k)]) * v[m]);
       }
     }
     store_line<true>(v, data, ncols, n, ld, logP, TL);
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
-template <typename T>
+template <typename T, int REM>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
     const int i = lane + m * G;
     v[m] = (m < 8 && valid && i < n) ? src[i] : czero<C>();
   }
-  fft_regs<T, -1, true>(v, buf, logP, lane, tw, logPtab, false);
+  fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
   line_sync(logP);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
 }
 
 // transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
-template <typename T>
+template <typename T, int REM>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   C v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
-  fft_regs<T, 1, false>(v, buf, logP, lane, tw, logPtab, true);
+  fft_regs<T, 1, false, REM>(v, buf, logP, lane, tw, logPtab, true);
   if (line < nlines) {
     C* dst = out + g * gout + (size_t)line * ldo;
 #pragma unroll
@@ -463,14 +468,23 @@ cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-}  // namespace
-
-size_t apply_work_bytes(const Plan& p, int real_bytes) {
-  const size_t cb = 2 * (size_t)real_bytes;
-  size_t b = align256(p.s1_elems * cb);
-  if (p.d == 3) b += align256(p.s2_elems * cb);
-  return b;
+// The transform kernels are instantiated per REM = log2(P) mod 4 (the stage sequence is
+// then fixed at compile time); f(RemTag<REM>) launches the matching instance.
+template <int R>
+struct RemTag {
+  static constexpr int value = R;
+};
+template <typename F>
+cudaError_t with_rem(int logP, F&& f) {
+  switch (logP & 3) {
+    case 0: return f(RemTag<0>{});
+    case 1: return f(RemTag<1>{});
+    case 2: return f(RemTag<2>{});
+    default: return f(RemTag<3>{});
+  }
 }
+
+}  // namespace
 
 // B instances of the same shape: u, y at stride `vstride` elements, workspace at stride
 // apply_work_bytes(p), symbols at stride lam_stride (0: all share one), skip flags at
@@ -537,12 +551,17 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
-    cudaError_t e = set_smem(k_r2c_T<T>, sm);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    k_r2c_T<T><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(logPx - 1, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_r2c_T<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_r2c_T<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
   }
   LamMap map;
   map.d = p.d;
@@ -555,13 +574,18 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     const int G = p.P[1] >> 4;
     const int tl = pick_tl(sline(p.P[1]), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(p.P[1]) * eb;
-    cudaError_t e = set_smem(k_colmul<T>, sm);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int ncols = Hx + 1;
     const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    k_colmul<T><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(logPy, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_colmul<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_colmul<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
   } else {
     const int Py = p.P[1], Pz = p.P[2];
     // ---- stage 2: S1[kx][z][y] -> FFT_y -> S2[kx][ky][z]
@@ -569,42 +593,54 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int G = Py >> 4;
       const int tl = pick_tl(sline(Py), eb, G, budget, 64);
       const size_t sm = (size_t)tl * sline(Py) * eb;
-      cudaError_t e = set_smem(k_c2cT_fwd<T>, sm);
-      if (e != cudaSuccess) return e;
+      cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
-      if ((e = mark()) != cudaSuccess) return e;
-      k_c2cT_fwd<T><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz,
-                                                       nz, logPy, tl, tw[1], logPy, skip, b_ws);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    e = with_rem(logPy, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_c2cT_fwd<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_c2cT_fwd<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz, nz, logPy, tl, tw[1], logPy, skip, b_ws);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
     }
     // ---- stage 3: S2[kx][ky][:] -> FFT_z, * lambda, IFFT_z
     {
       const int G = Pz >> 4;
       const int tl = pick_tl(sline(Pz), eb, G, budget, 64);
       const size_t sm = (size_t)tl * sline(Pz) * eb;
-      cudaError_t e = set_smem(k_colmul<T>, sm);
-      if (e != cudaSuccess) return e;
+      cudaError_t e;
       const int ncols = (Hx + 1) * Py;
       const int grid = (ncols + tl - 1) / tl;
-      if ((e = mark()) != cudaSuccess) return e;
-      k_colmul<T><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz,
-                                                     skip, b_ws);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    e = with_rem(logPz, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_colmul<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_colmul<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz, skip, b_ws);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
     }
     // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
     {
       const int G = Py >> 4;
       const int tl = pick_tl(sline(Py), eb, G, budget, 64);
       const size_t sm = (size_t)tl * sline(Py) * eb;
-      cudaError_t e = set_smem(k_c2cT_inv<T>, sm);
-      if (e != cudaSuccess) return e;
+      cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
-      if ((e = mark()) != cudaSuccess) return e;
-      k_c2cT_inv<T><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny,
-                                                       ny, logPy, tl, tw[1], logPy, skip, b_ws);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    e = with_rem(logPy, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_c2cT_inv<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_c2cT_inv<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny, logPy, tl, tw[1], logPy, skip, b_ws);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
     }
   }
   // ---- last stage: S1[kx][row] -> rows of y
@@ -612,12 +648,17 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
-    cudaError_t e = set_smem(k_c2r_T<T>, sm);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    k_c2r_T<T><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(logPx - 1, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_c2r_T<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_c2r_T<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
   }
   return mark();
 }
@@ -633,31 +674,6 @@ cudaError_t apply_batch_launch(const Plan& p, int B, const io_t<T>* u, io_t<T>* 
                                cudaStream_t s, const int* skip, int skip_stride, const T* lam, size_t lam_stride,
                                cudaEvent_t const* ev) {
   return apply_launch_b<T>(p, B, u, y, vstride, work, s, skip, skip_stride, ev, lam, lam_stride);
-}
-
-cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
-                    cudaEvent_t const* ev) {
-  if (p.df64) return apply_launch<dfl>(p, u, y, work, s, skip, ev, nullptr);
-  return apply_launch<double>(p, u, y, work, s, skip, ev, nullptr);
-}
-
-template cudaError_t apply_batch_launch<double>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
-                                                const int*, int, const double*, size_t, cudaEvent_t const*);
-template cudaError_t apply_batch_launch<float>(const Plan&, int, const float*, float*, size_t, void*, cudaStream_t,
-                                               const int*, int, const float*, size_t, cudaEvent_t const*);
-template cudaError_t apply_batch_launch<dfl>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
-                                             const int*, int, const dfl*, size_t, cudaEvent_t const*);
-
-template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
-                                          cudaEvent_t const*, const double*);
-template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
-                                         cudaEvent_t const*, const float*);
-template cudaError_t apply_launch<dfl>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
-                                       cudaEvent_t const*, const dfl*);
-
-size_t spectrum_elems(const Plan& p) {
-  const size_t Hx1 = p.P[0] / 2 + 1;
-  return (p.d == 2) ? Hx1 * p.P[1] : Hx1 * p.P[1] * p.P[2];
 }
 
 // SP = F R^T u on the half spectrum: 2D [kx][ky], 3D [kx][ky][kz] (kx <= P_x/2, full ky, kz).
@@ -678,10 +694,14 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
-    if ((e = set_smem(k_r2c_T<T>, sm)) != cudaSuccess) return e;
-    k_r2c_T<T><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(u, S1, nrows, nx, nx, (size_t)nrows, p.logP[0] - 1, tl,
-                                                          tw[0], p.logP[0], nullptr, Batch{});
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(p.logP[0] - 1, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_r2c_T<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_r2c_T<T, REM><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(u, S1, nrows, nx, nx, (size_t)nrows, p.logP[0] - 1, tl, tw[0], p.logP[0], nullptr, Batch{});
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
   }
   const C* lines = S1;
   int ncols = Hx + 1, n = ny, logP = p.logP[1];
@@ -692,11 +712,15 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
     const int G = Py >> 4;
     const int tl = pick_tl(sline(Py), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(Py) * eb;
-    if ((e = set_smem(k_c2cT_fwd<T>, sm)) != cudaSuccess) return e;
     const int tiles = (nz + tl - 1) / tl;
-    k_c2cT_fwd<T><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz,
-                                                        nz, p.logP[1], tl, tw[1], p.logP[1], nullptr, Batch{});
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(p.logP[1], [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_c2cT_fwd<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_c2cT_fwd<T, REM><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz, nz, p.logP[1], tl, tw[1], p.logP[1], nullptr, Batch{});
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
     lines = S2;
     ncols = (Hx + 1) * Py;
     n = nz;
@@ -754,26 +778,30 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
     const int G = Py >> 4;
     const int tl = pick_tl(sline(Py), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(Py) * eb;
-    if ((e = set_smem(k_c2cT_inv<T>, sm)) != cudaSuccess) return e;
     const int tiles = (nz + tl - 1) / tl;
-    k_c2cT_inv<T><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny,
-                                                        p.logP[1], tl, tw[1], p.logP[1], nullptr, Batch{});
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(p.logP[1], [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_c2cT_inv<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_c2cT_inv<T, REM><<<(Hx + 1) * tiles, tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny, p.logP[1], tl, tw[1], p.logP[1], nullptr, Batch{});
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
   }
   {
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
-    if ((e = set_smem(k_c2r_T<T>, sm)) != cudaSuccess) return e;
-    k_c2r_T<T><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(S1, y, nrows, nx, (size_t)nrows, nx, p.logP[0] - 1, tl,
-                                                          tw[0], p.logP[0], nullptr, Batch{});
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = with_rem(p.logP[0] - 1, [&](auto tag) {
+      constexpr int REM = decltype(tag)::value;
+      cudaError_t e2 = set_smem(k_c2r_T<T, REM>, sm);
+      if (e2 != cudaSuccess) return e2;
+      k_c2r_T<T, REM><<<(nrows + tl - 1) / tl, tl * G, sm, s>>>(S1, y, nrows, nx, (size_t)nrows, nx, p.logP[0] - 1, tl, tw[0], p.logP[0], nullptr, Batch{});
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
-
-template cudaError_t spectrum_forward<double>(const Plan&, const double*, double2*, void*, cudaStream_t);
-template cudaError_t spectrum_inverse<double>(const Plan&, const double2*, const double*, double*, void*,
-                                              cudaStream_t);
 
 }  // namespace frlap

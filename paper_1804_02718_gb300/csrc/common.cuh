@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstring>
 
 #include <string>
 
@@ -34,6 +35,26 @@ template <> struct cplx_t<float> { using type = float2; };
 template <> struct cplx_t<double> { using type = double2; };
 template <> struct cplx_t<dfl> { using type = cdf; };
 template <typename T> using cplx = typename cplx_t<T>::type;
+
+// Load of data a kernel reads once (cache-streaming: evict-first in L1 and L2), so that the
+// twiddle tables keep the L1.  8- and 16-byte values: float2 / float4 / double2 / cdf; 4 and 8
+// byte scalars.
+template <typename V>
+__device__ __forceinline__ V ld_stream(const V* p) {
+  static_assert(sizeof(V) == 4 || sizeof(V) == 8 || sizeof(V) == 16, "ld_stream: 4, 8 or 16 bytes");
+  V r;
+  if constexpr (sizeof(V) == 4) {
+    const float t = __ldcs(reinterpret_cast<const float*>(p));
+    memcpy(&r, &t, 4);
+  } else if constexpr (sizeof(V) == 8) {
+    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    memcpy(&r, &t, 8);
+  } else {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    memcpy(&r, &t, 16);
+  }
+  return r;
+}
 
 // storage type of the real grid vectors and of the symbol for each compute type:
 // FP32 and FP64 compute and store in their own type; double-float computes in

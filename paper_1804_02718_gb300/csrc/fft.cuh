@@ -312,8 +312,8 @@ __device__ __forceinline__ void fft_line(cplx<T>* buf, int logL, int lane, const
 // ---------------------------------------------------------------------------------------
 // Register-resident transform.  The Stockham stages all read the same element set per
 // thread: lane j (of G = L/16) reads x[j + m G], m = 0..15.  So a caller can load that set
-// straight from global memory into registers, and after the last (radix-16, Ns = L/16)
-// stage the thread holds X[j + m G] in the same registers: it can multiply, start another
+// straight from global memory into registers, and after the last stage the thread holds
+// X[j + m G] in the same registers: it can multiply, start another
 // transform, or store to global memory without a shared-memory round trip.  Only the
 // exchanges between stages go through `buf` (padded layout, see spad).
 //
@@ -321,91 +321,141 @@ __device__ __forceinline__ void fft_line(cplx<T>* buf, int logL, int lane, const
 // sync_first: other threads may still be reading `buf` (a barrier precedes the first
 // write).  ZIN: x[L/2..L) is zero (first-stage DFTs take the zero-aware form for FP64).
 
-// First stage (Ns = 1) of radix R = 16 / B: butterfly b of this lane is j = lane + b G and
-// takes x[j + r L/R] = v[b + r B]; its output r goes to position j R + r.
+// Stage order.  REM = log2(L) mod 4 is a template parameter, so each kernel carries only
+// the stages its length needs.  The leftover radix-2^REM stage runs last for REM = 1, 2
+// (a leading radix-2/4 stage writes with stride 2/4 elements, which conflicts in shared
+// memory for 16-byte elements) and first for REM = 3 (measured faster for the 2048-point
+// row transforms).  A last stage of any radix R leaves its outputs in the register layout:
+// butterfly b of this lane is j = lane + b G (b < B = 16/R), takes x[j + r L/R] = v[b + r B]
+// and produces X[j + r L/R], which is again v[b + r B].
+
+// First stage (Ns = 1) of radix R: butterfly b is j = lane + b G with inputs v[b + r B];
+// its outputs replace them (v[b + r B] = output r, to go to position j R + r).
 template <typename T, int R, int SIGN, bool ZIN>
 __device__ __forceinline__ void regs_first_stage(cplx<T>* v) {
   using C = cplx<T>;
   constexpr int B = 16 / R;
   constexpr bool Z = ZIN && std::is_same<T, double>::value;
-  if constexpr (B > 1) {
-    C w[16];
 #pragma unroll
-    for (int b = 0; b < B; ++b)
+  for (int b = 0; b < B; ++b) {
+    C t[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) w[b * R + r] = v[b + r * B];
+    for (int r = 0; r < R; ++r) t[r] = v[b + r * B];
+    dftR<R, SIGN, Z>(t);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = w[i];
+    for (int r = 0; r < R; ++r) v[b + r * B] = t[r];
   }
-#pragma unroll
-  for (int b = 0; b < B; ++b) dftR<R, SIGN, Z>(&v[b * R]);
 }
 
-// write the first stage's outputs (index b R + r) to position (lane + b G) R + r
 template <typename T, int R>
 __device__ __forceinline__ void regs_first_write(cplx<T>* buf, const cplx<T>* v, int lane, int G) {
   constexpr int B = 16 / R;
 #pragma unroll
   for (int b = 0; b < B; ++b) {
-    const int o = (lane + b * G) * R;  // o + r never crosses a 16-element group (R divides 16)
-    const int ob = spad(o);
+    const int ob = spad((lane + b * G) * R);  // j R + r never crosses a 16-element group
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[ob + r] = v[b * R + r];
+    for (int r = 0; r < R; ++r) buf[ob + r] = v[b + r * B];
   }
 }
 
-template <typename T, int SIGN, bool ZIN>
+// Last stage (Ns = L/R) of radix R: k = j, twiddles W_L^{r j} = tw[(r j) << shift].
+template <typename T, int R, int SIGN>
+__device__ __forceinline__ void regs_last_stage(cplx<T>* v, int lane, int G, const cplx<T>* __restrict__ tw,
+                                                int shift) {
+  using C = cplx<T>;
+  constexpr int B = 16 / R;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = lane + b * G;
+    C t[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      t[r] = v[b + r * B];
+      if (r > 0) {
+        const C wr = tw[(r * j) << shift];
+        t[r] = (SIGN < 0) ? cmul(t[r], wr) : cmulc(t[r], wr);
+      }
+    }
+    dftR<R, SIGN, false>(t);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b + r * B] = t[r];
+  }
+}
+
+// v[m] = x[lane + m G] from buf
+template <typename T>
+__device__ __forceinline__ void regs_read(cplx<T>* v, const cplx<T>* buf, int lane, int G) {
+  const bool g16 = (G & 15) == 0;
+  const int rbase = spad(lane), rstep = G + (G >> 4);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = buf[g16 ? rbase + m * rstep : spad(lane + m * G)];
+}
+
+// radix-16 stage with Ns = 2^logNs on v: twiddles W_{16 Ns}^{r k}, k = lane mod Ns
+template <typename T, int SIGN>
+__device__ __forceinline__ void regs_stage16(cplx<T>* v, int lane, int logNs, const cplx<T>* __restrict__ tw,
+                                             int logPtab) {
+  if (logNs > 0) {
+    const int k = lane & ((1 << logNs) - 1);
+    cplx<T> w[16];
+    twiddles16<T>(w, tw, k, logPtab - logNs - 4);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = (SIGN < 0) ? cmul(v[r], w[r]) : cmulc(v[r], w[r]);
+  }
+  dft16<SIGN>(v);
+}
+
+// outputs of a radix-16 stage with Ns = 2^logNs: element r to (lane - k) 16 + k + r Ns
+template <typename T>
+__device__ __forceinline__ void regs_write16(cplx<T>* buf, const cplx<T>* v, int lane, int logNs) {
+  const int Ns = 1 << logNs;
+  const int k = lane & (Ns - 1);
+  const int o = (lane - k) * 16 + k;
+  const bool ns16 = (Ns & 15) == 0;
+  const int obase = spad(o), sstep = Ns + (Ns >> 4);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) buf[ns16 ? obase + r * sstep : spad(o + r * Ns)] = v[r];
+}
+
+template <typename T, int SIGN, bool ZIN, int REM>
 __device__ __forceinline__ void fft_regs(cplx<T>* v, cplx<T>* buf, int logL, int lane,
                                          const cplx<T>* __restrict__ tw, int logPtab, bool sync_first) {
   const int G = 1 << (logL - 4);
-  const int rem = logL & 3;
-  int logNs;
-  if (rem == 1) {
-    regs_first_stage<T, 2, SIGN, ZIN>(v);
-    if (sync_first) line_sync(logL);
-    regs_first_write<T, 2>(buf, v, lane, G);
-    logNs = 1;
-  } else if (rem == 2) {
-    regs_first_stage<T, 4, SIGN, ZIN>(v);
-    if (sync_first) line_sync(logL);
-    regs_first_write<T, 4>(buf, v, lane, G);
-    logNs = 2;
-  } else if (rem == 3) {
+  if constexpr (REM == 3) {
     regs_first_stage<T, 8, SIGN, ZIN>(v);
     if (sync_first) line_sync(logL);
     regs_first_write<T, 8>(buf, v, lane, G);
-    logNs = 3;
+    int logNs = 3;
+    while (true) {
+      line_sync(logL);
+      regs_read<T>(v, buf, lane, G);
+      regs_stage16<T, SIGN>(v, lane, logNs, tw, logPtab);
+      if (logNs + 4 == logL) return;
+      line_sync(logL);
+      regs_write16<T>(buf, v, lane, logNs);
+      logNs += 4;
+    }
   } else {
     regs_first_stage<T, 16, SIGN, ZIN>(v);
-    if (logL == 4) return;  // one stage: output r of lane 0 is X[r]
+    if (REM == 0 && logL == 4) return;  // one stage: output r of lane 0 is X[r]
     if (sync_first) line_sync(logL);
-    regs_first_write<T, 16>(buf, v, lane, G);
-    logNs = 4;
-  }
-  const bool g16 = (G & 15) == 0;
-  const int rbase = spad(lane), rstep = G + (G >> 4);
-  while (true) {
-    line_sync(logL);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = buf[g16 ? rbase + m * rstep : spad(lane + m * G)];
-    // radix-16 stage with Ns = 2^logNs: twiddles W_{16 Ns}^{r k}, k = lane mod Ns
-    const int Ns = 1 << logNs;
-    const int k = lane & (Ns - 1);
-    {
-      cplx<T> w[16];
-      twiddles16<T>(w, tw, k, logPtab - logNs - 4);
-#pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = (SIGN < 0) ? cmul(v[r], w[r]) : cmulc(v[r], w[r]);
+    regs_write16<T>(buf, v, lane, 0);
+    int logNs = 4;
+    while (true) {
+      line_sync(logL);
+      regs_read<T>(v, buf, lane, G);
+      if constexpr (REM != 0) {
+        if (logNs + REM == logL) {
+          regs_last_stage<T, (1 << REM), SIGN>(v, lane, G, tw, logPtab - logL);
+          return;
+        }
+      }
+      regs_stage16<T, SIGN>(v, lane, logNs, tw, logPtab);
+      if (logNs + 4 == logL) return;
+      line_sync(logL);
+      regs_write16<T>(buf, v, lane, logNs);
+      logNs += 4;
     }
-    dft16<SIGN>(v);
-    logNs += 4;
-    if (logNs == logL) return;  // Ns was L/16: output r sits at lane + r G
-    line_sync(logL);
-    const int o = (lane - k) * 16 + k;
-    const bool ns16 = (Ns & 15) == 0;
-    const int obase = spad(o), sstep = Ns + (Ns >> 4);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) buf[ns16 ? obase + r * sstep : spad(o + r * Ns)] = v[r];
   }
 }
 
