@@ -110,7 +110,6 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   const bool valid = line < nlines;
   const int LS = sline(H);
   C* buf = smem + (size_t)l * LS;
-  T* rb = reinterpret_cast<T*>(buf);
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
   // for q >= H/2 (m >= 8): the upper half of the transform input.
@@ -130,24 +129,17 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
   line_sync(logH);
-  // unpack the half-length transform of the packed even/odd samples into X[k], k = 0..H
+  // unpack the half-length transform Z of the packed samples into X[k], k = 0..H:
+  // with a = Z[k], b = conj Z[H-k], E = (a + b)/2 and O = -i (a - b)/2,
+  // X[k] = E + W^k O and X[H-k] = conj(E - W^k O)  (W = exp(-2 pi i / 2H); one product per pair)
   for (int k = lane; k <= H / 2; k += G) {
     const int km = H - k;
-    const C zk = buf[spad(k)];
-    const C zm = buf[spad(km & (H - 1))];
-    constexpr T half = T(0.5);
-    {
-      const C a = zk, b = conjg(zm);
-      const C xe = half * (a + b);
-      const C xo = half * mul_i<-1>(a - b);
-      buf[spad(k)] = xe + cmul(tw[k], xo);
-    }
-    if (k != km) {
-      const C a = zm, b = conjg(zk);
-      const C xe = half * (a + b);
-      const C xo = half * mul_i<-1>(a - b);
-      buf[spad(km)] = xe + cmul(tw[km], xo);
-    }
+    const C a = buf[spad(k)];
+    const C b = conjg(buf[spad(km & (H - 1))]);
+    const C e = halve(a + b);
+    const C t = cmul(tw[k], halve(mul_i<-1>(a - b)));
+    buf[spad(k)] = e + t;
+    if (k != km) buf[spad(km)] = conjg(e - t);
   }
   __syncthreads();
   const int total = TL * (H + 1);
@@ -181,19 +173,17 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   load_transposed<C>(smem, in, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
-  // repack: Z[k] = (X[k] + conj X[H-k]) + i W^{-k} (X[k] - conj X[H-k]), so that the
-  // unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1])
+  // repack: Z[k] = A + i T with A = X[k] + conj X[H-k], T = W^{-k} (X[k] - conj X[H-k]), so that
+  // the unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1]); the partner is
+  // Z[H-k] = conj(A - i T)  (one product per pair)
   for (int k = lane; k <= H / 2; k += G) {
     const int km = H - k;
-    const C xk = buf[spad(k)], xm = buf[spad(km)];
-    {
-      const C a = xk, b = conjg(xm);
-      buf[spad(k)] = (a + b) + mul_i<1>(cmulc(a - b, tw[k]));
-    }
-    if (k != km && km != H) {
-      const C a = xm, b = conjg(xk);
-      buf[spad(km)] = (a + b) + mul_i<1>(cmulc(a - b, tw[km]));
-    }
+    const C xk = buf[spad(k)];
+    const C b = conjg(buf[spad(km)]);
+    const C A = xk + b;
+    const C iT = mul_i<1>(cmulc(xk - b, tw[k]));
+    buf[spad(k)] = A + iT;
+    if (k != km && km != H) buf[spad(km)] = conjg(A - iT);
   }
   line_sync(logH);
   C v[16];

@@ -80,6 +80,12 @@ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_fl
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+// a / 2, exactly (a power-of-two scaling of each component)
+__device__ __forceinline__ float2 halve(float2 a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+__device__ __forceinline__ double2 halve(double2 a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+__device__ __forceinline__ cdf halve(cdf a) {
+  return cdf{dfl(0.5f * a.x.hi, 0.5f * a.x.lo), dfl(0.5f * a.y.hi, 0.5f * a.y.lo)};
+}
 __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 
 // complex product a*b
