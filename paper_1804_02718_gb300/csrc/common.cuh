@@ -80,6 +80,12 @@ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_fl
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+// Sums that only feed another sum: plain for FP32 / FP64; without the closing renormalisation
+// for double-float (dfloat.cuh).
+__device__ __forceinline__ float2 add_lazy(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub_lazy(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 add_lazy(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 sub_lazy(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 // a / 2, exactly (a power-of-two scaling of each component)
 __device__ __forceinline__ float2 halve(float2 a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
 __device__ __forceinline__ double2 halve(double2 a) { return make_double2(0.5 * a.x, 0.5 * a.y); }

@@ -36,9 +36,11 @@ __device__ __forceinline__ void dft2(C& a, C& b) {
   b = t;
 }
 
+// The first-level sums feed only the second level, so they skip the double-float
+// renormalisation (add_lazy); the outputs are normalised.
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
-  C s0 = a + c, d0 = a - c, s1 = b + d, d1 = mul_i<SIGN>(b - d);
+  C s0 = add_lazy(a, c), d0 = sub_lazy(a, c), s1 = add_lazy(b, d), d1 = mul_i<SIGN>(sub_lazy(b, d));
   a = s0 + s1;
   c = s0 - s1;
   b = d0 + d1;

@@ -219,3 +219,22 @@ def test_apply_batch_full_size_and_errors(frlap):
     assert lib.frlap_apply_batch(plan.handle, 0, p(U.data_ptr()), p(Y.data_ptr()), w, None, None) == 1
     assert lib.frlap_apply_batch(plan.handle, 8, p(U.data_ptr()), p(U[4].data_ptr()), w, None, None) == 1  # overlap
     assert frlap.frlap_apply_batch_workspace_bytes(plan, 8) == 8 * plan.workspace_bytes(frlap.FRLAP_OP_APPLY)
+
+
+@pytest.mark.parametrize("d,N,alpha", [(2, 512, 1.5), (2, 2048, 1.9), (3, 64, 1.2)])
+def test_double_float_accuracy_level(frlap, d, N, alpha):
+    """The double-float engine stays at FP64-class accuracy, well inside the 1e-12 parity bound:
+    normwise against the native FP64 engine (itself ~1e-16), on N(0,1) and on a smooth input."""
+    h = 2.0 / N
+    Ns = (N,) * d
+    p64 = frlap.Plan(d, alpha, h, Ns, prec=frlap.FRLAP_F64)
+    pdf = frlap.Plan(d, alpha, h, Ns, prec=frlap.FRLAP_DF64)
+    lam_max = float(p64.symbol().abs().max().item() * np.prod(p64.P))
+    for u in (inp.normal_field(Ns, seed=7), inp.gaussian_sum_field(Ns, h, seed=8)):
+        ut = _t(u)
+        y64 = frlap.frlap_apply(p64, ut)
+        ydf = frlap.frlap_apply(pdf, ut)
+        err = (torch.linalg.norm(ydf - y64) / (lam_max * torch.linalg.norm(ut))).item()
+        rel = (torch.linalg.norm(ydf - y64) / torch.linalg.norm(y64)).item()
+        print(f"double-float vs FP64: d={d} N={N} alpha={alpha}: normwise {err:.2e}, relative {rel:.2e}")
+        assert err <= 2e-14, err
