@@ -108,6 +108,11 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
+// products that only feed a sum: as cmul / cmulc here, unrenormalised for double-float
+__device__ __forceinline__ float2 cmul_lazy(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 cmul_lazy(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float2 cmulc_lazy(float2 a, float2 b) { return cmulc(a, b); }
+__device__ __forceinline__ double2 cmulc_lazy(double2 a, double2 b) { return cmulc(a, b); }
 template <typename C> __device__ __forceinline__ C conjg(C a) { a.y = -a.y; return a; }
 // multiply by -i (forward) or +i (inverse): sign = -1 gives -i*a
 template <int SIGN, typename C> __device__ __forceinline__ C mul_i(C a) {

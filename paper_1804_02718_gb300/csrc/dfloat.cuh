@@ -100,6 +100,23 @@ __device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d) {
   return fast_two_sum(s, __fadd_rn(t, __fadd_rn(e, f)));
 }
 
+// df_dot2 without the closing renormalisation (16 instructions), for a product that only
+// feeds a sum
+__device__ __forceinline__ dfl df_dot2_lazy(dfl a, dfl b, dfl c, dfl d) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float q = __fmul_rn(c.hi, d.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  float f = __fmaf_rn(c.hi, d.hi, -q);
+  const float s = __fadd_rn(p, q);
+  const float v = __fsub_rn(s, p);
+  const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(q, v));
+  e = __fmaf_rn(a.hi, b.lo, e);
+  f = __fmaf_rn(c.hi, d.lo, f);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  f = __fmaf_rn(c.lo, d.hi, f);
+  return dfl(s, __fadd_rn(t, __fadd_rn(e, f)));
+}
+
 __device__ __forceinline__ cdf operator+(cdf a, cdf b) { return cdf{a.x + b.x, a.y + b.y}; }
 __device__ __forceinline__ cdf add_lazy(cdf a, cdf b) { return cdf{add_lazy(a.x, b.x), add_lazy(a.y, b.y)}; }
 __device__ __forceinline__ cdf sub_lazy(cdf a, cdf b) { return cdf{add_lazy(a.x, -b.x), add_lazy(a.y, -b.y)}; }
@@ -111,6 +128,13 @@ __device__ __forceinline__ cdf cmul(cdf a, cdf b) {
 // a * conj(b)
 __device__ __forceinline__ cdf cmulc(cdf a, cdf b) {
   return cdf{df_dot2(a.x, b.x, a.y, b.y), df_dot2(a.y, b.x, -a.x, b.y)};
+}
+// products that only feed a sum (the twiddle factors ahead of a DFT kernel)
+__device__ __forceinline__ cdf cmul_lazy(cdf a, cdf b) {
+  return cdf{df_dot2_lazy(a.x, b.x, -a.y, b.y), df_dot2_lazy(a.x, b.y, a.y, b.x)};
+}
+__device__ __forceinline__ cdf cmulc_lazy(cdf a, cdf b) {
+  return cdf{df_dot2_lazy(a.x, b.x, a.y, b.y), df_dot2_lazy(a.y, b.x, -a.x, b.y)};
 }
 
 }  // namespace frlap

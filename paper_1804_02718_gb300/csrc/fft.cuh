@@ -108,7 +108,7 @@ __device__ __forceinline__ void dft16_tail(C* v) {
     for (int j2 = 1; j2 < 4; ++j2) {
       const int m = j2 * k1;
       if (m == 4) v[4 * k1 + j2] = mul_i<SIGN>(v[4 * k1 + j2]);  // W16^4 = SIGN i
-      else v[4 * k1 + j2] = cmul(v[4 * k1 + j2], w16<SIGN, T>(m));
+      else v[4 * k1 + j2] = cmul_lazy(v[4 * k1 + j2], w16<SIGN, T>(m));  // feeds the second-level sums
     }
   // length-4 DFTs over j2 for each k1: X[k1 + 4 k2]
   C out[16];
@@ -375,7 +375,7 @@ __device__ __forceinline__ void regs_last_stage(cplx<T>* v, int lane, int G, con
       t[r] = v[b + r * B];
       if (r > 0) {
         const C wr = tw[(r * j) << shift];
-        t[r] = (SIGN < 0) ? cmul(t[r], wr) : cmulc(t[r], wr);
+        t[r] = (SIGN < 0) ? cmul_lazy(t[r], wr) : cmulc_lazy(t[r], wr);
       }
     }
     dftR<R, SIGN, false>(t);
@@ -402,7 +402,7 @@ __device__ __forceinline__ void regs_stage16(cplx<T>* v, int lane, int logNs, co
     cplx<T> w[16];
     twiddles16<T>(w, tw, k, logPtab - logNs - 4);
 #pragma unroll
-    for (int r = 1; r < 16; ++r) v[r] = (SIGN < 0) ? cmul(v[r], w[r]) : cmulc(v[r], w[r]);
+    for (int r = 1; r < 16; ++r) v[r] = (SIGN < 0) ? cmul_lazy(v[r], w[r]) : cmulc_lazy(v[r], w[r]);
   }
   dft16<SIGN>(v);
 }
