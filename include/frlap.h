@@ -60,7 +60,12 @@ typedef enum {
  * DF64: FP64 vectors in memory, FFT stages in double-float arithmetic (pairs
  * of FP32 numbers, about 48 significant bits), which GB300 runs several times
  * faster than FP64 at an accuracy within the FP64 tolerance of the apply.
- * MIXED_DF64: MIXED with the FP64 side computed as in DF64. */
+ * MIXED_DF64: MIXED with the FP64 side computed as in DF64.
+ * In frlap_pcg_solve and the Allen-Cahn calls the iterations use the plan's
+ * engine, but every residual f - B x that starts, restarts or confirms a solve
+ * is computed with the native FP64 engine (double-float rounding, about
+ * 5e-15 lambda_max ||x||, would otherwise set a residual floor near 1e-10 ||f||
+ * at 2047^2). */
 typedef enum { FRLAP_F64 = 0, FRLAP_F32 = 1, FRLAP_MIXED = 2, FRLAP_DF64 = 3, FRLAP_MIXED_DF64 = 4 } frlap_prec;
 
 /* Which scratch size frlap_workspace_bytes reports. */

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
 // power of two, in whole warps.
 // (every apply kernel is compiled for at most 512 threads per CTA; CTAs of at most 256
 // threads measured fastest: more independent CTAs per SM overlap their phases)
-int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
+int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines, long long lines = 1LL << 40) {
   int tl = budget / (len * elem_bytes);
   tl = tl < 1 ? 1 : tl;
   while (tl > 1 && tl * G > 256) --tl;
@@ -449,7 +449,10 @@ int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines) {
   while (2 * p2 <= tl) p2 *= 2;
   tl = p2;
   // whole warps (the FFT stages of lines shorter than 32 lanes end with a warp barrier)
-  if (G < 32 && tl < 32 / G) tl = 32 / G;
+  const int q = G < 32 ? 32 / G : 1;
+  if (tl < q) tl = q;
+  // a launch of few lines in all: fewer lines per CTA, so that it still spreads over the SMs
+  while (tl > q && (lines + tl - 1) / tl < 2 * 152) tl /= 2;
   return tl;
 }
 
@@ -539,7 +542,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   // ---- stage 1: rows of u -> S1[kx][row]
   {
     const int G = Hx >> 4;
-    const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
+    const int tl = pick_tl(sline(Hx), eb, G, budget, 64, (long long)nrows * B);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
@@ -562,7 +565,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   map.Hz1 = p.d == 3 ? p.P[2] / 2 + 1 : 1;
   if (p.d == 2) {
     const int G = p.P[1] >> 4;
-    const int tl = pick_tl(sline(p.P[1]), eb, G, budget, 64);
+    const int tl = pick_tl(sline(p.P[1]), eb, G, budget, 64, (long long)(Hx + 1) * B);
     const size_t sm = (size_t)tl * sline(p.P[1]) * eb;
     cudaError_t e;
     const int ncols = Hx + 1;
@@ -581,7 +584,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     // ---- stage 2: S1[kx][z][y] -> FFT_y -> S2[kx][ky][z]
     {
       const int G = Py >> 4;
-      const int tl = pick_tl(sline(Py), eb, G, budget, 64);
+      const int tl = pick_tl(sline(Py), eb, G, budget, 64, (long long)nz * (Hx + 1) * B);
       const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
@@ -599,7 +602,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     // ---- stage 3: S2[kx][ky][:] -> FFT_z, * lambda, IFFT_z
     {
       const int G = Pz >> 4;
-      const int tl = pick_tl(sline(Pz), eb, G, budget, 64);
+      const int tl = pick_tl(sline(Pz), eb, G, budget, 64, (long long)(Hx + 1) * Py * B);
       const size_t sm = (size_t)tl * sline(Pz) * eb;
       cudaError_t e;
       const int ncols = (Hx + 1) * Py;
@@ -617,7 +620,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
     {
       const int G = Py >> 4;
-      const int tl = pick_tl(sline(Py), eb, G, budget, 64);
+      const int tl = pick_tl(sline(Py), eb, G, budget, 64, (long long)nz * (Hx + 1) * B);
       const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
@@ -636,7 +639,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   // ---- last stage: S1[kx][row] -> rows of y
   {
     const int G = Hx >> 4;
-    const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
+    const int tl = pick_tl(sline(Hx), eb, G, budget, 64, (long long)nrows * B);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;

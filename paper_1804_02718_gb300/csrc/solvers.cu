@@ -22,6 +22,11 @@ namespace {
 
 constexpr int kBlocks = 2 * 152;  // grid of the vector kernels: two CTAs per SM
 constexpr int kThreads = 512;
+// grid for n elements: two CTAs per SM, fewer for short vectors (the reductions use gridDim.x)
+inline unsigned vgrid(size_t n) {
+  const size_t b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < 1 ? 1 : (b > (size_t)kBlocks ? (size_t)kBlocks : b));
+}
 
 struct CgState {
   double rr;        // r . r
@@ -35,6 +40,7 @@ struct CgState {
   int status;       // frlap_status of the iteration
   int iters;
   unsigned counter; // last-block ticket for the reductions
+  unsigned passes;  // loop passes of the graph-launched iterations
 };
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -245,6 +251,14 @@ __global__ void k_set_state(CgState* S, double sigma, double s) {
   S->done = 0;
   S->status = FRLAP_OK;
   S->iters = 0;
+  S->passes = 0u;
+}
+
+// loop control of the graph-launched CG: another pass while the solve runs (bounded)
+__global__ void k_cg_control(CgState* S, unsigned max_passes, cudaGraphConditionalHandle h) {
+  const unsigned c = S->passes + 1u;
+  S->passes = c;
+  cudaGraphSetConditional(h, (!S->done && c < max_passes) ? 1u : 0u);
 }
 
 // true residual norms: out[0] = ||f - (sigma x + s q)||^2, out[1] = ||f||^2
@@ -303,6 +317,17 @@ static cudaError_t apply_T(const Plan& p, const T* u, T* y, void* work, cudaStre
   else return apply_launch<float>(p, u, y, work, s, skip);
 }
 
+// The residuals f - B x that start, restart and confirm a solve: FP64 vectors always go
+// through the native FP64 engine, also on double-float plans.  The iterations may run on
+// double-float (48-bit products, 3x faster), but a residual computed with it carries that
+// rounding (about 5e-15 lambda_max ||x||), which at 2047^2 already sits near 1e-10 ||f||;
+// the native residual lets a restart remove the drift, as in iterative refinement.
+template <typename T>
+static cudaError_t apply_residual(const Plan& p, const T* u, T* y, void* work, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) return apply_launch<double>(p, u, y, work, s, nullptr);
+  else return apply_launch<float>(p, u, y, work, s, nullptr);
+}
+
 // workspace of one (P)CG solve in precision T:
 // [apply work T][apply work FP32 (precond, T = double)][r][p][q][z][r32][z32][partials][state]
 size_t cg_work_bytes(const Plan& p, int eb) {
@@ -358,7 +383,7 @@ template <typename T>
 static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu, cudaStream_t st) {
   const float* src;
   if constexpr (sizeof(T) == 8) {
-    k_to32<T><<<kBlocks, kThreads, 0, st>>>(reinterpret_cast<const T*>(b.r), b.r32, p.M, b.S);
+    k_to32<T><<<vgrid(p.M), kThreads, 0, st>>>(reinterpret_cast<const T*>(b.r), b.r32, p.M, b.S);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     src = b.r32;
@@ -385,46 +410,92 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   k_set_state<<<1, 1, 0, st>>>(S, sigma, s);
   FRLAP_LAUNCH_CHECK("k_set_state");
   if (use_x0) {
-    cudaError_t e = apply_T<T>(p, x, q, b.awork, st, nullptr);
+    cudaError_t e = apply_residual<T>(p, x, q, b.awork, st);
     if (e != cudaSuccess) return cuda_fail(e, "apply (initial residual)");
   }
-  k_cg_init<T><<<kBlocks, kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
+  k_cg_init<T><<<vgrid(n), kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
   FRLAP_LAUNCH_CHECK("k_cg_init");
   if (mu) {
     cudaError_t e = precondition<T>(p, b, mu, st);
     if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
-    k_pcg_start<T, float><<<kBlocks, kThreads, 0, st>>>(r, b.z32, z, pv, n, b.partials, S);
+    k_pcg_start<T, float><<<vgrid(n), kThreads, 0, st>>>(r, b.z32, z, pv, n, b.partials, S);
   } else {
-    k_pcg_start<T, T><<<kBlocks, kThreads, 0, st>>>(r, nullptr, z, pv, n, b.partials, S);
+    k_pcg_start<T, T><<<vgrid(n), kThreads, 0, st>>>(r, nullptr, z, pv, n, b.partials, S);
   }
   FRLAP_LAUNCH_CHECK("k_pcg_start");
   if (snap && nsnap > 0) FRLAP_CUDA_TRY(cudaMemcpyAsync(snap, x, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
   const int* done = &S->done;
+  // one iteration on stream `ss`; the snapshot copy (training pairs) needs the host's count
+  auto iteration = [&](cudaStream_t ss, int it) -> cudaError_t {
+    cudaError_t e = apply_T<T>(p, pv, q, b.awork, ss, done);
+    if (e != cudaSuccess) return e;
+    k_cg_pq<T><<<vgrid(n), kThreads, 0, ss>>>(pv, q, n, b.partials, S);
+    k_cg_update<T><<<vgrid(n), kThreads, 0, ss>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr);
+    if (snap && it + 1 < nsnap) {
+      e = cudaMemcpyAsync(snap + (size_t)(it + 1) * n, x, n * sizeof(T), cudaMemcpyDeviceToDevice, ss);
+      if (e != cudaSuccess) return e;
+    }
+    if (mu) {
+      e = precondition<T>(p, b, mu, ss);
+      if (e != cudaSuccess) return e;
+      k_pcg_beta<T, float><<<vgrid(n), kThreads, 0, ss>>>(r, b.z32, z, q, n, b.partials, S);
+    }
+    k_cg_dir<T><<<vgrid(n), kThreads, 0, ss>>>(z, pv, n, S);
+    return cudaGetLastError();
+  };
+  // The first iterations run as plain launches; when the solve goes on (and takes no
+  // snapshots), the rest runs as one CUDA-graph launch: a conditional WHILE node whose body
+  // is one iteration plus k_cg_control, which ends the loop once the update kernel has set
+  // `done` (converged, breakdown or maxit), and after at most maxit + 2 passes regardless.
   const int chunk = 8;
   int launched = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      cudaError_t e = apply_T<T>(p, pv, q, b.awork, st, done);
-      if (e != cudaSuccess) return cuda_fail(e, "apply (CG)");
-      k_cg_pq<T><<<kBlocks, kThreads, 0, st>>>(pv, q, n, b.partials, S);
-      k_cg_update<T><<<kBlocks, kThreads, 0, st>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr);
-      if (snap && launched + c + 1 < nsnap)
-        FRLAP_CUDA_TRY(cudaMemcpyAsync(snap + (size_t)(launched + c + 1) * n, x, n * sizeof(T),
-                                       cudaMemcpyDeviceToDevice, st));
-      if (mu) {
-        e = precondition<T>(p, b, mu, st);
-        if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
-        k_pcg_beta<T, float><<<kBlocks, kThreads, 0, st>>>(r, b.z32, z, q, n, b.partials, S);
-      }
-      k_cg_dir<T><<<kBlocks, kThreads, 0, st>>>(z, pv, n, S);
-      FRLAP_LAUNCH_CHECK("CG iteration kernels");
+      cudaError_t e = iteration(st, launched + c);
+      if (e != cudaSuccess) return cuda_fail(e, "CG iteration");
     }
     launched += chunk;
     FRLAP_CUDA_TRY(cudaMemcpyAsync(hS, S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hS->done) break;
-    if (launched > maxit + chunk) break;  // cannot happen: the update kernel stops at maxit
+    if (hS->done) return FRLAP_OK;
+    if (launched > maxit + chunk) return FRLAP_OK;  // cannot happen: the update kernel stops at maxit
+    if (!snap) break;
   }
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t eb = iteration(cs, launched);
+    if (eb == cudaSuccess) {
+      k_cg_control<<<1, 1, 0, cs>>>(S, (unsigned)maxit + 2u, h);
+      eb = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (eb != cudaSuccess) e = eb;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hS, S, sizeof(CgState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "graph-launched CG iterations");
   return FRLAP_OK;
 }
 
@@ -437,10 +508,10 @@ static frlap_status true_residual(const Plan& p, const double* f, const double* 
   CgState* S = b.S;
   // the reduction ticket must start at zero (this workspace may not have run a CG yet)
   FRLAP_CUDA_TRY(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), st));
-  cudaError_t e = apply64(p, x, q, b.awork, st, nullptr);
+  cudaError_t e = apply_residual<double>(p, x, q, b.awork, st);
   if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
   double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
-  k_resid<<<kBlocks, kThreads, 0, st>>>(f, x, q, p.M, sigma, s, b.partials, &S->counter, out, rvec, rnorm_dev);
+  k_resid<<<vgrid(p.M), kThreads, 0, st>>>(f, x, q, p.M, sigma, s, b.partials, &S->counter, out, rvec, rnorm_dev);
   FRLAP_LAUNCH_CHECK("k_resid");
   double h[2];
   FRLAP_CUDA_TRY(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -467,7 +538,7 @@ frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, d
   const int np = hS.iters < K ? hS.iters : K;
   for (int j = 0; j < np; ++j) {
     double* Ej = E + (size_t)j * p.M;
-    k_err_from_snap<<<kBlocks, kThreads, 0, st>>>(Ej, x, p.M);
+    k_err_from_snap<<<vgrid(p.M), kThreads, 0, st>>>(Ej, x, p.M);
     FRLAP_LAUNCH_CHECK("k_err_from_snap");
     cudaError_t e = apply64(p, Ej, R + (size_t)j * p.M, b.awork, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "apply (training pairs)");
@@ -490,12 +561,15 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
   CgState hS;
   if (solver == FRLAP_SOLVE_CG) {
     // CG, then the true residual; if rounding left the true residual above rtol while the
-    // recursive one met it, restart from the current x (at most 4 restarts, within maxit)
+    // recursive one met it, restart from the current x (at most 4 restarts, within maxit).
+    // A restart aims at rtol / 10: it starts from the native FP64 residual, so its own
+    // recursive residual going well below rtol carries the true one below rtol too.
     int total = 0;
     double rel = 0.0;
     frlap_status rc = FRLAP_OK;
     for (int restart = 0; restart < 5; ++restart) {
-      rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, maxit - total, 1, mu, work, st, &hS);
+      const double rt = restart == 0 ? rtol : 0.1 * rtol;
+      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, 1, mu, work, st, &hS);
       if (rc != FRLAP_OK) return rc;
       total += hS.iters;
       rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
@@ -529,13 +603,13 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
     if (rc != FRLAP_OK) return rc;
     if (!isfinite(rel)) return fail(FRLAP_ENAN, "non-finite residual in iterative refinement");
     if (rel <= rtol || outer == max_outer || total >= maxit) break;
-    k_to_f32<<<kBlocks, kThreads, 0, st>>>(r64, rnorm, r32, d32, p.M);
+    k_to_f32<<<vgrid(p.M), kThreads, 0, st>>>(r64, rnorm, r32, d32, p.M);
     FRLAP_LAUNCH_CHECK("k_to_f32");
     rc = run_cg<float>(p, r32, d32, 0.0, 1.0, inner_rtol, maxit - total, 0, mu, work32, st, &hS);
     if (rc != FRLAP_OK) return rc;
     total += hS.iters;
     if (hS.status == FRLAP_ENAN) return fail(FRLAP_ENAN, "non-finite value in the FP32 inner solve");
-    k_correct<<<kBlocks, kThreads, 0, st>>>(x, d32, rnorm, p.M);
+    k_correct<<<vgrid(p.M), kThreads, 0, st>>>(x, d32, rnorm, p.M);
     FRLAP_LAUNCH_CHECK("k_correct");
   }
   if (iters) *iters = total;
@@ -553,7 +627,7 @@ frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, i
   int total = 0;
   CgState hS;
   for (int step = 0; step < nsteps; ++step) {
-    k_ac_rhs<<<kBlocks, kThreads, 0, st>>>(u, rhs, p.M, tau);
+    k_ac_rhs<<<vgrid(p.M), kThreads, 0, st>>>(u, rhs, p.M, tau);
     FRLAP_LAUNCH_CHECK("k_ac_rhs");
     frlap_status rc = run_cg<double>(p, rhs, u, 1.0, tau * eps * eps, rtol, 100000, 1, nullptr, cgw, st, &hS);
     if (rc != FRLAP_OK) return rc;

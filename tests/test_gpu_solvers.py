@@ -95,6 +95,9 @@ def test_solver_error_paths(frlap):
     f = _t(inp.gaussian_sum_field(Ns, h, seed=1))
     x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-12, maxit=2, raise_on_error=False)
     assert code == 5 and it == 2 and rel > 1e-12  # FRLAP_ENOCONV
+    # maxit reached inside the graph-launched part of the iteration (past the first 8)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-14, maxit=21, raise_on_error=False)
+    assert code == 5 and it == 21 and rel > 1e-14
     fbad = f.clone()
     fbad[3, 4] = float("nan")
     x, it, rel, code = frlap.frlap_pcg_solve(plan, fbad, rtol=1e-10, raise_on_error=False)
@@ -104,3 +107,22 @@ def test_solver_error_paths(frlap):
     # the context still works
     x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-10)
     assert code == 0 and rel <= 1e-10
+
+
+def test_double_float_cg_reaches_fp64_residual(frlap):
+    """Plain CG on a double-float plan at 1023^2, alpha = 1.9: the iterations run in double-float,
+    the residuals that restart and confirm the solve in native FP64, so the true FP64 residual
+    reaches 1e-10 and the solution matches the native-FP64 solve."""
+    N, alpha = 1024, 1.9
+    h = 2.0 / N
+    f = _t(inp.gaussian_sum_field((N, N), h, seed=2))
+    pdf = frlap.Plan(2, alpha, h, (N, N), prec=frlap.FRLAP_DF64)
+    x, it, rel, code = frlap.frlap_pcg_solve(pdf, f, rtol=1e-10, raise_on_error=False)
+    print("double-float CG 1023^2 alpha 1.9:", it, rel, code)
+    assert code == 0 and rel <= 1e-10
+    p64 = frlap.Plan(2, alpha, h, (N, N), prec=frlap.FRLAP_F64)
+    x64, it64, rel64, code64 = frlap.frlap_pcg_solve(p64, f, rtol=1e-10)
+    assert code64 == 0
+    d = torch.linalg.norm(x - x64).item() / torch.linalg.norm(x64).item()
+    print("native FP64 CG:", it64, rel64, "solution difference", d)
+    assert d <= 1e-8
