@@ -61,11 +61,11 @@ typedef enum {
  * of FP32 numbers, about 48 significant bits), which GB300 runs several times
  * faster than FP64 at an accuracy within the FP64 tolerance of the apply.
  * MIXED_DF64: MIXED with the FP64 side computed as in DF64.
- * In frlap_pcg_solve and the Allen-Cahn calls the iterations use the plan's
- * engine, but every residual f - B x that starts, restarts or confirms a solve
- * is computed with the native FP64 engine (double-float rounding, about
- * 5e-15 lambda_max ||x||, would otherwise set a residual floor near 1e-10 ||f||
- * at 2047^2). */
+ * In frlap_pcg_solve the iterations use the plan's engine, but the residuals
+ * f - A x that restart a CG solve or decide convergence (the final check, and
+ * the refinement residuals from 1e-6 relative on) are computed with the native
+ * FP64 engine: double-float rounding, about 5e-15 lambda_max ||x||, would
+ * otherwise set a residual floor near 1e-10 ||f|| at 2047^2. */
 typedef enum { FRLAP_F64 = 0, FRLAP_F32 = 1, FRLAP_MIXED = 2, FRLAP_DF64 = 3, FRLAP_MIXED_DF64 = 4 } frlap_prec;
 
 /* Which scratch size frlap_workspace_bytes reports. */
@@ -149,6 +149,19 @@ int frlap_apply_nstages(const frlap_plan* plan);
 size_t frlap_apply_batch_workspace_bytes(const frlap_plan* plan, int nbatch);
 frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d_u, void* d_y, void* d_work,
                                void* stream, void* const* events);
+
+/* frlap_apply_batch from and to HOST buffers: y_b = A u_b for b = 0..nbatch-1, with
+ * h_u, h_y in host memory (nbatch vectors back to back, element type as in
+ * frlap_apply).  The batch moves in chunks of `chunk` vectors through two device
+ * slots: the copy in of chunk i+1 and the copy out of chunk i-1 run on internal
+ * streams while chunk i is applied on `stream`.  For the copies to overlap,
+ * h_u and h_y must be pinned (page-locked); pageable buffers give the same
+ * result with serialised copies.  d_work: frlap_apply_host_workspace_bytes(plan,
+ * chunk) bytes, 256-byte aligned.  Synchronises `stream`: h_y is complete on
+ * return.  1 <= chunk <= 65535, nbatch >= 1, else FRLAP_EINVAL. */
+size_t frlap_apply_host_workspace_bytes(const frlap_plan* plan, int chunk);
+frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, const void* h_u, void* h_y,
+                              void* d_work, void* stream);
 
 /* frlap_apply with timing marks: events[i] (a cudaEvent_t, or NULL to skip) is
  * recorded on `stream` just before stage i, events[nstages] after the last

@@ -44,6 +44,8 @@ _SIGS = {
     "frlap_apply_profiled": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "frlap_apply_batch_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
     "frlap_apply_batch": (_I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "frlap_apply_host_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
+    "frlap_apply_host": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
     "frlap_precond_strang": (_I, [_P, ctypes.POINTER(_I), _P]),
     "frlap_precond_set_symbol": (_I, [_P, _P, _P]),
@@ -278,6 +280,36 @@ def frlap_apply_batch(plan: Plan, U: torch.Tensor, Y: torch.Tensor = None, work:
                                              for e in events])
     _check(lib().frlap_apply_batch(plan.handle, nb, _dev(U, dt, "U"), _dev(Y, dt, "Y"),
                                    ctypes.c_void_p(work.data_ptr()), _stream(stream), arr), "frlap_apply_batch")
+    return Y
+
+
+def frlap_apply_host_workspace_bytes(plan: Plan, chunk: int) -> int:
+    return int(lib().frlap_apply_host_workspace_bytes(plan.handle, int(chunk)))
+
+
+def frlap_apply_host(plan: Plan, U: torch.Tensor, Y: torch.Tensor = None, chunk: int = 4, work: torch.Tensor = None,
+                     stream=None):
+    """Y[b] = A U[b] with U, Y in HOST memory (CPU tensors; pinned for copy/compute overlap).  The
+    library moves the batch through the GPU in chunks of `chunk` vectors, overlapping the copies
+    with the applies, and returns when Y is complete."""
+    dt = _apply_dtype(plan)
+    if U.is_cuda or U.dtype != dt or not U.is_contiguous():
+        raise TypeError(f"U must be a contiguous CPU tensor of dtype {dt}")
+    if U.numel() % plan.M != 0 or U.numel() == 0:
+        raise ValueError(f"U has {U.numel()} entries, not a positive multiple of the plan's {plan.M} unknowns")
+    nb = U.numel() // plan.M
+    if Y is None:
+        Y = torch.empty_like(U, pin_memory=U.is_pinned())
+    if Y.is_cuda or Y.dtype != dt or not Y.is_contiguous() or Y.numel() != U.numel():
+        raise TypeError("Y must be a contiguous CPU tensor like U")
+    if work is None:
+        nbytes = frlap_apply_host_workspace_bytes(plan, chunk)
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        off = (-raw.data_ptr()) % 256
+        work = raw[off:off + nbytes]
+    _check(lib().frlap_apply_host(plan.handle, nb, int(chunk), ctypes.c_void_p(U.data_ptr()),
+                                  ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(work.data_ptr()), _stream(stream)),
+           "frlap_apply_host")
     return Y
 
 

@@ -316,6 +316,103 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
   return FRLAP_OK;
 }
 
+// Host-buffer batch: two device slots, each holding `chunk` input and output vectors, and
+// the batched apply workspace of one chunk.
+static size_t host_slot_bytes(const frlap_plan* plan, int chunk) {
+  const size_t vb = (size_t)chunk * plan->M * (plan->prec == FRLAP_F32 ? 4 : 8);
+  return 2 * align256(vb);
+}
+
+size_t frlap_apply_host_workspace_bytes(const frlap_plan* plan, int chunk) {
+  if (!plan || chunk < 1) return 0;
+  return 2 * host_slot_bytes(plan, chunk) + frlap_apply_batch_workspace_bytes(plan, chunk);
+}
+
+frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, const void* h_u, void* h_y,
+                              void* d_work, void* stream) {
+  if (!plan || !h_u || !h_y) return fail(FRLAP_EINVAL, "plan, h_u or h_y is NULL");
+  if (nbatch < 1 || chunk < 1 || chunk > 65535) return fail(FRLAP_EINVAL, "need nbatch >= 1 and chunk in 1..65535");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  const size_t eb = plan->prec == FRLAP_F32 ? 4 : 8;
+  const size_t vbytes = plan->M * eb;
+  unsigned char* w = reinterpret_cast<unsigned char*>(d_work);
+  unsigned char* du[2];
+  unsigned char* dy[2];
+  for (int k = 0; k < 2; ++k) {
+    du[k] = w + k * host_slot_bytes(plan, chunk);
+    dy[k] = du[k] + align256((size_t)chunk * vbytes);
+  }
+  void* awork = w + 2 * host_slot_bytes(plan, chunk);
+  const cudaStream_t cs = (cudaStream_t)stream;
+  const int nchunks = (nbatch + chunk - 1) / chunk;
+  cudaStream_t sin = nullptr, sout = nullptr;
+  // in[k]: slot k's input has arrived; done[k]: slot k's apply finished; out[k]: slot k's output copied
+  cudaEvent_t in[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, out[2] = {nullptr, nullptr};
+  cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out[k], cudaEventDisableTiming);
+  }
+  // the copy streams start after the caller's earlier work on `stream`
+  if (e == cudaSuccess) e = cudaEventRecord(done[0], cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, done[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[0], 0);
+  auto copy_in = [&](int c) -> cudaError_t {
+    const int k = c & 1;
+    const int nb = (c + 1) * chunk <= nbatch ? chunk : nbatch - c * chunk;
+    cudaError_t r = cudaSuccess;
+    if (c >= 2) r = cudaStreamWaitEvent(sin, done[k], 0);  // slot k's previous apply has read its input
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(du[k], static_cast<const unsigned char*>(h_u) + (size_t)c * chunk * vbytes,
+                          (size_t)nb * vbytes, cudaMemcpyHostToDevice, sin);
+    if (r == cudaSuccess) r = cudaEventRecord(in[k], sin);
+    return r;
+  };
+  if (e == cudaSuccess) e = copy_in(0);
+  for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+    const int k = c & 1;
+    const int nb = (c + 1) * chunk <= nbatch ? chunk : nbatch - c * chunk;
+    if (c + 1 < nchunks) e = copy_in(c + 1);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, in[k], 0);
+    if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(cs, out[k], 0);  // slot k's output copied out
+    if (e == cudaSuccess) {
+      if (plan->prec == FRLAP_F32)
+        e = apply_batch_launch<float>(*plan, nb, (const float*)du[k], (float*)dy[k], plan->M, awork, cs, nullptr, 0,
+                                      nullptr, 0);
+      else if (plan->df64)
+        e = apply_batch_launch<dfl>(*plan, nb, (const double*)du[k], (double*)dy[k], plan->M, awork, cs, nullptr,
+                                    0, nullptr, 0);
+      else
+        e = apply_batch_launch<double>(*plan, nb, (const double*)du[k], (double*)dy[k], plan->M, awork, cs, nullptr,
+                                       0, nullptr, 0);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(done[k], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<unsigned char*>(h_y) + (size_t)c * chunk * vbytes, dy[k], (size_t)nb * vbytes,
+                          cudaMemcpyDeviceToHost, sout);
+    if (e == cudaSuccess) e = cudaEventRecord(out[k], sout);
+  }
+  // `stream` ends after the last copy out; then wait for everything
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(cs, out[k], 0);
+  cudaError_t es = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess) e = es;
+  if (sin) cudaStreamSynchronize(sin);
+  if (sout) cudaStreamSynchronize(sout);
+  for (int k = 0; k < 2; ++k) {
+    if (in[k]) cudaEventDestroy(in[k]);
+    if (done[k]) cudaEventDestroy(done[k]);
+    if (out[k]) cudaEventDestroy(out[k]);
+  }
+  if (sin) cudaStreamDestroy(sin);
+  if (sout) cudaStreamDestroy(sout);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_host");
+  return FRLAP_OK;
+}
+
 frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream,
                                   void* const* events) {
   if (!plan || !d_u || !d_y || !events) return fail(FRLAP_EINVAL, "plan, d_u, d_y or events is NULL");

@@ -317,7 +317,7 @@ static cudaError_t apply_T(const Plan& p, const T* u, T* y, void* work, cudaStre
   else return apply_launch<float>(p, u, y, work, s, skip);
 }
 
-// The residuals f - B x that start, restart and confirm a solve: FP64 vectors always go
+// The residuals f - B x that restart a solve or decide its convergence: FP64 vectors go
 // through the native FP64 engine, also on double-float plans.  The iterations may run on
 // double-float (48-bit products, 3x faster), but a residual computed with it carries that
 // rounding (about 5e-15 lambda_max ||x||), which at 2047^2 already sits near 1e-10 ||f||;
@@ -410,7 +410,8 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   k_set_state<<<1, 1, 0, st>>>(S, sigma, s);
   FRLAP_LAUNCH_CHECK("k_set_state");
   if (use_x0) {
-    cudaError_t e = apply_residual<T>(p, x, q, b.awork, st);
+    // use_x0 = 1: the plan's engine; 2: native FP64 (a restart, which must see the true residual)
+    cudaError_t e = use_x0 == 2 ? apply_residual<T>(p, x, q, b.awork, st) : apply_T<T>(p, x, q, b.awork, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "apply (initial residual)");
   }
   k_cg_init<T><<<vgrid(n), kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
@@ -502,13 +503,13 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
 // true relative residual ||f - B x|| / ||f|| in FP64 (uses the apply work and q buffer)
 static frlap_status true_residual(const Plan& p, const double* f, const double* x, double sigma, double s,
                                   void* work, cudaStream_t st, double* relres, double* rvec,
-                                  double* rnorm_dev) {
+                                  double* rnorm_dev, bool native = true) {
   const CgBufs b = carve(p, work, 8);
   double* q = reinterpret_cast<double*>(b.q);
   CgState* S = b.S;
   // the reduction ticket must start at zero (this workspace may not have run a CG yet)
   FRLAP_CUDA_TRY(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), st));
-  cudaError_t e = apply_residual<double>(p, x, q, b.awork, st);
+  cudaError_t e = native ? apply_residual<double>(p, x, q, b.awork, st) : apply64(p, x, q, b.awork, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
   double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
   k_resid<<<vgrid(p.M), kThreads, 0, st>>>(f, x, q, p.M, sigma, s, b.partials, &S->counter, out, rvec, rnorm_dev);
@@ -569,7 +570,7 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
     frlap_status rc = FRLAP_OK;
     for (int restart = 0; restart < 5; ++restart) {
       const double rt = restart == 0 ? rtol : 0.1 * rtol;
-      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, 1, mu, work, st, &hS);
+      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, restart == 0 ? 1 : 2, mu, work, st, &hS);
       if (rc != FRLAP_OK) return rc;
       total += hS.iters;
       rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
@@ -598,9 +599,16 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
   int total = 0;
   double rel = 0.0;
   const int max_outer = 60;
+  // Outer residuals use the plan's FP64-side engine while far from rtol; from 1e-6 on (and to
+  // decide convergence) the native FP64 engine computes them.
+  double prev = 1.0;
   for (int outer = 0; outer <= max_outer; ++outer) {
-    frlap_status rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm);
+    const bool native = prev <= 1e-6;
+    frlap_status rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm, native);
+    if (rc == FRLAP_OK && !native && rel <= 1e-6)
+      rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm, true);
     if (rc != FRLAP_OK) return rc;
+    prev = rel;
     if (!isfinite(rel)) return fail(FRLAP_ENAN, "non-finite residual in iterative refinement");
     if (rel <= rtol || outer == max_outer || total >= maxit) break;
     k_to_f32<<<vgrid(p.M), kThreads, 0, st>>>(r64, rnorm, r32, d32, p.M);

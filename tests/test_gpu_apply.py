@@ -238,3 +238,21 @@ def test_double_float_accuracy_level(frlap, d, N, alpha):
         rel = (torch.linalg.norm(ydf - y64) / torch.linalg.norm(y64)).item()
         print(f"double-float vs FP64: d={d} N={N} alpha={alpha}: normwise {err:.2e}, relative {rel:.2e}")
         assert err <= 2e-14, err
+
+
+@pytest.mark.parametrize("d,Ns,prec", [(2, (64, 40), 1), (2, (64, 40), 3), (3, (12, 20, 9), 0)])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_apply_host_matches_batch(frlap, d, Ns, prec, pinned):
+    """frlap_apply_host (host buffers, chunked copies overlapped with the applies): bit for bit the
+    device batch apply, for a batch that is not a multiple of the chunk, pinned or pageable."""
+    h = 2.0 / max(Ns)
+    plan = frlap.Plan(d, 1.3, h, Ns, prec=prec)
+    dt = torch.float32 if prec == 1 else torch.float64
+    U = torch.from_numpy(np.stack([inp.normal_field(Ns, seed=40 + b) for b in range(5)])).to(dt)
+    if pinned:
+        U = U.pin_memory()
+    Y = frlap.frlap_apply_host(plan, U, chunk=2)
+    Yd = frlap.frlap_apply_batch(plan, U.cuda())
+    assert torch.equal(Y, Yd.cpu())
+    Y1 = frlap.frlap_apply_host(plan, U, chunk=8)  # one chunk holding the whole batch
+    assert torch.equal(Y1, Y)
