@@ -39,7 +39,7 @@ import frlap_inputs as inp  # noqa: E402
 ALPHA = 1.5
 NGRID = 2048
 BATCH = 8
-E2E_CHUNK = 1  # vectors per chunk of the host-buffer pipeline (1, 2, 4, 8 measured 6.5, 6.4, 5.8, 4.7 G unknowns/s)
+E2E_CHUNK = 1  # vectors per chunk of the host-buffer pipeline (1, 2, 4, 8 measured 6.9, 6.6, 5.8, 4.7 G unknowns/s)
 METRIC = "apply unknowns/s & %HBM peak; PCG time to 1e-10 of FP64 sol vs plain FP64 CG"
 UNIT = "unknowns/s"
 

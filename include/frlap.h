@@ -154,7 +154,8 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
  * h_u, h_y in host memory (nbatch vectors back to back, element type as in
  * frlap_apply).  The batch moves in chunks of `chunk` vectors through two device
  * slots: the copy in of chunk i+1 and the copy out of chunk i-1 run on internal
- * streams while chunk i is applied on `stream`.  For the copies to overlap,
+ * streams while chunk i is applied (the two slots compute on `stream` and on an
+ * internal stream, so consecutive chunks' kernels may overlap).  For the copies to overlap,
  * h_u and h_y must be pinned (page-locked); pageable buffers give the same
  * result with serialised copies.  d_work: frlap_apply_host_workspace_bytes(plan,
  * chunk) bytes, 256-byte aligned.  Synchronises `stream`: h_y is complete on

@@ -316,16 +316,16 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
   return FRLAP_OK;
 }
 
-// Host-buffer batch: two device slots, each holding `chunk` input and output vectors, and
-// the batched apply workspace of one chunk.
+// Host-buffer batch: two device slots, each holding `chunk` input and output vectors and the
+// batched apply workspace of one chunk (the slots compute on two streams).
 static size_t host_slot_bytes(const frlap_plan* plan, int chunk) {
   const size_t vb = (size_t)chunk * plan->M * (plan->prec == FRLAP_F32 ? 4 : 8);
-  return 2 * align256(vb);
+  return 2 * align256(vb) + align256(frlap_apply_batch_workspace_bytes(plan, chunk));
 }
 
 size_t frlap_apply_host_workspace_bytes(const frlap_plan* plan, int chunk) {
   if (!plan || chunk < 1) return 0;
-  return 2 * host_slot_bytes(plan, chunk) + frlap_apply_batch_workspace_bytes(plan, chunk);
+  return 2 * host_slot_bytes(plan, chunk);
 }
 
 frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, const void* h_u, void* h_y,
@@ -339,27 +339,33 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   unsigned char* w = reinterpret_cast<unsigned char*>(d_work);
   unsigned char* du[2];
   unsigned char* dy[2];
+  void* awork[2];
   for (int k = 0; k < 2; ++k) {
     du[k] = w + k * host_slot_bytes(plan, chunk);
     dy[k] = du[k] + align256((size_t)chunk * vbytes);
+    awork[k] = dy[k] + align256((size_t)chunk * vbytes);
   }
-  void* awork = w + 2 * host_slot_bytes(plan, chunk);
   const cudaStream_t cs = (cudaStream_t)stream;
   const int nchunks = (nbatch + chunk - 1) / chunk;
-  cudaStream_t sin = nullptr, sout = nullptr;
+  // slot k computes on comp[k] (comp[0] = the caller's stream): the kernels of consecutive
+  // chunks overlap, filling each other's last partial wave
+  cudaStream_t sin = nullptr, sout = nullptr, c1 = nullptr;
   // in[k]: slot k's input has arrived; done[k]: slot k's apply finished; out[k]: slot k's output copied
   cudaEvent_t in[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, out[2] = {nullptr, nullptr};
   cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c1, cudaStreamNonBlocking);
+  const cudaStream_t comp[2] = {cs, c1};
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&in[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out[k], cudaEventDisableTiming);
   }
-  // the copy streams start after the caller's earlier work on `stream`
+  // the internal streams start after the caller's earlier work on `stream`
   if (e == cudaSuccess) e = cudaEventRecord(done[0], cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, done[0], 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c1, done[0], 0);
   auto copy_in = [&](int c) -> cudaError_t {
     const int k = c & 1;
     const int nb = (c + 1) * chunk <= nbatch ? chunk : nbatch - c * chunk;
@@ -376,20 +382,21 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
     const int k = c & 1;
     const int nb = (c + 1) * chunk <= nbatch ? chunk : nbatch - c * chunk;
     if (c + 1 < nchunks) e = copy_in(c + 1);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, in[k], 0);
-    if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(cs, out[k], 0);  // slot k's output copied out
+    const cudaStream_t ks = comp[k];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, in[k], 0);
+    if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(ks, out[k], 0);  // slot k's output copied out
     if (e == cudaSuccess) {
       if (plan->prec == FRLAP_F32)
-        e = apply_batch_launch<float>(*plan, nb, (const float*)du[k], (float*)dy[k], plan->M, awork, cs, nullptr, 0,
-                                      nullptr, 0);
+        e = apply_batch_launch<float>(*plan, nb, (const float*)du[k], (float*)dy[k], plan->M, awork[k], ks, nullptr,
+                                      0, nullptr, 0);
       else if (plan->df64)
-        e = apply_batch_launch<dfl>(*plan, nb, (const double*)du[k], (double*)dy[k], plan->M, awork, cs, nullptr,
+        e = apply_batch_launch<dfl>(*plan, nb, (const double*)du[k], (double*)dy[k], plan->M, awork[k], ks, nullptr,
                                     0, nullptr, 0);
       else
-        e = apply_batch_launch<double>(*plan, nb, (const double*)du[k], (double*)dy[k], plan->M, awork, cs, nullptr,
-                                       0, nullptr, 0);
+        e = apply_batch_launch<double>(*plan, nb, (const double*)du[k], (double*)dy[k], plan->M, awork[k], ks,
+                                       nullptr, 0, nullptr, 0);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(done[k], cs);
+    if (e == cudaSuccess) e = cudaEventRecord(done[k], ks);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[k], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(static_cast<unsigned char*>(h_y) + (size_t)c * chunk * vbytes, dy[k], (size_t)nb * vbytes,
@@ -402,6 +409,7 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   if (e == cudaSuccess) e = es;
   if (sin) cudaStreamSynchronize(sin);
   if (sout) cudaStreamSynchronize(sout);
+  if (c1) cudaStreamSynchronize(c1);
   for (int k = 0; k < 2; ++k) {
     if (in[k]) cudaEventDestroy(in[k]);
     if (done[k]) cudaEventDestroy(done[k]);
@@ -409,6 +417,7 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   }
   if (sin) cudaStreamDestroy(sin);
   if (sout) cudaStreamDestroy(sout);
+  if (c1) cudaStreamDestroy(c1);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_apply_host");
   return FRLAP_OK;
 }
