@@ -300,6 +300,7 @@ def main():
     h = 2.0 / NGRID
     Ns = (NGRID, NGRID)
     plan = fl.Plan(2, ALPHA, h, Ns, prec=prec)
+    tuned = fl.frlap_plan_autotune(plan, BATCH)  # launch shapes, before the timed region
     U = torch.stack([torch.from_numpy(inp.normal_field(Ns, seed=100 + b)) for b in range(BATCH)]).to("cuda", dt)
     Y = torch.empty_like(U)
     work = batch_workspace(fl, torch, plan, BATCH)
@@ -391,6 +392,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"2D {NGRID - 1}x{NGRID - 1} alpha={ALPHA} {args.prec.upper()} FFT Toeplitz apply",
                        "batch_per_step": BATCH, "launch": "frlap_apply_batch (one launch per stage for the batch)",
+                       "lines_per_cta": {"fp64_side": tuned[0][:3], "fp32": tuned[1][:3],
+                                         "chosen_by": "frlap_plan_autotune"},
                        "embedding": list(plan.P),
                        "l2": "inputs larger than L2 (8 distinct 2047^2 vectors per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -422,6 +425,7 @@ def run_extras(fl, torch, args):
         dt = torch.float32 if prec == fl.FRLAP_F32 else torch.float64
         eb = 4 if prec == fl.FRLAP_F32 else 8
         plan = fl.Plan(d, ALPHA if d == 2 else 1.0, 2.0 / N, (N,) * d, prec=prec)
+        fl.frlap_plan_autotune(plan, batch)
         U = torch.randn((batch,) + plan.shape, dtype=dt, device="cuda")
         Y = torch.empty_like(U)
         work = batch_workspace(fl, torch, plan, batch)

@@ -160,6 +160,19 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
  * result with serialised copies.  d_work: frlap_apply_host_workspace_bytes(plan,
  * chunk) bytes, 256-byte aligned.  Synchronises `stream`: h_y is complete on
  * return.  1 <= chunk <= 65535, nbatch >= 1, else FRLAP_EINVAL. */
+/* Autotuner of the apply's launch shapes.  For each stage of the apply, and for each
+ * engine the plan uses (FP32, and FP64 or double-float), times every admissible
+ * number of FFT lines per CTA (powers of two up to 512 threads and 227 KB of shared
+ * memory) on a batch of nbatch zero vectors, and keeps the fastest in the plan;
+ * later applies, batched applies, solves and Allen-Cahn runs on the plan use it.
+ * The stages are timed independently (one launch each), so the search is exact
+ * per stage.  d_work: frlap_autotune_workspace_bytes(plan, nbatch) bytes, 256-byte
+ * aligned; chosen (may be NULL): 10 ints, the FP64-side choices of stages 0..4, then
+ * the FP32 ones (0 where a stage or engine does not exist).  Synchronises stream;
+ * not to be called while another thread uses the plan.  1 <= nbatch <= 65535. */
+size_t frlap_autotune_workspace_bytes(const frlap_plan* plan, int nbatch);
+frlap_status frlap_plan_autotune(frlap_plan* plan, int nbatch, void* d_work, void* stream, int* chosen);
+
 size_t frlap_apply_host_workspace_bytes(const frlap_plan* plan, int chunk);
 frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, const void* h_u, void* h_y,
                               void* d_work, void* stream);

@@ -45,6 +45,8 @@ _SIGS = {
     "frlap_apply_batch_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
     "frlap_apply_batch": (_I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "frlap_apply_host_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
+    "frlap_autotune_workspace_bytes": (ctypes.c_size_t, [_P, _I]),
+    "frlap_plan_autotune": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I)]),
     "frlap_apply_host": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
     "frlap_precond_strang": (_I, [_P, ctypes.POINTER(_I), _P]),
@@ -311,6 +313,19 @@ def frlap_apply_host(plan: Plan, U: torch.Tensor, Y: torch.Tensor = None, chunk:
                                   ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(work.data_ptr()), _stream(stream)),
            "frlap_apply_host")
     return Y
+
+
+def frlap_plan_autotune(plan: Plan, nbatch: int = 8, stream=None):
+    """Time every admissible lines-per-CTA choice of each apply stage (per engine of the plan) on
+    nbatch zero vectors and keep the fastest in the plan.  Returns (FP64-side choices, FP32 choices),
+    5 ints each (0 = stage or engine absent)."""
+    nbytes = int(lib().frlap_autotune_workspace_bytes(plan.handle, int(nbatch)))
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    off = (-raw.data_ptr()) % 256
+    out = (ctypes.c_int * 10)()
+    _check(lib().frlap_plan_autotune(plan.handle, int(nbatch), ctypes.c_void_p(raw.data_ptr() + off),
+                                     _stream(stream), out), "frlap_plan_autotune")
+    return list(out[:5]), list(out[5:])
 
 
 def frlap_apply_f32(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch.Tensor = None, stream=None):

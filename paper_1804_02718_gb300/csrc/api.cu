@@ -316,6 +316,41 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
   return FRLAP_OK;
 }
 
+size_t frlap_autotune_workspace_bytes(const frlap_plan* plan, int nbatch) {
+  if (!plan || nbatch < 1) return 0;
+  return 2 * align256((size_t)nbatch * plan->M * 8) + (size_t)nbatch * apply_work_bytes(*plan, 8);
+}
+
+frlap_status frlap_plan_autotune(frlap_plan* plan, int nbatch, void* d_work, void* stream, int* chosen) {
+  if (!plan) return fail(FRLAP_EINVAL, "plan is NULL");
+  if (nbatch < 1 || nbatch > 65535) return fail(FRLAP_EINVAL, "nbatch must be in 1..65535");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  unsigned char* w = reinterpret_cast<unsigned char*>(d_work);
+  void* u = w;
+  void* y = w + align256((size_t)nbatch * plan->M * 8);
+  void* work = w + 2 * align256((size_t)nbatch * plan->M * 8);
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  const int p = plan->prec;
+  if (p == FRLAP_F64 || p == FRLAP_MIXED)
+    e = autotune_engine<double>(*plan, nbatch, (double*)u, (double*)y, work, s);
+  else if (p == FRLAP_DF64 || p == FRLAP_MIXED_DF64)
+    e = autotune_engine<dfl>(*plan, nbatch, (double*)u, (double*)y, work, s);
+  if (e == cudaSuccess && p != FRLAP_F64 && p != FRLAP_DF64)
+    e = autotune_engine<float>(*plan, nbatch, (float*)u, (float*)y, work, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_plan_autotune");
+  if (chosen) {
+    const int e64 = plan->df64 ? 2 : 1;
+    for (int st = 0; st < 5; ++st) {
+      chosen[st] = plan->tl_tuned[e64][st];
+      chosen[5 + st] = plan->tl_tuned[0][st];
+    }
+  }
+  return FRLAP_OK;
+}
+
 // Host-buffer batch: two device slots, each holding `chunk` input and output vectors and the
 // batched apply workspace of one chunk (the slots compute on two streams).
 static size_t host_slot_bytes(const frlap_plan* plan, int chunk) {

@@ -8,4 +8,6 @@ template cudaError_t apply_batch_launch<dfl>(const Plan&, int, const double*, do
 template cudaError_t apply_launch<dfl>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
                                        cudaEvent_t const*, const dfl*);
 
+template cudaError_t autotune_engine<dfl>(Plan&, int, double*, double*, void*, cudaStream_t);
+
 }  // namespace frlap

@@ -8,4 +8,6 @@ template cudaError_t apply_batch_launch<float>(const Plan&, int, const float*, f
 template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void*, cudaStream_t, const int*,
                                          cudaEvent_t const*, const float*);
 
+template cudaError_t autotune_engine<float>(Plan&, int, float*, float*, void*, cudaStream_t);
+
 }  // namespace frlap

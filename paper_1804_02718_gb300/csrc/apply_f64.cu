@@ -36,4 +36,6 @@ template cudaError_t spectrum_forward<double>(const Plan&, const double*, double
 template cudaError_t spectrum_inverse<double>(const Plan&, const double2*, const double*, double*, void*,
                                               cudaStream_t);
 
+template cudaError_t autotune_engine<double>(Plan&, int, double*, double*, void*, cudaStream_t);
+
 }  // namespace frlap

@@ -456,6 +456,22 @@ int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines, long long
   return tl;
 }
 
+// A tuned choice (> 0) replaces the shared-memory / thread budget; whole warps and the
+// spreading of small launches still apply.
+int pick_tl_tuned(int tuned, int len, int elem_bytes, int G, int budget, long long lines) {
+  if (tuned <= 0) return pick_tl(len, elem_bytes, G, budget, 64, lines);
+  int tl = tuned;
+  const int q = G < 32 ? 32 / G : 1;
+  if (tl < q) tl = q;
+  while (tl > q && (lines + tl - 1) / tl < 2 * 152) tl /= 2;
+  return tl;
+}
+
+template <typename T>
+constexpr int engine_index() {
+  return std::is_same<T, float>::value ? 0 : (std::is_same<T, double>::value ? 1 : 2);
+}
+
 template <typename Kern>
 cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -512,6 +528,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   using C = cplx<T>;
   const int eb = sizeof(C);
   const int budget = 96 * 1024;
+  const int* tuned = p.tl_tuned[engine_index<T>()];
   const C* tw[3];
   for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
   const T* lam = lam_override ? lam_override : symbol_table<T>(p);
@@ -542,7 +559,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   // ---- stage 1: rows of u -> S1[kx][row]
   {
     const int G = Hx >> 4;
-    const int tl = pick_tl(sline(Hx), eb, G, budget, 64, (long long)nrows * B);
+    const int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
@@ -565,7 +582,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   map.Hz1 = p.d == 3 ? p.P[2] / 2 + 1 : 1;
   if (p.d == 2) {
     const int G = p.P[1] >> 4;
-    const int tl = pick_tl(sline(p.P[1]), eb, G, budget, 64, (long long)(Hx + 1) * B);
+    const int tl = pick_tl_tuned(tuned[1], sline(p.P[1]), eb, G, budget, (long long)(Hx + 1) * B);
     const size_t sm = (size_t)tl * sline(p.P[1]) * eb;
     cudaError_t e;
     const int ncols = Hx + 1;
@@ -584,7 +601,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     // ---- stage 2: S1[kx][z][y] -> FFT_y -> S2[kx][ky][z]
     {
       const int G = Py >> 4;
-      const int tl = pick_tl(sline(Py), eb, G, budget, 64, (long long)nz * (Hx + 1) * B);
+      const int tl = pick_tl_tuned(tuned[1], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
       const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
@@ -602,7 +619,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     // ---- stage 3: S2[kx][ky][:] -> FFT_z, * lambda, IFFT_z
     {
       const int G = Pz >> 4;
-      const int tl = pick_tl(sline(Pz), eb, G, budget, 64, (long long)(Hx + 1) * Py * B);
+      const int tl = pick_tl_tuned(tuned[2], sline(Pz), eb, G, budget, (long long)(Hx + 1) * Py * B);
       const size_t sm = (size_t)tl * sline(Pz) * eb;
       cudaError_t e;
       const int ncols = (Hx + 1) * Py;
@@ -620,7 +637,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
     {
       const int G = Py >> 4;
-      const int tl = pick_tl(sline(Py), eb, G, budget, 64, (long long)nz * (Hx + 1) * B);
+      const int tl = pick_tl_tuned(tuned[3], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
       const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
@@ -639,7 +656,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   // ---- last stage: S1[kx][row] -> rows of y
   {
     const int G = Hx >> 4;
-    const int tl = pick_tl(sline(Hx), eb, G, budget, 64, (long long)nrows * B);
+    const int tl = pick_tl_tuned(tuned[p.d == 2 ? 2 : 4], sline(Hx), eb, G, budget, (long long)nrows * B);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
@@ -795,6 +812,59 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+
+// Lines per CTA candidates of apply stage `st`: powers of two from whole warps up to the
+// compiled 512-thread bound, 64 lines, and 227 KB of shared memory.
+template <typename T>
+static int stage_line_length(const Plan& p, int st) {
+  const int Hx = p.P[0] / 2;
+  if (p.d == 2) return st == 1 ? p.P[1] : Hx;
+  if (st == 0 || st == 4) return Hx;
+  return st == 2 ? p.P[2] : p.P[1];
+}
+
+template <typename T>
+cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s) {
+  const int ns = p.d == 2 ? 3 : 5;
+  const int eng = engine_index<T>();
+  const int eb = (int)sizeof(cplx<T>);
+  cudaEvent_t ev[6];
+  for (int i = 0; i <= ns; ++i) {
+    cudaError_t e = cudaEventCreate(&ev[i]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+      return e;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(u, 0, (size_t)B * p.M * sizeof(io_t<T>), s);
+  for (int st = 0; st < ns && e == cudaSuccess; ++st) {
+    const int L = stage_line_length<T>(p, st);
+    const int G = L >> 4;
+    int best = 0;
+    float best_ms = 0.f;
+    for (int t = 1; t <= 64 && e == cudaSuccess; t *= 2) {
+      if (t * G > 512 || (size_t)t * sline(L) * eb > 227 * 1024) break;
+      if (G < 32 && t < 32 / G) continue;
+      p.tl_tuned[eng][st] = t;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // one warm-up, two timed
+        e = apply_launch_b<T>(p, B, u, y, p.M, work, s, nullptr, 0, ev, nullptr, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[ns]);
+        float t_ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, ev[st], ev[st + 1]);
+        if (rep > 0) ms += t_ms;
+      }
+      if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+        best = t;
+        best_ms = ms;
+      }
+    }
+    p.tl_tuned[eng][st] = best;
+  }
+  for (int i = 0; i <= ns; ++i) cudaEventDestroy(ev[i]);
+  return e;
 }
 
 }  // namespace frlap

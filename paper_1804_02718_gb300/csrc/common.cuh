@@ -152,6 +152,9 @@ struct Plan {
   // preconditioner multipliers (line-major like lam32, FP32; nullptr until built)
   float* mu_strang = nullptr;   // inverse of the multilevel Strang circulant, embedded like A
   float* mu_learned = nullptr;  // learned Fourier multiplier
+  // lines per CTA of each apply stage, per engine (0 FP32, 1 FP64, 2 double-float), set by
+  // frlap_plan_autotune; 0 = the built-in choice
+  int tl_tuned[3][5] = {};
 };
 
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
@@ -163,6 +166,10 @@ cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work
 cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
                     cudaEvent_t const* ev = nullptr);
 size_t apply_work_bytes(const Plan& p, int real_bytes);
+// times every admissible lines-per-CTA choice of each apply stage on a batch of B zero vectors
+// (u, y: B vectors each; work: B apply workspaces) and stores the fastest in p.tl_tuned
+template <typename T>
+cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s);
 // B same-shape instances in one launch per stage (see apply.cu)
 template <typename T>
 cudaError_t apply_batch_launch(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,

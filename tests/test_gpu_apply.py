@@ -256,3 +256,23 @@ def test_apply_host_matches_batch(frlap, d, Ns, prec, pinned):
     assert torch.equal(Y, Yd.cpu())
     Y1 = frlap.frlap_apply_host(plan, U, chunk=8)  # one chunk holding the whole batch
     assert torch.equal(Y1, Y)
+
+
+@pytest.mark.parametrize("d,Ns,prec", [(2, (256, 192), 3), (3, (32, 24, 40), 2), (2, (128, 128), 1)])
+def test_autotune_keeps_results(frlap, d, Ns, prec):
+    """frlap_plan_autotune picks a power-of-two lines-per-CTA count for every stage of each engine the
+    plan uses; the launch shape does not change the arithmetic, so applies stay bit for bit the same."""
+    h = 2.0 / max(Ns)
+    plan = frlap.Plan(d, 1.4, h, Ns, prec=prec)
+    dt = torch.float32 if prec == 1 else torch.float64
+    U = _t(np.stack([inp.normal_field(Ns, seed=60 + b) for b in range(3)]), dt)
+    Y0 = frlap.frlap_apply_batch(plan, U)
+    y32 = frlap.frlap_apply_f32(plan, U[0].float().contiguous()) if prec == 2 else None
+    c64, c32 = frlap.frlap_plan_autotune(plan, 3)
+    ns = 3 if d == 2 else 5
+    used = [c32] if prec == 1 else ([c64, c32] if prec == 2 else [c64])
+    for c in used:
+        assert all(t > 0 and (t & (t - 1)) == 0 for t in c[:ns]), c
+    assert torch.equal(frlap.frlap_apply_batch(plan, U), Y0)
+    if y32 is not None:
+        assert torch.equal(frlap.frlap_apply_f32(plan, U[0].float().contiguous()), y32)
