@@ -532,6 +532,7 @@ def run_solver_suite(args):
         row = {}
         for name, prec, solver, pre in variants:
             plan = fl.Plan(d, alpha, h, (N,) * d, prec=prec)
+            fl.frlap_plan_autotune(plan, 1)  # launch shapes (not part of the solve time)
             if pre == fl.FRLAP_PRECOND_STRANG:
                 fl.frlap_precond_strang(plan)
             elif pre == fl.FRLAP_PRECOND_LEARNED:

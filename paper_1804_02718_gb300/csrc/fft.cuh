@@ -337,7 +337,7 @@ template <typename T, int R, int SIGN, bool ZIN>
 __device__ __forceinline__ void regs_first_stage(cplx<T>* v) {
   using C = cplx<T>;
   constexpr int B = 16 / R;
-  constexpr bool Z = ZIN && std::is_same<T, double>::value;
+  constexpr bool Z = ZIN && !std::is_same<T, float>::value;  // FP32: the zero-aware form measured no faster
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     C t[R];
