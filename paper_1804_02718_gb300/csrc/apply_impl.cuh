@@ -125,10 +125,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
     v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
   }
   fft_regs<T, -1, true, REM>(v, buf, logH, lane, tw, logP, false);
-  line_sync(logH);
+  line_sync<T>(logH);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
-  line_sync(logH);
+  line_sync<T>(logH);
   // unpack the half-length transform Z of the packed samples into X[k], k = 0..H:
   // with a = Z[k], b = conj Z[H-k], E = (a + b)/2 and O = -i (a - b)/2,
   // X[k] = E + W^k O and X[H-k] = conj(E - W^k O)  (W = exp(-2 pi i / 2H); one product per pair)
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
     buf[spad(k)] = A + iT;
     if (k != km && km != H) buf[spad(km)] = conjg(A - iT);
   }
-  line_sync(logH);
+  line_sync<T>(logH);
   C v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
     v[m] = (m < 8 && valid && i < n) ? src[i] : czero<C>();
   }
   fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
-  line_sync(logP);
+  line_sync<T>(logP);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
   __syncthreads();
