@@ -59,7 +59,7 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # DRAM traffic of one batched launch (8 instances) of the dominant kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu captures summarised under profiles/; absent where the kernel
 # changed since the capture
-MEASURED_TRAFFIC = {("colmul", "df64"): 1293.6e6, ("colmul", "f32"): 598.0e6}
+MEASURED_TRAFFIC = {("colmul", "df64"): 1293.1e6, ("colmul", "f32"): 597.4e6}
 
 # double-float: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the FP32
 # instructions one FP64-equivalent FFT flop costs (add 11, mul 7; FFT mix 2 adds : 1 mul -> 29/3)
