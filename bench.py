@@ -220,6 +220,21 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def max_over_ranks(dist, ms, device):
+    """The slowest rank's time (the job's time) on every rank; ms itself without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, batch, unknowns, total_ms):
+    """Whole-job unknowns/s: every rank applies steps x batch vectors of `unknowns` in the job's time."""
+    return world * steps * batch * unknowns / (total_ms / 1e3)
+
+
 def time_applies(fl, torch, plan, U, Y, work, steps, warmup, d, barrier=None):
     """Time `steps` steps, each one batched apply of all of U (shape (batch, *plan.shape)) with one
     launch per stage.  Returns (total_ms, per-stage ms per instance (launch time / batch), launches)."""
@@ -309,12 +324,9 @@ def main():
     clocks.start()
     total_ms, stage_ms, launches = time_applies(fl, torch, plan, U, Y, work, args.steps, args.warmup, 2, barrier)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
     M = plan.M
-    value = world * args.steps * BATCH * M / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, BATCH, M, total_ms)
 
     # roofline of the dominant kernel
     names = stage_names(2)
