@@ -574,6 +574,10 @@ def run_solver_suite(args):
     # batched Allen-Cahn: 64 instances, alpha ~ U[1.2,1.9], grids 255/511/1023, 200 steps, one graph launch
     batch = inp.allen_cahn_batch()
     plans = [fl.Plan(2, al, 2.0 / (n + 1), (n + 1, n + 1), prec=fl.FRLAP_DF64) for al, n, _ in batch]
+    # the first plan of each grid leads its group in the batched launch: tune its launch shapes
+    for n in sorted({n for _, n, _ in batch}):
+        first = next(i for i, (_, m, _) in enumerate(batch) if m == n)
+        fl.frlap_plan_autotune(plans[first], sum(1 for _, m, _ in batch if m == n))
     us = [torch.from_numpy(u0).cuda() for _, _, u0 in batch]
     dt, (its, st, code) = _timed(lambda: fl.frlap_allen_cahn_batch(plans, us, 1e-3, 0.05, 200, rtol=1e-10,
                                                                    raise_on_error=False))
