@@ -197,11 +197,13 @@ def test_apply_batch_matches_oracle(frlap, d, Ns, alpha, prec, tol):
 
 
 def test_apply_batch_full_size_and_errors(frlap):
-    """The throughput launch: 8 x 2047^2 double-float instances in one batched apply; two checked
-    against the oracle, all eight bit for bit against single applies.  Bad arguments are refused."""
+    """The throughput launch: 8 x 2047^2 double-float instances in one batched apply with the autotuned
+    launch shapes, as the bench times it; two checked against the oracle, all eight bit for bit against
+    single applies.  Bad arguments are refused."""
     Ns, alpha = (2048, 2048), 1.5
     h = 2.0 / 2048
     plan = frlap.Plan(2, alpha, h, Ns, prec=frlap.FRLAP_DF64)
+    frlap.frlap_plan_autotune(plan, 8)  # the bench's launch shapes
     U = torch.stack([_t(inp.normal_field(Ns, seed=100 + b)) for b in range(8)])
     Y = frlap.frlap_apply_batch(plan, U)
     a_ref, c = _oracle(2, alpha, h, Ns)
