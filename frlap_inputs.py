@@ -101,3 +101,19 @@ def allen_cahn_batch(count=64, seed_alpha=4, seed_u0=5, grids=(255, 511, 1023)):
         u0 = np.random.default_rng(seed_u0 + i).uniform(-0.9, 0.9, size=(n, n))
         out.append((float(alphas[i]), n, u0))
     return out
+
+
+def kissing_bubbles(N, h, delta, centers=None, radius=0.12, a=0.0):
+    """Two osculating bubbles on the box (0, N h)^d: u0 = 1 - tanh(d1/delta) - tanh(d2/delta) with
+    d_i = |x - x_i| - radius (the initial condition of the paper's Allen-Cahn example, eq.
+    u0-two_bubble; centres (0.4, 0.4), (0.6, 0.6) in 2D and (0.4, 0.6, 0.5), (0.6, 0.4, 0.5) in 3D).
+    Returns u0 on the interior nodes."""
+    d = len(N)
+    if centers is None:
+        centers = [(0.4, 0.4), (0.6, 0.6)] if d == 2 else [(0.4, 0.6, 0.5), (0.6, 0.4, 0.5)]
+    X = grid(N, h, a)
+    u = np.ones_like(X[0])
+    for c in centers:
+        r = np.sqrt(sum((X[k] - c[k]) ** 2 for k in range(d)))
+        u -= np.tanh((r - radius) / delta)
+    return u

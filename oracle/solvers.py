@@ -8,6 +8,13 @@
   u_t = -eps^2 (-Delta)^{alpha/2} u + u - u^3 with u = 0 outside the box; the
   paper's own model (eqs. AC-1, AC-2) uses Crank-Nicolson and u = -1 outside,
   this is the semi-implicit variant of the same equation.
+* allen_cahn_cn_step: the paper's own model (eqs. AC-1, AC-2, Sec. 5.4):
+  u_t = -(-Delta)^{alpha/2} u - delta^{-alpha} u (u^2 - 1), u = -1 outside the box,
+  written for ubar = u + 1 (zero outside; the fractional Laplacian of a constant is 0)
+  and stepped by Crank-Nicolson in the linear term, the reaction term taken at t_n:
+  (I + tau/2 A) ubar^{n+1} = (I - tau/2 A) ubar^n - tau delta^{-alpha} f(ubar^n - 1),
+  f(u) = u (u^2 - 1).  The paper says Crank-Nicolson with CG per step but not how the
+  reaction term enters; this linear-per-step form is the reading.
 * strang_symbol / strang_solve: the multilevel Strang circulant of the Toeplitz
   matrix (first column t_{min(j, n-j)} per axis), inverted by FFTs of size n.
 """
@@ -73,3 +80,28 @@ def strang_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
 def strang_solve(lam_s: np.ndarray, r: np.ndarray) -> np.ndarray:
     """z = C^-1 r for the Strang circulant with eigenvalues lam_s."""
     return np.fft.ifftn(np.fft.fftn(r) / lam_s).real
+
+
+def allen_cahn_cn_rhs(apply, ubar: np.ndarray, tau: float, delta: float, alpha: float) -> np.ndarray:
+    """(I - tau/2 A) ubar - tau delta^{-alpha} u (u^2 - 1), u = ubar - 1."""
+    u = ubar - 1.0
+    return ubar - 0.5 * tau * apply(ubar) - tau * delta ** (-alpha) * u * (u * u - 1.0)
+
+
+def allen_cahn_cn_step(apply, ubar: np.ndarray, tau: float, delta: float, alpha: float, rtol: float = 1e-10,
+                       maxit: int = 100000):
+    """One Crank-Nicolson step of the paper's model for ubar = u + 1: solve
+    (I + tau/2 A) v = allen_cahn_cn_rhs(...) by CG from v0 = ubar."""
+    rhs = allen_cahn_cn_rhs(apply, ubar, tau, delta, alpha)
+
+    def shifted(v):
+        return v + 0.5 * tau * apply(v)
+
+    return cg(shifted, rhs, x0=ubar, rtol=rtol, maxit=maxit)
+
+
+def bubble_mass(ubar: np.ndarray, h: float) -> float:
+    """h^d sum ubar: the integral of u + 1 over the box (u + 1 vanishes outside), the bubbles' area
+    (2D) or volume (3D) up to the interface width.  The paper plots int |u|, which is infinite
+    with u = -1 outside; this is the reading."""
+    return float(ubar.sum() * h ** ubar.ndim)

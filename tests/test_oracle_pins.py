@@ -282,3 +282,55 @@ def test_strang_circulant_inverse_and_positivity():
         C = col[diff]
         x = inp.normal_field(tuple(nr + 1 for nr in reversed(shape)), seed=2)
         np.testing.assert_allclose(solvers.strang_solve(lam, (C @ x.reshape(-1)).reshape(shape)), x, rtol=1e-10, atol=1e-12)
+
+
+def _small_operator(alpha, N=8):
+    h = 1.0 / N
+    a = scheme.coefficients(2, alpha, h, N)
+    c = scheme.c_d_alpha(2, alpha)
+    A = scheme.dense_matrix(a, c, (N - 1, N - 1))
+    return A, h
+
+
+def test_allen_cahn_cn_linear_part_is_second_order():
+    """With the reaction switched off (delta huge) the Crank-Nicolson step must track exp(-t A) ubar0
+    (computed from the eigen-decomposition of the dense matrix) with second-order error in tau: halving
+    tau quarters the error.  A first-order scheme (backward Euler) would halve it; a wrong sign or a
+    missing 1/2 would not converge."""
+    A, h = _small_operator(1.5)
+    lam, V = np.linalg.eigh(A)
+    u0 = inp.kissing_bubbles((8, 8), h, 0.1) + 1.0
+    T = 0.02
+    exact = V @ (np.exp(-T * lam) * (V.T @ u0.reshape(-1)))
+    errs = []
+    for nsteps in (4, 8, 16):
+        tau = T / nsteps
+        ub = u0.copy()
+        for _ in range(nsteps):
+            ub, _, _ = solvers.allen_cahn_cn_step(lambda v: (A @ v.reshape(-1)).reshape(v.shape), ub, tau, 1e12,
+                                                  1.5, rtol=1e-14)
+        errs.append(np.linalg.norm(ub.reshape(-1) - exact))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def test_allen_cahn_cn_reaction_part_fixed_points_and_first_order():
+    """With A = 0 the step is explicit Euler for u' = -delta^-alpha u (u^2 - 1): u = -1, 0, 1 stay fixed
+    (ubar = 0, 1, 2), and the error against the exact solution
+    u(t) = u0 / sqrt(u0^2 + (1 - u0^2) exp(-2 t / delta^alpha)) halves with tau."""
+    zero = lambda v: np.zeros_like(v)  # noqa: E731
+    delta, alpha = 0.5, 1.3
+    for ubar in (0.0, 1.0, 2.0):
+        v = np.full((3, 3), ubar)
+        out, _, _ = solvers.allen_cahn_cn_step(zero, v, 0.01, delta, alpha)
+        assert np.allclose(out, ubar, atol=1e-15)
+    u0 = np.array([[-0.7, -0.2, 0.3, 0.8]])
+    T = 0.2
+    k = delta ** (-alpha)
+    exact = u0 / np.sqrt(u0 ** 2 + (1 - u0 ** 2) * np.exp(-2 * k * T))
+    errs = []
+    for nsteps in (50, 100, 200):
+        ub = u0 + 1.0
+        for _ in range(nsteps):
+            ub, _, _ = solvers.allen_cahn_cn_step(zero, ub, T / nsteps, delta, alpha)
+        errs.append(np.abs(ub - 1.0 - exact).max())
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2, errs
