@@ -585,6 +585,21 @@ def run_solver_suite(args):
     out["allen_cahn_batch_64x200"] = {"s": dt, "status": code, "total_cg_iters": int(sum(its)),
                                      "unknown_steps_per_s": unknown_steps / dt,
                                      "max_abs_u": max(float(u.abs().max().item()) for u in us)}
+    # the paper's own Allen-Cahn example (Crank-Nicolson, u = -1 outside, kissing bubbles, delta = 0.03,
+    # tau = 5e-4 until t = 0.015 = 30 steps), at the grids and alphas of its CPU-time table Tab10
+    cn = {}
+    for N in (128, 256, 512, 1024):
+        for al in (1.9, 1.5, 1.0, 0.7):
+            h = 1.0 / N
+            plan = fl.Plan(2, al, h, (N, N), prec=fl.FRLAP_DF64)
+            fl.frlap_plan_autotune(plan, 1)
+            ub = torch.from_numpy(inp.kissing_bubbles((N, N), h, 0.03) + 1.0).cuda()
+            plan.workspace(fl.FRLAP_OP_AC)
+            dt, (its, mass) = _timed(lambda: fl.frlap_allen_cahn_cn(plan, ub, 5e-4, 0.03, 30, rtol=1e-10))
+            cn[f"N{N}_alpha{al}"] = {"s": dt, "cg_iters": its, "mass_t0.015": mass[-1]}
+            del plan, ub
+            torch.cuda.empty_cache()
+    out["paper_allen_cahn_cn_to_t0.015"] = cn
     print(json.dumps(out), flush=True)
 
 

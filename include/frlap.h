@@ -253,6 +253,20 @@ frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void*
 frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double tau, double eps, int nsteps,
                                    double rtol, int* iters, void* d_work, void* stream);
 
+/* nsteps Crank-Nicolson steps of the paper's own fractional Allen-Cahn model (eqs.
+ * AC-1, AC-2, Sec. 5.4): u_t = -(-Delta)^{alpha/2} u - delta^{-alpha} u (u^2 - 1) on the
+ * box, u = -1 outside.  The unknown is ubar = u + 1, which vanishes outside (the
+ * fractional Laplacian of a constant is zero).  Each step solves
+ *   (I + tau/2 A) ubar^{n+1} = (I - tau/2 A) ubar^n - tau delta^{-alpha} u^n ((u^n)^2 - 1)
+ * by CG from ubar^n to relative residual rtol (the reaction term taken at t_n: the
+ * paper states Crank-Nicolson with one CG solve per step but not how the reaction
+ * enters).  d_ubar: prod(n_r) doubles, updated in place.  h_mass (host, may be NULL):
+ * nsteps doubles, h^d sum ubar after each step (the bubbles' area or volume).
+ * *iters (may be NULL): total CG iterations.  d_work: frlap_workspace_bytes(plan,
+ * FRLAP_OP_AC) bytes.  Synchronises stream.  F32 plans are refused (FRLAP_EINVAL). */
+frlap_status frlap_allen_cahn_cn(const frlap_plan* plan, double* d_ubar, double tau, double delta, int nsteps,
+                                 double rtol, int* iters, double* h_mass, void* d_work, void* stream);
+
 /* ---- learned preconditioner (spec extension; the paper has no learned part) ----
  * A per-frequency MLP on the symbol octant: features (alpha, kappa_x, kappa_y,
  * kappa_z), kappa_r = k_r / (P_r/2) (kappa_z = 0 in 2D), two tanh layers of

@@ -10,7 +10,7 @@ from ._binding import (  # noqa: F401
     FRLAP_SOLVE_IR, FRLAP_PRECOND_NONE, FRLAP_PRECOND_STRANG, FRLAP_PRECOND_LEARNED, LIB_PATH, STATUS, FrlapError, Plan, frlap_allen_cahn_step, frlap_apply, frlap_apply_f32,
     frlap_apply_nstages, frlap_apply_profiled, frlap_apply_noalloc, NOALLOC_MAX_BYTES,
     frlap_apply_batch, frlap_apply_batch_workspace_bytes, frlap_apply_host, frlap_apply_host_workspace_bytes,
-    frlap_plan_autotune,
+    frlap_plan_autotune, frlap_allen_cahn_cn,
     frlap_c_dalpha, frlap_coeffs, frlap_pcg_solve, frlap_precond_strang, frlap_precond_set_symbol, frlap_precond_apply,
     frlap_mlp_multiplier, frlap_learn_workspace_bytes, frlap_learn_grad, frlap_adam_step, frlap_cg_pairs, MLP_NPARAM,
     frlap_allen_cahn_batch, frlap_allen_cahn_batch_workspace_bytes, frlap_plan_create, frlap_plan_destroy,

@@ -61,6 +61,7 @@ _SIGS = {
     "frlap_allen_cahn_batch": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _D, _I, _D, _I,
                                     ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P]),
     "frlap_allen_cahn_step": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), _P, _P]),
+    "frlap_allen_cahn_cn": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
 
@@ -466,3 +467,17 @@ def frlap_allen_cahn_step(plan: Plan, u: torch.Tensor, tau: float, eps: float, n
                                        ctypes.byref(it), ctypes.c_void_p(work.data_ptr()), _stream(stream)),
            "frlap_allen_cahn_step")
     return it.value
+
+
+def frlap_allen_cahn_cn(plan: Plan, ubar: torch.Tensor, tau: float, delta: float, nsteps: int = 1,
+                        rtol: float = 1e-10, work: torch.Tensor = None, stream=None):
+    """Crank-Nicolson steps of the paper's Allen-Cahn model for ubar = u + 1 (in place).
+    Returns (total CG iterations, list of the masses h^d sum ubar after each step)."""
+    it = ctypes.c_int(0)
+    mass = (ctypes.c_double * max(1, int(nsteps)))()
+    if work is None:
+        work = plan.workspace(FRLAP_OP_AC)
+    _check(lib().frlap_allen_cahn_cn(plan.handle, _dev(ubar, torch.float64, "ubar"), float(tau), float(delta),
+                                     int(nsteps), float(rtol), ctypes.byref(it), mass,
+                                     ctypes.c_void_p(work.data_ptr()), _stream(stream)), "frlap_allen_cahn_cn")
+    return int(it.value), list(mass[:int(nsteps)])

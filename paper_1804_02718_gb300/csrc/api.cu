@@ -45,6 +45,8 @@ frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, d
                            void* work, cudaStream_t st);
 cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host);
 cudaError_t scale_to_f32_launch(const double* src, float* dst, size_t n, double s, cudaStream_t st);
+frlap_status allen_cahn_cn_impl(const Plan& p, double* ub, double tau, double delta, int nsteps, double rtol,
+                                int* iters, double* h_mass, void* work, cudaStream_t st);
 frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, int nsteps, double rtol,
                              int* iters, void* work, cudaStream_t st);
 
@@ -628,6 +630,17 @@ frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double t
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
   return allen_cahn_impl(*plan, d_u, tau, eps, nsteps, rtol, iters, d_work, (cudaStream_t)stream);
+}
+
+frlap_status frlap_allen_cahn_cn(const frlap_plan* plan, double* d_ubar, double tau, double delta, int nsteps,
+                                 double rtol, int* iters, double* h_mass, void* d_work, void* stream) {
+  if (!plan || !d_ubar) return fail(FRLAP_EINVAL, "plan or d_ubar is NULL");
+  if (plan->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "Allen-Cahn steps need an F64, DF64 or MIXED plan");
+  if (!(tau > 0.0) || !(delta > 0.0) || nsteps < 0 || !(rtol > 0.0))
+    return fail(FRLAP_EINVAL, "need tau > 0, delta > 0, nsteps >= 0, rtol > 0");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  return allen_cahn_cn_impl(*plan, d_ubar, tau, delta, nsteps, rtol, iters, h_mass, d_work, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -297,6 +297,25 @@ __global__ void k_correct(double* x, const float* __restrict__ d32, const double
     x[i] += sc * (double)d32[i];
 }
 
+// Crank-Nicolson right-hand side of the paper's model for ubar = u + 1 (eqs. AC-1, AC-2):
+// ubar - tau/2 A ubar - tau delta^-alpha u (u^2 - 1), u = ubar - 1
+__global__ void k_cn_rhs(const double* __restrict__ ub, const double* __restrict__ aub, double* rhs, size_t n,
+                         double tau, double kdel) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double b = ub[i], u = b - 1.0;
+    rhs[i] = b - 0.5 * tau * aub[i] - tau * kdel * u * (u * u - 1.0);
+  }
+}
+
+// out = scale * sum x, by one CTA in a fixed order (deterministic)
+__global__ void k_sum_one_block(const double* __restrict__ x, size_t n, double scale, double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) v += x[i];
+  const double t = block_sum(v, red);
+  if (threadIdx.x == 0) *out = scale * t;
+}
+
 // Allen-Cahn right-hand side u + tau (u - u^3)
 __global__ void k_ac_rhs(const double* __restrict__ u, double* rhs, size_t n, double tau) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -554,7 +573,8 @@ size_t ir_work_bytes(const Plan& p) {
   return cg_work_bytes(p, 8) + cg_work_bytes(p, 4) + vec_bytes(p, 8) + 2 * vec_bytes(p, 4) + 256;
 }
 
-size_t ac_work_bytes(const Plan& p) { return cg_work_bytes(p, 8) + vec_bytes(p, 8); }
+// CG workspace, two vectors (right-hand side, A ubar) and a slot for the mass of the Crank-Nicolson model
+size_t ac_work_bytes(const Plan& p) { return cg_work_bytes(p, 8) + 2 * vec_bytes(p, 8) + 256; }
 
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                             const float* mu, double inner_rtol, int* iters, double* relres, void* work,
@@ -623,6 +643,47 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
   if (iters) *iters = total;
   if (relres) *relres = rel;
   if (!(rel <= rtol)) return fail(FRLAP_ENOCONV, "iterative refinement did not reach rtol");
+  return FRLAP_OK;
+}
+
+// The paper's model (eqs. AC-1, AC-2; Crank-Nicolson in time, Sec. 5.4) for ubar = u + 1: per step
+// rhs = (I - tau/2 A) ubar - tau delta^-alpha f(ubar - 1), then (I + tau/2 A) ubar' = rhs by CG from
+// ubar; h_mass[step] = h^d sum ubar' if h_mass is given.
+frlap_status allen_cahn_cn_impl(const Plan& p, double* ub, double tau, double delta, int nsteps, double rtol,
+                                int* iters, double* h_mass, void* work, cudaStream_t st) {
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  void* cgw = w;
+  w += cg_work_bytes(p, 8);
+  double* rhs = reinterpret_cast<double*>(w);
+  w += vec_bytes(p, 8);
+  double* aub = reinterpret_cast<double*>(w);
+  w += vec_bytes(p, 8);
+  double* dmass = reinterpret_cast<double*>(w);
+  const CgBufs b = carve(p, cgw, 8);  // its apply workspace is free between the solves
+  const double kdel = pow(delta, -p.alpha);
+  const double hd = pow(p.h, (double)p.d);
+  int total = 0;
+  CgState hS;
+  for (int step = 0; step < nsteps; ++step) {
+    cudaError_t e = apply64(p, ub, aub, b.awork, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "apply (Crank-Nicolson right-hand side)");
+    k_cn_rhs<<<vgrid(p.M), kThreads, 0, st>>>(ub, aub, rhs, p.M, tau, kdel);
+    FRLAP_LAUNCH_CHECK("k_cn_rhs");
+    frlap_status rc = run_cg<double>(p, rhs, ub, 1.0, 0.5 * tau, rtol, 100000, 1, nullptr, cgw, st, &hS);
+    if (rc != FRLAP_OK) return rc;
+    total += hS.iters;
+    if (hS.status != FRLAP_OK) {
+      if (iters) *iters = total;
+      return fail((frlap_status)hS.status, "Allen-Cahn (Crank-Nicolson) CG solve stopped early");
+    }
+    if (h_mass) {
+      k_sum_one_block<<<1, 1024, 0, st>>>(ub, p.M, hd, dmass);
+      FRLAP_LAUNCH_CHECK("k_sum_one_block");
+      FRLAP_CUDA_TRY(cudaMemcpyAsync(h_mass + step, dmass, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (h_mass) FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (iters) *iters = total;
   return FRLAP_OK;
 }
 
