@@ -128,20 +128,20 @@ def test_double_float_cg_reaches_fp64_residual(frlap):
     assert d <= 1e-8
 
 
-@pytest.mark.parametrize("prec", [0, 3])
-def test_allen_cahn_cn_matches_oracle(frlap, prec):
+@pytest.mark.parametrize("d,N,prec", [(2, 64, 0), (2, 64, 3), (3, 16, 3)])
+def test_allen_cahn_cn_matches_oracle(frlap, d, N, prec):
     """The paper's Allen-Cahn model (Crank-Nicolson for ubar = u + 1, u = -1 outside) from the kissing
-    bubbles on (0,1)^2: four steps and the masses after each against the oracle."""
-    N, alpha, tau, delta = 64, 1.5, 1e-3, 0.1
+    bubbles on (0,1)^d: four steps and the masses after each against the oracle."""
+    alpha, tau, delta = 1.5, 1e-3, 0.1
     h = 1.0 / N
-    a, c = _coef(2, alpha, h, N), scheme.c_d_alpha(2, alpha)
-    ub0 = inp.kissing_bubbles((N, N), h, delta) + 1.0
+    a, c = _coef(d, alpha, h, N), scheme.c_d_alpha(d, alpha)
+    ub0 = inp.kissing_bubbles((N,) * d, h, delta) + 1.0
     op = fast.FastOperator(a, c, ub0.shape)
     ref, masses = ub0.copy(), []
     for _ in range(4):
         ref, _, _ = solvers.allen_cahn_cn_step(op, ref, tau, delta, alpha, rtol=1e-13)
         masses.append(solvers.bubble_mass(ref, h))
-    plan = frlap.Plan(2, alpha, h, (N, N), prec=prec)
+    plan = frlap.Plan(d, alpha, h, (N,) * d, prec=prec)
     ub = _t(ub0)
     it, m = frlap.frlap_allen_cahn_cn(plan, ub, tau, delta, nsteps=4, rtol=1e-13)
     assert it > 0
