@@ -38,7 +38,9 @@ import frlap_inputs as inp  # noqa: E402
 
 ALPHA = 1.5
 NGRID = 2048
-BATCH = 8
+BATCH = 8  # vectors per step of the 2D workload
+BATCH_2D = BATCH
+NGRID_3D, ALPHA_3D, BATCH_3D = 256, 1.0, 2
 E2E_CHUNK = 1  # vectors per chunk of the host-buffer pipeline (1, 2, 4, 8 measured 6.9, 6.6, 5.8, 4.7 G unknowns/s)
 METRIC = "apply unknowns/s & %HBM peak; PCG time to 1e-10 of FP64 sol vs plain FP64 CG"
 UNIT = "unknowns/s"
@@ -56,10 +58,11 @@ def peaks():
 # FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
-# DRAM traffic of one batched launch (8 instances) of the dominant kernel (dram__bytes_read.sum +
+# DRAM traffic of one batched launch of the dominant kernel, by (dims, kernel, engine) (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu captures summarised under profiles/; absent where the kernel
 # changed since the capture
-MEASURED_TRAFFIC = {("colmul", "df64"): 1293.1e6, ("colmul", "f32"): 597.4e6}
+MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1293.1e6, (2, "colmul", "f32"): 597.4e6,
+                    (3, "colmul", "df64"): 2462.1e6, (3, "colmul", "f32"): 1187.0e6}
 
 # double-float: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the FP32
 # instructions one FP64-equivalent FFT flop costs (add 11, mul 7; FFT mix 2 adds : 1 mul -> 29/3)
@@ -281,6 +284,8 @@ def main():
     ap.add_argument("--suite", default="apply", choices=["apply", "solvers"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--dims", type=int, default=2, choices=[2, 3],
+                    help="2: the 2047^2 workload (default); 3: 255^3, alpha = 1.0, 2 vectors per step")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -312,9 +317,12 @@ def main():
     prec = {"f32": fl.FRLAP_F32, "f64": fl.FRLAP_F64, "df64": fl.FRLAP_DF64}[args.prec]
     dt = torch.float32 if args.prec == "f32" else torch.float64
     eb = 4 if args.prec == "f32" else 8
-    h = 2.0 / NGRID
-    Ns = (NGRID, NGRID)
-    plan = fl.Plan(2, ALPHA, h, Ns, prec=prec)
+    # the workload: 2D 2047^2, alpha = 1.5, 8 vectors per step (default) or 3D 255^3, alpha = 1.0, 2 vectors
+    D = args.dims
+    NG, AL, BATCH = (NGRID, ALPHA, BATCH_2D) if D == 2 else (NGRID_3D, ALPHA_3D, BATCH_3D)
+    h = 2.0 / NG
+    Ns = (NG,) * D
+    plan = fl.Plan(D, AL, h, Ns, prec=prec)
     tuned = fl.frlap_plan_autotune(plan, BATCH)  # launch shapes, before the timed region
     U = torch.stack([torch.from_numpy(inp.normal_field(Ns, seed=100 + b)) for b in range(BATCH)]).to("cuda", dt)
     Y = torch.empty_like(U)
@@ -322,16 +330,16 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    total_ms, stage_ms, launches = time_applies(fl, torch, plan, U, Y, work, args.steps, args.warmup, 2, barrier)
+    total_ms, stage_ms, launches = time_applies(fl, torch, plan, U, Y, work, args.steps, args.warmup, D, barrier)
     clk = clocks.stop()
     total_ms = max_over_ranks(dist, total_ms, "cuda")
     M = plan.M
     value = job_throughput(world, args.steps, BATCH, M, total_ms)
 
     # roofline of the dominant kernel
-    names = stage_names(2)
-    sb = stage_bytes(2, plan.n, plan.P, eb)
-    sf = stage_flops(2, plan.n, plan.P)
+    names = stage_names(D)
+    sb = stage_bytes(D, plan.n, plan.P, eb)
+    sf = stage_flops(D, plan.n, plan.P)
     dom = int(np.argmax(stage_ms))
     hbm, hbm_src = peaks()
     if args.prec == "f64":
@@ -346,13 +354,13 @@ def main():
         ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
         roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": DF64_PEAK_TFLOPS,
                 "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / DF64_PEAK_TFLOPS,
-                "traffic": MEASURED_TRAFFIC.get((names[dom], args.prec)),
+                "traffic": MEASURED_TRAFFIC.get((D, names[dom], args.prec)),
                 "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / 29/3 FP32 instructions per FP64-equivalent flop",
                 "flops_per_launch": sf[dom] * BATCH}
     else:
         ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": MEASURED_TRAFFIC.get((names[dom], args.prec)),
+                "frac": ach / hbm, "traffic": MEASURED_TRAFFIC.get((D, names[dom], args.prec)),
                 "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom] * BATCH}
     roof["instances_per_launch"] = BATCH
     roof["launch_ms"] = stage_ms[dom] * BATCH
@@ -394,7 +402,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate()
+        cpu = cpu_oracle_rate(d=D, N=NG, alpha=AL)
 
     if rank == 0:
         line = {
@@ -402,12 +410,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"df64": "f32x2"}.get(args.prec, args.prec),
             "data": "synthetic",
-            "config": {"workload": f"2D {NGRID - 1}x{NGRID - 1} alpha={ALPHA} {args.prec.upper()} FFT Toeplitz apply",
+            "config": {"workload": f"{D}D {NG - 1}^{D} alpha={AL} {args.prec.upper()} FFT Toeplitz apply",
                        "batch_per_step": BATCH, "launch": "frlap_apply_batch (one launch per stage for the batch)",
                        "lines_per_cta": {"fp64_side": tuned[0][:3], "fp32": tuned[1][:3],
                                          "chosen_by": "frlap_plan_autotune"},
                        "embedding": list(plan.P),
-                       "l2": "inputs larger than L2 (8 distinct 2047^2 vectors per step)",
+                       "l2": f"inputs larger than L2 ({BATCH} distinct {NG - 1}^{D} vectors per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
             "apply": {"ms": apply_ms, "model_bytes": model_bytes,
