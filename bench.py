@@ -64,9 +64,46 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1293.1e6, (2, "colmul", "f32"): 597.4e6,
                     (3, "colmul", "df64"): 2462.1e6, (3, "colmul", "f32"): 1187.0e6}
 
-# double-float: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the FP32
-# instructions one FP64-equivalent FFT flop costs (add 11, mul 7; FFT mix 2 adds : 1 mul -> 29/3)
-DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / (29.0 / 3.0) / 1e12
+# double-float roofline: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the
+# FP32 instructions the kernel's double-float butterflies take per FP64-equivalent flop (flops counted
+# by the usual 5 L log2 L per complex transform).  Instruction costs of the double-float operations:
+# add 11, add without renormalisation 8, multiply 7, complex product feeding a sum (two lazy
+# two-product sums) 32.
+FP32_ISSUE = 152 * 128 * 2.07e9
+DF_DFT4 = 4 * 2 * 8 + 4 * 2 * 11                              # lazy first-level sums, full second level
+DF_DFT16_TAIL = 8 * 32 + 4 * DF_DFT4                          # 8 products by W16^m, four length-4 DFTs
+DF_DFT16 = 4 * DF_DFT4 + DF_DFT16_TAIL
+DF_DFT16_ZIN = 4 * 4 * 2 * 11 + DF_DFT16_TAIL                 # upper half of the input zero
+DF_DFT8_COMBINE = 2 * (2 * 11 + 2 * 7) + 8 * 2 * 11
+DF_DFT8 = 2 * DF_DFT4 + DF_DFT8_COMBINE
+DF_DFT8_ZIN = 8 * 2 * 11 + DF_DFT8_COMBINE
+DF_TW16 = 15 * 32                                             # stage twiddles of a radix-16 butterfly
+
+
+def df_fft_instr(L, zin):
+    """FP32 instructions of one double-float transform of length L (the engine's stage order)."""
+    n = int(math.log2(L))
+    rem = n % 4
+    if rem == 3:
+        return L // 8 * (DF_DFT8_ZIN if zin else DF_DFT8) + (n - 3) // 4 * L // 16 * (DF_DFT16 + DF_TW16)
+    first = L // 16 * (DF_DFT16_ZIN if zin else DF_DFT16)
+    mid = ((n - rem) // 4 - 1) * L // 16 * (DF_DFT16 + DF_TW16)
+    last = {0: 0, 1: L // 2 * (32 + 2 * 2 * 11), 2: L // 4 * (3 * 32 + DF_DFT4)}[rem]
+    return first + mid + last
+
+
+def df64_instr_per_flop(kernel, P):
+    """FP32 instructions per FP64-equivalent flop of one line of `kernel` (P: embedding per axis)."""
+    if kernel == "colmul":
+        L = P[-1]
+        return (df_fft_instr(L, True) + df_fft_instr(L, False) + 14 * L) / (10 * L * math.log2(L) + 2 * L)
+    if kernel in ("c2cT_fwd", "c2cT_inv"):
+        L = P[1]
+        return df_fft_instr(L, kernel == "c2cT_fwd") / (5 * L * math.log2(L))
+    # r2c_T / c2r_T: half-length complex transform and the split of its H + 1 bins (two sums, a
+    # product, a sum: about 104 instructions a bin)
+    H = P[0] // 2
+    return (df_fft_instr(H, kernel == "r2c_T") + 104 * (H + 1)) / (2.5 * P[0] * math.log2(P[0]))
 
 
 class ClockSampler:
@@ -352,10 +389,13 @@ def main():
         # FFT flops counted as FP64-equivalent operations, each executed as a double-float sequence
         # on the FP32 pipes; peak = FP32 issue rate / FP32 instructions per FP64-equivalent flop
         ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": DF64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / DF64_PEAK_TFLOPS,
+        ipf = df64_instr_per_flop(names[dom], plan.P)
+        peak = FP32_ISSUE / ipf / 1e12
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / peak,
                 "traffic": MEASURED_TRAFFIC.get((D, names[dom], args.prec)),
-                "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / 29/3 FP32 instructions per FP64-equivalent flop",
+                "peak_source": f"FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / {ipf:.2f} FP32 instructions "
+                               "per FP64-equivalent flop of this kernel's double-float butterflies",
                 "flops_per_launch": sf[dom] * BATCH}
     else:
         ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9

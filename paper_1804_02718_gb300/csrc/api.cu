@@ -188,16 +188,17 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   if (prec != FRLAP_F64 && cudaMalloc(&p->lam32, p->lam_count * sizeof(float)) != cudaSuccess)
     return cleanup(FRLAP_ENOMEM, "plan allocation failed");
   for (int r = 0; r < d; ++r) {
-    if (cudaMalloc(&p->tw64[r], p->P[r] * sizeof(double2)) != cudaSuccess ||
+    const int ntw = twiddle_entries(p->P[r]);
+    if (cudaMalloc(&p->tw64[r], ntw * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&p->tw32[r], p->P[r] * sizeof(float2)) != cudaSuccess)
       return cleanup(FRLAP_ENOMEM, "plan allocation failed");
     cudaError_t e = twiddle_launch(p->P[r], p->tw64[r], p->tw32[r], s);
     if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));
     if (p->df64) {
-      if (cudaMalloc(&p->twdf[r], p->P[r] * sizeof(cdf)) != cudaSuccess)
+      if (cudaMalloc(&p->twdf[r], ntw * sizeof(cdf)) != cudaSuccess)
         return cleanup(FRLAP_ENOMEM, "plan allocation failed");
       e = to_df_launch(reinterpret_cast<const double*>(p->tw64[r]), reinterpret_cast<dfl*>(p->twdf[r]),
-                       2 * (size_t)p->P[r], s);
+                       2 * (size_t)ntw, s);
       if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));
     }
   }

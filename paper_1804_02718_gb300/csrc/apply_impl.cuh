@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   const int line0 = blockIdx.x * TL;
   const int line = line0 + l;
   const bool valid = line < nlines;
-  const int LS = sline(H);
+  const int LS = sline_T(H, TL, (int)sizeof(C));
   C* buf = smem + (size_t)l * LS;
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int line0 = blockIdx.x * TL;
   const int line = line0 + l;
-  const int LS = sline(H);
+  const int LS = sline_T(H, TL, (int)sizeof(C));
   const int total = TL * (H + 1);
   load_transposed<C>(smem, in, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   const int line0 = tile * TL;
   const int line = line0 + l;
   const bool valid = line < nlines;
-  const int LS = sline(P);
+  const int LS = sline_T(P, TL, (int)sizeof(C));
   C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
   C v[16];
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   const int line0 = tile * TL;
   const int line = line0 + l;
   const C* src = in + g * gin;
-  const int LS = sline(P);
+  const int LS = sline_T(P, TL, (int)sizeof(C));
   const int total = TL * P;
   load_transposed<C>(smem, src, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
@@ -560,7 +560,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   {
     const int G = Hx >> 4;
     const int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
-    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
@@ -602,7 +602,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     {
       const int G = Py >> 4;
       const int tl = pick_tl_tuned(tuned[1], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
-      const size_t sm = (size_t)tl * sline(Py) * eb;
+      const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
@@ -638,7 +638,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     {
       const int G = Py >> 4;
       const int tl = pick_tl_tuned(tuned[3], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
-      const size_t sm = (size_t)tl * sline(Py) * eb;
+      const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
@@ -657,7 +657,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   {
     const int G = Hx >> 4;
     const int tl = pick_tl_tuned(tuned[p.d == 2 ? 2 : 4], sline(Hx), eb, G, budget, (long long)nrows * B);
-    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
@@ -703,7 +703,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
   {
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
     e = with_rem(p.logP[0] - 1, [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
       cudaError_t e2 = set_smem(k_r2c_T<T, REM>, sm);
@@ -721,7 +721,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
     const int Py = p.P[1];
     const int G = Py >> 4;
     const int tl = pick_tl(sline(Py), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline(Py) * eb;
+    const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
     const int tiles = (nz + tl - 1) / tl;
     e = with_rem(p.logP[1], [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
@@ -787,7 +787,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
     const int Py = p.P[1];
     const int G = Py >> 4;
     const int tl = pick_tl(sline(Py), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline(Py) * eb;
+    const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
     const int tiles = (nz + tl - 1) / tl;
     e = with_rem(p.logP[1], [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
@@ -801,7 +801,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
   {
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
     e = with_rem(p.logP[0] - 1, [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
       cudaError_t e2 = set_smem(k_c2r_T<T, REM>, sm);
@@ -845,7 +845,7 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
     int best = 0;
     float best_ms = 0.f;
     for (int t = 1; t <= 64 && e == cudaSuccess; t *= 2) {
-      if (t * G > 512 || (size_t)t * sline(L) * eb > 227 * 1024) break;
+      if (t * G > 512 || (size_t)t * sline_T(L, t, eb) * eb > 227 * 1024) break;
       if (G < 32 && t < 32 / G) continue;
       p.tl_tuned[eng][st] = t;
       float ms = 0.f;

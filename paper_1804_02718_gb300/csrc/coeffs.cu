@@ -296,6 +296,17 @@ __global__ void k_twiddle(int P, double2* tw64, float2* tw32) {
   if (tw32) tw32[m] = make_float2((float)c, (float)-s);
 }
 
+// radix-16 stage entries of the table (layout: twiddle_entries), gathered from its first P
+__global__ void k_twiddle_stage(int P, int logP, double2* tw64) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 15 * (P / 8 - 1)) return;
+  int logNs = 0;
+  while (15 * ((2 << logNs) - 1) <= i) ++logNs;
+  const int Ns = 1 << logNs, off = i - 15 * (Ns - 1);
+  const int r = off / Ns + 1, k = off % Ns;
+  tw64[P + i] = tw64[(r * k) << (logP - logNs - 4)];
+}
+
 }  // namespace
 
 size_t coeffs_scratch_bytes(int d, int Nmax) {
@@ -337,6 +348,10 @@ cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int N, do
 
 cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s) {
   k_twiddle<<<(P + 255) / 256, 256, 0, s>>>(P, tw64, tw32);
+  int logP = 0;
+  while ((1 << logP) < P) ++logP;
+  const int nst = twiddle_entries(P) - P;
+  k_twiddle_stage<<<(nst + 255) / 256, 256, 0, s>>>(P, logP, tw64);
   return cudaGetLastError();
 }
 

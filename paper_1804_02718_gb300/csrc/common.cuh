@@ -141,8 +141,10 @@ struct Plan {
   double* lam64 = nullptr;     // natural order, FP64 (always built)
   double* lamL64 = nullptr;    // line-major, FP64 (always built)
   float* lam32 = nullptr;      // line-major, FP32 (all plans but F64)
-  double2* tw64[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i m / P_r), m < P_r
-  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  // exp(-2 pi i m / P_r), m < P_r, followed (tw64, twdf) by the radix-16 stage table of
+  // twiddle_entries(P_r): see there
+  double2* tw64[3] = {nullptr, nullptr, nullptr};
+  float2* tw32[3] = {nullptr, nullptr, nullptr};   // the first P_r entries only
   cdf* twdf[3] = {nullptr, nullptr, nullptr};      // the same twiddles as double-floats
   dfl* lamdf = nullptr;        // line-major, as double-floats (DF64 plans)
   bool df64 = false;           // FP64-precision vectors are applied with double-float FFTs
@@ -187,6 +189,14 @@ cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int Nmax,
                           cudaStream_t s);
 size_t coeffs_scratch_bytes(int d, int Nmax);
 cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
+// Entries of an FP64 / double-float twiddle table for embedding size P (a power of two >= 32).
+// [0, P): W_P^m = exp(-2 pi i m / P).  Then, for Ns = 1, 2, 4, ..., P/16, the twiddles of a
+// radix-16 Stockham stage with Ns: W_{16 Ns}^{r k} (r = 1..15, k < Ns) at
+// P + 15 (Ns - 1) + (r - 1) Ns + k, so a warp's 32 consecutive k of one r are 32 consecutive
+// entries (one load over a few cache lines instead of one line per lane).  The stage entries
+// are copies of plain entries (W_{16 Ns}^{r k} = W_P^{r k P / (16 Ns)}), so both give the same bits.
+inline int twiddle_entries(int P) { return P + 15 * (P / 8 - 1); }
+// fills tw64 (twiddle_entries(P) entries) and tw32 (P entries, may be null)
 cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s);
 cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st);
 // dst (line-major, converted to To) = s * oct (natural order); To = double, float or dfl

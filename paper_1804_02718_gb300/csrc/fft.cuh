@@ -28,6 +28,16 @@ namespace frlap {
 __host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 // Slots per line for logical indices 0..L (L itself is used by the real-data transforms).
 __host__ __device__ __forceinline__ int sline(int L) { return L + (L >> 4) + 1; }
+// Line stride of the kernels whose CTA reads or writes its TL lines transposed (element k of
+// lines 0..TL-1 at consecutive addresses in global memory): sline(L) plus the smallest pad that
+// makes the stride W/TL modulo W (W = elements per 128-byte shared-memory wavefront), so the TL
+// lines' elements of W/TL consecutive k fall in distinct bank groups.
+__host__ __device__ __forceinline__ int sline_T(int L, int TL, int esize) {
+  const int W = 128 / esize, base = sline(L);
+  if (TL <= 1) return base;
+  const int target = TL >= W ? 1 : W / TL;
+  return base + ((target - base) % W + W) % W;
+}
 
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft2(C& a, C& b) {
@@ -167,17 +177,22 @@ __device__ __forceinline__ void dftR(C* v) {
   }
 }
 
-// Twiddles W^r, r = 1..15, of one radix-16 butterfly (W = tw[k << sh]), loaded after the
-// stage barrier.  FP64 and double-float load every power from the table (products would
-// cost more than the loads there); FP32 loads W, W^4 and W^8 and forms the rest with at
-// most three chained products.  (Issuing these loads before the barrier was measured
-// slower: the extra live registers cost more than the hidden latency.)
+// Twiddles W^r, r = 1..15, W = W_{16 Ns}^k, of one radix-16 butterfly, loaded after the
+// stage barrier.  FP64 and double-float load every power from the table's stage entries
+// (layout: twiddle_entries; products would cost more than the loads there); FP32 loads W,
+// W^4 and W^8 from the plain entries and forms the rest with at most three chained
+// products.  (Issuing these loads before the barrier was measured slower: the extra live
+// registers cost more than the hidden latency.)
 template <typename T>
-__device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict__ tw, int k, int sh) {
+__device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict__ tw, int k, int logNs,
+                                           int logPtab) {
   if constexpr (!std::is_same<T, float>::value) {
+    const int Ns = 1 << logNs;
+    const cplx<T>* st = tw + (1 << logPtab) + 15 * (Ns - 1) - Ns + k;
 #pragma unroll
-    for (int r = 1; r < 16; ++r) w[r] = tw[(r * k) << sh];
+    for (int r = 1; r < 16; ++r) w[r] = st[r * Ns];
   } else {
+    const int sh = logPtab - logNs - 4;
     w[1] = tw[k << sh];
     w[4] = tw[(4 * k) << sh];
     w[8] = tw[(8 * k) << sh];
@@ -256,7 +271,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
     if (Ns > 1) {
       if constexpr (R == 16) {
         C w[16];
-        twiddles16<T>(w, tw, k, sh);
+        twiddles16<T>(w, tw, k, logNs, logPtab);
 #pragma unroll
         for (int r = 1; r < 16; ++r) v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], w[r]) : cmulc(v[b * R + r], w[r]);
       } else {
@@ -412,7 +427,7 @@ __device__ __forceinline__ void regs_stage16(cplx<T>* v, int lane, int logNs, co
   if (logNs > 0) {
     const int k = lane & ((1 << logNs) - 1);
     cplx<T> w[16];
-    twiddles16<T>(w, tw, k, logPtab - logNs - 4);
+    twiddles16<T>(w, tw, k, logNs, logPtab);
 #pragma unroll
     for (int r = 1; r < 16; ++r) v[r] = (SIGN < 0) ? cmul_lazy(v[r], w[r]) : cmulc_lazy(v[r], w[r]);
   }
