@@ -64,29 +64,36 @@ __device__ __forceinline__ void load_line(C* buf, const C* __restrict__ src, int
   }
 }
 
+// Asynchronous copy of one 8- or 16-byte element from global to shared memory (cp.async;
+// with pred false it writes zeros and reads nothing).  The copies of a thread complete at
+// cp_async_wait_all(); a CTA barrier after it makes them visible to the other threads.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool pred) {
+  static_assert(BYTES == 8 || BYTES == 16, "cp_async_elem: 8 or 16 bytes");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = pred ? BYTES : 0;
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // smem[l][spad(k)] = src[k * ld + line0 + l] for l < TL, k < total / TL (zero past nlines);
-// TL is a power of two
+// TL is a power of two.  Every element is an asynchronous copy, so a thread has all of its
+// loads in flight at once and no registers hold them; the caller synchronises the CTA.
 template <typename C>
 __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ src, int total, int TL, int LS,
                                                 size_t ld, int line0, int nlines) {
-  constexpr int U = sizeof(C) <= 8 ? 8 : 4;
-  const int step = blockDim.x;
   const int logTL = __ffs(TL) - 1;
-#pragma unroll 1
-  for (int idx0 = threadIdx.x; idx0 < total; idx0 += U * step) {
-    C t[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = idx0 + u * step;
-      const int l2 = idx & (TL - 1), k = idx >> logTL;
-      t[u] = (idx < total && line0 + l2 < nlines) ? src[(size_t)k * ld + line0 + l2] : czero<C>();
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = idx0 + u * step;
-      if (idx < total) smem[(size_t)(idx & (TL - 1)) * LS + spad(idx >> logTL)] = t[u];
-    }
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l2 = idx & (TL - 1), k = idx >> logTL;
+    const bool ok = line0 + l2 < nlines;
+    cp_async_elem<(int)sizeof(C)>(&smem[(size_t)l2 * LS + spad(k)], ok ? &src[(size_t)k * ld + line0 + l2] : src, ok);
   }
+  cp_async_wait_all();
 }
 
 template <typename T, int REM>
