@@ -190,7 +190,7 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   for (int r = 0; r < d; ++r) {
     const int ntw = twiddle_entries(p->P[r]);
     if (cudaMalloc(&p->tw64[r], ntw * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&p->tw32[r], p->P[r] * sizeof(float2)) != cudaSuccess)
+        cudaMalloc(&p->tw32[r], ntw * sizeof(float2)) != cudaSuccess)
       return cleanup(FRLAP_ENOMEM, "plan allocation failed");
     cudaError_t e = twiddle_launch(p->P[r], p->tw64[r], p->tw32[r], s);
     if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));

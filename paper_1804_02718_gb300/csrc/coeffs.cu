@@ -297,14 +297,16 @@ __global__ void k_twiddle(int P, double2* tw64, float2* tw32) {
 }
 
 // radix-16 stage entries of the table (layout: twiddle_entries), gathered from its first P
-__global__ void k_twiddle_stage(int P, int logP, double2* tw64) {
+__global__ void k_twiddle_stage(int P, int logP, double2* tw64, float2* tw32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 15 * (P / 8 - 1)) return;
   int logNs = 0;
   while (15 * ((2 << logNs) - 1) <= i) ++logNs;
   const int Ns = 1 << logNs, off = i - 15 * (Ns - 1);
   const int r = off / Ns + 1, k = off % Ns;
-  tw64[P + i] = tw64[(r * k) << (logP - logNs - 4)];
+  const double2 w = tw64[(r * k) << (logP - logNs - 4)];
+  tw64[P + i] = w;
+  if (tw32) tw32[P + i] = make_float2((float)w.x, (float)w.y);
 }
 
 }  // namespace
@@ -351,7 +353,7 @@ cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s) {
   int logP = 0;
   while ((1 << logP) < P) ++logP;
   const int nst = twiddle_entries(P) - P;
-  k_twiddle_stage<<<(nst + 255) / 256, 256, 0, s>>>(P, logP, tw64);
+  k_twiddle_stage<<<(nst + 255) / 256, 256, 0, s>>>(P, logP, tw64, tw32);
   return cudaGetLastError();
 }
 

@@ -141,10 +141,10 @@ struct Plan {
   double* lam64 = nullptr;     // natural order, FP64 (always built)
   double* lamL64 = nullptr;    // line-major, FP64 (always built)
   float* lam32 = nullptr;      // line-major, FP32 (all plans but F64)
-  // exp(-2 pi i m / P_r), m < P_r, followed (tw64, twdf) by the radix-16 stage table of
+  // exp(-2 pi i m / P_r), m < P_r, followed by the radix-16 stage table of
   // twiddle_entries(P_r): see there
   double2* tw64[3] = {nullptr, nullptr, nullptr};
-  float2* tw32[3] = {nullptr, nullptr, nullptr};   // the first P_r entries only
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
   cdf* twdf[3] = {nullptr, nullptr, nullptr};      // the same twiddles as double-floats
   dfl* lamdf = nullptr;        // line-major, as double-floats (DF64 plans)
   bool df64 = false;           // FP64-precision vectors are applied with double-float FFTs
@@ -196,7 +196,7 @@ cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cu
 // entries (one load over a few cache lines instead of one line per lane).  The stage entries
 // are copies of plain entries (W_{16 Ns}^{r k} = W_P^{r k P / (16 Ns)}), so both give the same bits.
 inline int twiddle_entries(int P) { return P + 15 * (P / 8 - 1); }
-// fills tw64 (twiddle_entries(P) entries) and tw32 (P entries, may be null)
+// fills tw64 and tw32 (twiddle_entries(P) entries each; tw32 may be null)
 cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s);
 cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s, cudaStream_t st);
 // dst (line-major, converted to To) = s * oct (natural order); To = double, float or dfl

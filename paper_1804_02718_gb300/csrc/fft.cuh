@@ -178,37 +178,16 @@ __device__ __forceinline__ void dftR(C* v) {
 }
 
 // Twiddles W^r, r = 1..15, W = W_{16 Ns}^k, of one radix-16 butterfly, loaded after the
-// stage barrier.  FP64 and double-float load every power from the table's stage entries
-// (layout: twiddle_entries; products would cost more than the loads there); FP32 loads W,
-// W^4 and W^8 from the plain entries and forms the rest with at most three chained
-// products.  (Issuing these loads before the barrier was measured slower: the extra live
-// registers cost more than the hidden latency.)
+// stage barrier from the table's stage entries (layout: twiddle_entries), so that the 32
+// lanes of a warp read consecutive entries.  (Issuing these loads before the barrier was
+// measured slower: the extra live registers cost more than the hidden latency.)
 template <typename T>
 __device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict__ tw, int k, int logNs,
                                            int logPtab) {
-  if constexpr (!std::is_same<T, float>::value) {
-    const int Ns = 1 << logNs;
-    const cplx<T>* st = tw + (1 << logPtab) + 15 * (Ns - 1) - Ns + k;
+  const int Ns = 1 << logNs;
+  const cplx<T>* st = tw + (1 << logPtab) + 15 * (Ns - 1) - Ns + k;
 #pragma unroll
-    for (int r = 1; r < 16; ++r) w[r] = st[r * Ns];
-  } else {
-    const int sh = logPtab - logNs - 4;
-    w[1] = tw[k << sh];
-    w[4] = tw[(4 * k) << sh];
-    w[8] = tw[(8 * k) << sh];
-    w[2] = cmul(w[1], w[1]);
-    w[3] = cmul(w[2], w[1]);
-    w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[4], w[2]);
-    w[7] = cmul(w[4], w[3]);
-    w[9] = cmul(w[8], w[1]);
-    w[10] = cmul(w[8], w[2]);
-    w[11] = cmul(w[8], w[3]);
-    w[12] = cmul(w[8], w[4]);
-    w[13] = cmul(w[12], w[1]);
-    w[14] = cmul(w[12], w[2]);
-    w[15] = cmul(w[12], w[3]);
-  }
+  for (int r = 1; r < 16; ++r) w[r] = st[r * Ns];
 }
 
 // Barrier between the read and write halves of a stage.  The G = L/16 lanes of a line

@@ -111,6 +111,16 @@ def test_apply_fp32_matches_oracle(frlap, d, Ns, alpha):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("d,Ns,alpha,gamma", [(2, (40, 56), 1.3, 1.7), (3, (12, 10, 14), 0.9, 1.5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-12), (1, 1e-5)])
+def test_apply_gamma_variant_matches_oracle(frlap, d, Ns, alpha, gamma, prec, tol):
+    """The splitting parameter gamma in (alpha, 2) (Sec. 2, the psi_gamma splitting; Figure 3 compares gammas), through the whole apply."""
+    prec = {0: frlap.FRLAP_F64, 3: frlap.FRLAP_DF64, 1: frlap.FRLAP_F32}[prec]
+    u = inp.normal_field(Ns, seed=5)
+    err, *_ = _apply_case(frlap, d, Ns, alpha, u, prec, gamma=gamma)
+    assert err <= tol, err
+
+
 def test_apply_config0_bubble_and_random(frlap):
     """63x63, alpha = 1.5: one apply to N(0,1) and to (1-x^2)(1-y^2), against the dense matrix."""
     Ns, alpha = (64, 64), 1.5
