@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   const int line0 = blockIdx.x * TL;
   const int line = line0 + l;
   const bool valid = line < nlines;
-  const int LS = sline_T(H, TL, (int)sizeof(C));
+  const int LS = sline(H);
   C* buf = smem + (size_t)l * LS;
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int line0 = blockIdx.x * TL;
   const int line = line0 + l;
-  const int LS = sline_T(H, TL, (int)sizeof(C));
+  const int LS = sline(H);
   const int total = TL * (H + 1);
   load_transposed<C>(smem, in, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
   const int line0 = tile * TL;
   const int line = line0 + l;
   const bool valid = line < nlines;
-  const int LS = sline_T(P, TL, (int)sizeof(C));
+  const int LS = sline(P);
   C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
   C v[16];
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
   const int line0 = tile * TL;
   const int line = line0 + l;
   const C* src = in + g * gin;
-  const int LS = sline_T(P, TL, (int)sizeof(C));
+  const int LS = sline(P);
   const int total = TL * P;
   load_transposed<C>(smem, src, total, TL, LS, ldi, line0, nlines);
   __syncthreads();
@@ -567,7 +567,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   {
     const int G = Hx >> 4;
     const int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
-    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
@@ -609,7 +609,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     {
       const int G = Py >> 4;
       const int tl = pick_tl_tuned(tuned[1], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
-      const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
+      const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
@@ -645,7 +645,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     {
       const int G = Py >> 4;
       const int tl = pick_tl_tuned(tuned[3], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
-      const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
+      const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
@@ -664,7 +664,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   {
     const int G = Hx >> 4;
     const int tl = pick_tl_tuned(tuned[p.d == 2 ? 2 : 4], sline(Hx), eb, G, budget, (long long)nrows * B);
-    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
@@ -710,7 +710,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
   {
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
     e = with_rem(p.logP[0] - 1, [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
       cudaError_t e2 = set_smem(k_r2c_T<T, REM>, sm);
@@ -728,7 +728,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
     const int Py = p.P[1];
     const int G = Py >> 4;
     const int tl = pick_tl(sline(Py), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
+    const size_t sm = (size_t)tl * sline(Py) * eb;
     const int tiles = (nz + tl - 1) / tl;
     e = with_rem(p.logP[1], [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
@@ -794,7 +794,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
     const int Py = p.P[1];
     const int G = Py >> 4;
     const int tl = pick_tl(sline(Py), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline_T(Py, tl, eb) * eb;
+    const size_t sm = (size_t)tl * sline(Py) * eb;
     const int tiles = (nz + tl - 1) / tl;
     e = with_rem(p.logP[1], [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
@@ -808,7 +808,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
   {
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline_T(Hx, tl, eb) * eb;
+    const size_t sm = (size_t)tl * sline(Hx) * eb;
     e = with_rem(p.logP[0] - 1, [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
       cudaError_t e2 = set_smem(k_c2r_T<T, REM>, sm);
@@ -852,7 +852,7 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
     int best = 0;
     float best_ms = 0.f;
     for (int t = 1; t <= 64 && e == cudaSuccess; t *= 2) {
-      if (t * G > 512 || (size_t)t * sline_T(L, t, eb) * eb > 227 * 1024) break;
+      if (t * G > 512 || (size_t)t * sline(L) * eb > 227 * 1024) break;
       if (G < 32 && t < 32 / G) continue;
       p.tl_tuned[eng][st] = t;
       float ms = 0.f;

@@ -28,16 +28,7 @@ namespace frlap {
 __host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 // Slots per line for logical indices 0..L (L itself is used by the real-data transforms).
 __host__ __device__ __forceinline__ int sline(int L) { return L + (L >> 4) + 1; }
-// Line stride of the kernels whose CTA reads or writes its TL lines transposed (element k of
-// lines 0..TL-1 at consecutive addresses in global memory): sline(L) plus the smallest pad that
-// makes the stride W/TL modulo W (W = elements per 128-byte shared-memory wavefront), so the TL
-// lines' elements of W/TL consecutive k fall in distinct bank groups.
-__host__ __device__ __forceinline__ int sline_T(int L, int TL, int esize) {
-  const int W = 128 / esize, base = sline(L);
-  if (TL <= 1) return base;
-  const int target = TL >= W ? 1 : W / TL;
-  return base + ((target - base) % W + W) % W;
-}
+
 
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft2(C& a, C& b) {
