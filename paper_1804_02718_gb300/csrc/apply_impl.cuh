@@ -230,10 +230,17 @@ __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int
 }
 
 // lines of length n (contiguous, stride ld) -> zero-pad to P, FFT, * lambda, IFFT, crop, in place
-template <typename T, int REM>
+// LOGP > 0: the line length 2^LOGP is fixed at compile time (the logP / logPtab arguments are
+// ignored), so stage spans, lane counts and shared-memory strides fold into constants.
+template <typename T, int REM, int LOGP = 0>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
                          const int* __restrict__ skip, Batch bt) {
+  static_assert(LOGP == 0 || (LOGP & 3) == REM, "k_colmul: REM = LOGP mod 4");
+  if constexpr (LOGP > 0) {
+    logP = LOGP;
+    logPtab = LOGP;
+  }
   {
     const size_t bi = blockIdx.y;
     data += bi * bt.in;
@@ -500,6 +507,32 @@ cudaError_t with_rem(int logP, F&& f) {
   }
 }
 
+template <int R, int L>
+struct ShapeTag {
+  static constexpr int rem = R;
+  static constexpr int logp = L;
+};
+// k_colmul shapes: FP32 and double-float lines of 2^5 .. 2^13 points run a kernel with the
+// length fixed at compile time; other lengths (and the FP64 engine) the run-time-length one.
+template <typename T, typename F>
+cudaError_t with_line_shape(int logP, F&& f) {
+  if constexpr (!std::is_same<T, double>::value) {
+    switch (logP) {
+      case 5: return f(ShapeTag<1, 5>{});
+      case 6: return f(ShapeTag<2, 6>{});
+      case 7: return f(ShapeTag<3, 7>{});
+      case 8: return f(ShapeTag<0, 8>{});
+      case 9: return f(ShapeTag<1, 9>{});
+      case 10: return f(ShapeTag<2, 10>{});
+      case 11: return f(ShapeTag<3, 11>{});
+      case 12: return f(ShapeTag<0, 12>{});
+      case 13: return f(ShapeTag<1, 13>{});
+      default: break;
+    }
+  }
+  return with_rem(logP, [&](auto t) { return f(ShapeTag<decltype(t)::value, 0>{}); });
+}
+
 }  // namespace
 
 // B instances of the same shape: u, y at stride `vstride` elements, workspace at stride
@@ -595,11 +628,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     const int ncols = Hx + 1;
     const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_rem(logPy, [&](auto tag) {
-      constexpr int REM = decltype(tag)::value;
-      cudaError_t e2 = set_smem(k_colmul<T, REM>, sm);
+    e = with_line_shape<T>(logPy, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LP = decltype(tag)::logp;
+      cudaError_t e2 = set_smem(k_colmul<T, REM, LP>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_colmul<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
+      k_colmul<T, REM, LP><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -632,11 +665,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int ncols = (Hx + 1) * Py;
       const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_rem(logPz, [&](auto tag) {
-      constexpr int REM = decltype(tag)::value;
-      cudaError_t e2 = set_smem(k_colmul<T, REM>, sm);
+    e = with_line_shape<T>(logPz, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LP = decltype(tag)::logp;
+      cudaError_t e2 = set_smem(k_colmul<T, REM, LP>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_colmul<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz, skip, b_ws);
+      k_colmul<T, REM, LP><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz, skip, b_ws);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
