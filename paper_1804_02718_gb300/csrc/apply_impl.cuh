@@ -96,10 +96,15 @@ __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ s
   cp_async_wait_all();
 }
 
-template <typename T, int REM>
+template <typename T, int REM, int LOGL = 0>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
+  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
+  if constexpr (LOGL > 0) {  // transform length fixed at compile time
+    logH = LOGL;
+    logP = LOGL + 1;
+  }
   {
     const size_t bi = blockIdx.y;
     in += bi * bt.in;
@@ -157,10 +162,15 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   }
 }
 
-template <typename T, int REM>
+template <typename T, int REM, int LOGL = 0>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, io_t<T>* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
+  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
+  if constexpr (LOGL > 0) {  // transform length fixed at compile time
+    logH = LOGL;
+    logP = LOGL + 1;
+  }
   {
     const size_t bi = blockIdx.y;
     in += bi * bt.in;
@@ -302,10 +312,15 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
-template <typename T, int REM>
+template <typename T, int REM, int LOGL = 0>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
+  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
+  if constexpr (LOGL > 0) {  // line length fixed at compile time
+    logP = LOGL;
+    logPtab = LOGL;
+  }
   {
     const size_t bi = blockIdx.y;
     in += bi * bt.in;
@@ -346,10 +361,15 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
 }
 
 // transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
-template <typename T, int REM>
+template <typename T, int REM, int LOGL = 0>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
+  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
+  if constexpr (LOGL > 0) {  // line length fixed at compile time
+    logP = LOGL;
+    logPtab = LOGL;
+  }
   {
     const size_t bi = blockIdx.y;
     in += bi * bt.in;
@@ -512,11 +532,13 @@ struct ShapeTag {
   static constexpr int rem = R;
   static constexpr int logp = L;
 };
-// k_colmul shapes: FP32 and double-float lines of 2^5 .. 2^13 points run a kernel with the
-// length fixed at compile time; other lengths (and the FP64 engine) the run-time-length one.
-template <typename T, typename F>
+// Transform shapes of the apply stages: with SPEC, lines of 2^5 .. 2^13 points run a kernel with
+// the length fixed at compile time; other lengths the run-time-length one.  k_colmul is
+// specialised for FP32 and double-float, the other stages for FP32 only (the double-float ones
+// gained too little for the compile time they cost).
+template <typename T, bool SPEC = !std::is_same<T, double>::value, typename F>
 cudaError_t with_line_shape(int logP, F&& f) {
-  if constexpr (!std::is_same<T, double>::value) {
+  if constexpr (SPEC) {
     switch (logP) {
       case 5: return f(ShapeTag<1, 5>{});
       case 6: return f(ShapeTag<2, 6>{});
@@ -604,11 +626,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_rem(logPx - 1, [&](auto tag) {
-      constexpr int REM = decltype(tag)::value;
-      cudaError_t e2 = set_smem(k_r2c_T<T, REM>, sm);
+    e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+      cudaError_t e2 = set_smem(k_r2c_T<T, REM, LL>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_r2c_T<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
+      k_r2c_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -647,11 +669,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_rem(logPy, [&](auto tag) {
-      constexpr int REM = decltype(tag)::value;
-      cudaError_t e2 = set_smem(k_c2cT_fwd<T, REM>, sm);
+    e = with_line_shape<T, std::is_same<T, float>::value>(logPy, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+      cudaError_t e2 = set_smem(k_c2cT_fwd<T, REM, LL>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_c2cT_fwd<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz, nz, logPy, tl, tw[1], logPy, skip, b_ws);
+      k_c2cT_fwd<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny, (size_t)Py * nz, nz, logPy, tl, tw[1], logPy, skip, b_ws);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -683,11 +705,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_rem(logPy, [&](auto tag) {
-      constexpr int REM = decltype(tag)::value;
-      cudaError_t e2 = set_smem(k_c2cT_inv<T, REM>, sm);
+    e = with_line_shape<T, std::is_same<T, float>::value>(logPy, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+      cudaError_t e2 = set_smem(k_c2cT_inv<T, REM, LL>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_c2cT_inv<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny, logPy, tl, tw[1], logPy, skip, b_ws);
+      k_c2cT_inv<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny, logPy, tl, tw[1], logPy, skip, b_ws);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -701,11 +723,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_rem(logPx - 1, [&](auto tag) {
-      constexpr int REM = decltype(tag)::value;
-      cudaError_t e2 = set_smem(k_c2r_T<T, REM>, sm);
+    e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+      cudaError_t e2 = set_smem(k_c2r_T<T, REM, LL>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_c2r_T<T, REM><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
+      k_c2r_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
