@@ -61,8 +61,8 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # DRAM traffic of one batched launch of the dominant kernel, by (dims, kernel, engine) (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu captures summarised under profiles/; absent where the kernel
 # changed since the capture
-MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1286.0e6, (2, "colmul", "f32"): 593.8e6,
-                    (3, "colmul", "df64"): 2460.1e6, (3, "colmul", "f32"): 1193.4e6}
+MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1282.7e6, (2, "colmul", "f32"): 598.3e6,
+                    (3, "colmul", "df64"): 2459.0e6, (3, "colmul", "f32"): 1261.6e6}
 
 # double-float roofline: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the
 # FP32 instructions the kernel's double-float butterflies take per FP64-equivalent flop (flops counted
