@@ -532,14 +532,16 @@ struct ShapeTag {
   static constexpr int rem = R;
   static constexpr int logp = L;
 };
-// Transform shapes of the apply stages: with SPEC, lines of 2^5 .. 2^13 points run a kernel with
-// the length fixed at compile time; other lengths the run-time-length one.  k_colmul is
-// specialised for FP32 and double-float, the other stages for FP32 only (the double-float ones
-// gained too little for the compile time they cost).
+// Transform shapes of the apply stages: with SPEC, every line length the plans allow (2^4 .. 2^13
+// points) runs a kernel with the length fixed at compile time; without, the run-time-length
+// kernel.  k_colmul is specialised for FP32 and double-float, the other stages for FP32 only
+// (the double-float ones are dominated by their arithmetic; their instances would double the
+// compile time).
 template <typename T, bool SPEC = !std::is_same<T, double>::value, typename F>
 cudaError_t with_line_shape(int logP, F&& f) {
   if constexpr (SPEC) {
     switch (logP) {
+      case 4: return f(ShapeTag<0, 4>{});
       case 5: return f(ShapeTag<1, 5>{});
       case 6: return f(ShapeTag<2, 6>{});
       case 7: return f(ShapeTag<3, 7>{});
@@ -549,10 +551,11 @@ cudaError_t with_line_shape(int logP, F&& f) {
       case 11: return f(ShapeTag<3, 11>{});
       case 12: return f(ShapeTag<0, 12>{});
       case 13: return f(ShapeTag<1, 13>{});
-      default: break;
+      default: return cudaErrorInvalidValue;  // plan creation admits no longer line
     }
+  } else {
+    return with_rem(logP, [&](auto t) { return f(ShapeTag<decltype(t)::value, 0>{}); });
   }
-  return with_rem(logP, [&](auto t) { return f(ShapeTag<decltype(t)::value, 0>{}); });
 }
 
 }  // namespace
