@@ -502,7 +502,7 @@ def run_extras(fl, torch, args):
     for name, prec in (("cufft_2047^2_f64", fl.FRLAP_F64), ("cufft_2047^2_f32", fl.FRLAP_F32)):
         out[name] = cufft_compare(fl, torch, prec, 8)
         torch.cuda.empty_cache()
-    # CG: 63^2, f = 1 (configs[0]) and 2047^2 Gaussian-sum f, plain FP64 CG vs FP32-inner refinement
+    # CG: 63^2 with f = 1 and 2047^2 with the Gaussian-sum f, plain FP64 CG vs FP32-inner refinement
     for name, N, f_kind, solver in [("cg_63^2_f1_fp64", 64, "one", fl.FRLAP_SOLVE_CG),
                                     ("cg_2047^2_gauss_fp64", 2048, "gauss", fl.FRLAP_SOLVE_CG),
                                     ("ir_2047^2_gauss_fp32inner", 2048, "gauss", fl.FRLAP_SOLVE_IR)]:
