@@ -1,5 +1,5 @@
 """The oracle reproduces the paper's printed errors: the operator's consistency errors (Tables
-Table1 and Table2 of Sec. 5.1) and the Poisson errors (Tables Tab1 and Tab2 of Sec. 5.2).
+Table1 and Table2 of Sec. 5.1) and the Poisson errors (Tables Tab1, Tab2 and Tab3 of Sec. 5.2).
 
 The paper prepares f with the scheme on the fine mesh h = 2^-12 and reports
 ||u - u_h|| at the coarse nodes.  This test uses h_ref = 2^-9 (N = 1024) for f,
@@ -69,3 +69,33 @@ def test_operator_table(table, alpha):
         tol = (3e-3, 8e-3, 2.5e-2)[k]
         assert einf == pytest.approx(OPERATOR[table]["inf"][key][k], rel=tol), (table, alpha, N)
         assert e2 == pytest.approx(OPERATOR[table]["two"][key][k], rel=tol), (table, alpha, N)
+
+
+POISSON_F1 = json.load(open(os.path.join(HERE, "golden", "paper_poisson_f1_table.json")))
+
+
+def _poisson_f1(alpha, N):
+    """Solution of the discrete problem with f = 1 on h = 2/N (CG with the Strang preconditioner)."""
+    h = 2.0 / N
+    c = scheme.c_d_alpha(2, alpha)
+    a = scheme.coefficients(2, alpha, h, N)
+    shape = (N - 1, N - 1)
+    lam = solvers.strang_symbol(a, c, shape)
+    u, _, rel = solvers.cg(fast.FastOperator(a, c, shape), np.ones(shape), rtol=1e-12,
+                           precond=lambda r: solvers.strang_solve(lam, r))
+    assert rel <= 1e-11
+    return u
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_poisson_f1_table(alpha):
+    """Example 5.2.3 (f = 1, Table Tab3): the printed errors are the differences between the
+    solutions on h and h/2 at the coarse nodes, reproduced here to the table's 4 digits."""
+    key = f"{alpha:.1f}"
+    sols = {N: _poisson_f1(alpha, N) for N in (32, 64, 128, 256)}
+    for k, N in enumerate((32, 64, 128)):
+        h = 2.0 / N
+        e = sols[N] - sols[2 * N][1::2, 1::2]
+        einf, e2 = np.abs(e).max(), np.sqrt(h * h * np.sum(e * e))
+        assert einf == pytest.approx(POISSON_F1["inf"][key][k], rel=2e-3), (alpha, N)
+        assert e2 == pytest.approx(POISSON_F1["two"][key][k], rel=2e-3), (alpha, N)
