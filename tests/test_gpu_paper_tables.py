@@ -1,4 +1,4 @@
-"""The GPU path reproduces the paper's printed Poisson errors (Tables Tab1 and Tab2 of Sec. 5.2).
+"""The GPU path reproduces the paper's printed Poisson errors (Tables Tab1, Tab2 and Tab3 of Sec. 5.2).
 
 Everything here runs through libfrlap: the fine-mesh f (the scheme on N = 4096, h =
 2^-11, double-float apply), the coarse coefficients and the coarse CG solves; only the
@@ -44,3 +44,29 @@ def test_poisson_table_on_gpu(frlap, table, alpha):
         key = f"{alpha:.1f}"
         assert einf == pytest.approx(TABLES[table]["inf"][key][k], rel=TOL[k]), (table, alpha, N, einf)
         assert e2 == pytest.approx(TABLES[table]["two"][key][k], rel=TOL[k]), (table, alpha, N, e2)
+
+
+POISSON_F1 = json.load(open(os.path.join(HERE, "golden", "paper_poisson_f1_table.json")))
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_poisson_f1_table_on_gpu(frlap, alpha):
+    """Table Tab3 (Example 5.2.3, f = 1), all six mesh sizes h = 1/16 .. 1/512: the differences
+    between the GPU solutions on h and h/2 at the coarse nodes match the printed errors to the
+    table's four digits (the printed values are consecutive-mesh differences)."""
+    sols = {}
+    for N in (32, 64, 128, 256, 512, 1024, 2048):
+        plan = frlap.Plan(2, alpha, 2.0 / N, (N, N))
+        frlap.frlap_precond_strang(plan)
+        f = torch.ones(plan.shape, dtype=torch.float64, device="cuda")
+        u, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-12, raise_on_error=False,
+                                                 precond=frlap.FRLAP_PRECOND_STRANG)
+        assert code in (0, 5) and rel <= 1e-11, (N, code, rel)
+        sols[N] = u.cpu().numpy()
+    key = f"{alpha:.1f}"
+    for k, N in enumerate((32, 64, 128, 256, 512, 1024)):
+        h = 2.0 / N
+        e = sols[N] - sols[2 * N][1::2, 1::2]
+        einf, e2 = np.abs(e).max(), np.sqrt(h * h * np.sum(e * e))
+        assert einf == pytest.approx(POISSON_F1["inf"][key][k], rel=2e-3), (alpha, N, einf)
+        assert e2 == pytest.approx(POISSON_F1["two"][key][k], rel=2e-3), (alpha, N, e2)
