@@ -238,7 +238,9 @@ def cpu_oracle_rate(d=2, N=NGRID, alpha=ALPHA, budget_s=15.0, min_applies=1):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    op, Ns = oracle_apply_setup(2, NGRID, ALPHA)
+    D = args.dims
+    NG, AL = (NGRID, ALPHA) if D == 2 else (NGRID_3D, ALPHA_3D)
+    op, Ns = oracle_apply_setup(D, NG, AL)
     u = inp.normal_field(Ns, seed=2)
     M = u.size
     for _ in range(args.warmup):
@@ -251,7 +253,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"2D {NGRID - 1}^2 alpha={ALPHA} FP64 apply, CPU oracle",
+            "data": "synthetic", "config": {"workload": f"{D}D {NG - 1}^{D} alpha={AL} FP64 apply, CPU oracle",
                                              "step": "1 apply", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} NumPy-FFT oracle applies after {args.warmup} warm-up"},
