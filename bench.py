@@ -8,10 +8,13 @@ of the 3D FP64 CG configuration), computed by the double-float FFT engine
 oracle, like native FP64).  One step = one batched apply (frlap_apply_batch, one
 launch per stage) to 8 distinct seeded N(0,1) vectors (268 MB of inputs, more than
 the 129 MB L2).  Reported: apply
-unknowns/s over all ranks, the per-kernel roofline of the dominant kernel, the
-same metric end to end through host buffers, and the CPU oracle timed on the
-host cores.  Extra lines (native FP64 and FP32 applies, 3D 255^3 applies, CG
-solve times) are measured after the timed region.  `--suite solvers` instead runs
+unknowns/s over all ranks, the HBM roofline of the dominant kernel (pass-model bytes
+over its measured duration, against the measured HBM copy rate), the same metric
+end to end through host buffers, and the CPU oracle timed on all host cores.  After
+the timed region: the metric's second half (time to a 1e-10 residual for plain FP64
+CG, Strang and learned PCG and FP32-inner refinement at 2047^2 and 255^3, each with
+its solution error against a tighter reference solve), native FP64, FP32 and 3D
+applies, and cuFFT as a comparison.  `--suite solvers` instead runs
 the solver configurations (time to 1e-10 for plain CG, refinement, Strang and
 learned preconditioning; the batched Allen-Cahn launch) and prints them.
 
@@ -55,55 +58,54 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 pipe: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # DRAM traffic of one batched launch of the dominant kernel, by (dims, kernel, engine) (dram__bytes_read.sum +
-# dram__bytes_write.sum) from the ncu captures summarised under profiles/; absent where the kernel
-# changed since the capture
-MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1282.7e6, (2, "colmul", "f32"): 598.3e6,
-                    (3, "colmul", "df64"): 2459.0e6, (3, "colmul", "f32"): 1261.6e6}
-
-# double-float roofline: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz = 40.3 T instr/s) over the
-# FP32 instructions the kernel's double-float butterflies take per FP64-equivalent flop (flops counted
-# by the usual 5 L log2 L per complex transform).  Instruction costs of the double-float operations:
-# add 11, add without renormalisation 8, multiply 7, complex product feeding a sum (two lazy
-# two-product sums) 32.
-FP32_ISSUE = 152 * 128 * 2.07e9
-DF_DFT4 = 4 * 2 * 8 + 4 * 2 * 11                              # lazy first-level sums, full second level
-DF_DFT16_TAIL = 8 * 32 + 4 * DF_DFT4                          # 8 products by W16^m, four length-4 DFTs
-DF_DFT16 = 4 * DF_DFT4 + DF_DFT16_TAIL
-DF_DFT16_ZIN = 4 * 4 * 2 * 11 + DF_DFT16_TAIL                 # upper half of the input zero
-DF_DFT8_COMBINE = 2 * (2 * 11 + 2 * 7) + 8 * 2 * 11
-DF_DFT8 = 2 * DF_DFT4 + DF_DFT8_COMBINE
-DF_DFT8_ZIN = 8 * 2 * 11 + DF_DFT8_COMBINE
-DF_TW16 = 15 * 32                                             # stage twiddles of a radix-16 butterfly
+# dram__bytes_write.sum) from the ncu captures summarised under profiles/; an entry is dropped when its
+# kernel changes after the capture
+MEASURED_TRAFFIC = {}
 
 
-def df_fft_instr(L, zin):
-    """FP32 instructions of one double-float transform of length L (the engine's stage order)."""
-    n = int(math.log2(L))
-    rem = n % 4
-    if rem == 3:
-        return L // 8 * (DF_DFT8_ZIN if zin else DF_DFT8) + (n - 3) // 4 * L // 16 * (DF_DFT16 + DF_TW16)
-    first = L // 16 * (DF_DFT16_ZIN if zin else DF_DFT16)
-    mid = ((n - rem) // 4 - 1) * L // 16 * (DF_DFT16 + DF_TW16)
-    last = {0: 0, 1: L // 2 * (32 + 2 * 2 * 11), 2: L // 4 * (3 * 32 + DF_DFT4)}[rem]
-    return first + mid + last
+def measure_fp32_fma_tflops(torch):
+    """The FP32 FMA-pipe rate of this GPU, measured: cuBLAS SGEMM (TF32 off, so it runs on the CUDA
+    cores' FMA pipes) of 8192^3, best of 5, 2 n^3 flops each."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = a @ b
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def df64_instr_per_flop(kernel, P):
-    """FP32 instructions per FP64-equivalent flop of one line of `kernel` (P: embedding per axis)."""
-    if kernel == "colmul":
-        L = P[-1]
-        return (df_fft_instr(L, True) + df_fft_instr(L, False) + 14 * L) / (10 * L * math.log2(L) + 2 * L)
-    if kernel in ("c2cT_fwd", "c2cT_inv"):
-        L = P[1]
-        return df_fft_instr(L, kernel == "c2cT_fwd") / (5 * L * math.log2(L))
-    # r2c_T / c2r_T: half-length complex transform and the split of its H + 1 bins (two sums, a
-    # product, a sum: about 104 instructions a bin)
-    H = P[0] // 2
-    return (df_fft_instr(H, kernel == "r2c_T") + 104 * (H + 1)) / (2.5 * P[0] * math.log2(P[0]))
+def cpu_model():
+    """The host CPU's model name (lscpu on Arm hosts, /proc/cpuinfo elsewhere)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -158,15 +160,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def fft_flops_2d(n, P):
-    """Algorithmic flops of one 2D apply, radix-2 convention 5 L log2 L per complex transform of length L
-    (a real transform of length L counts half)."""
-    nx, ny = n
-    Px, Py = P
-    Hx1 = Px // 2 + 1
-    f_rows = ny * 2.5 * Px * math.log2(Px)
-    f_cols = Hx1 * (2 * 5 * Py * math.log2(Py) + 2 * Py)
-    return {"r2c": f_rows, "colmul": f_cols, "c2r": f_rows}
+def pruned_fft_flops(L):
+    """Flops of one complex transform of length L whose input upper half is zero (or whose output upper
+    half is dropped), in the radix-2 count 5 L log2 L: one of its log2 L stages is trivial."""
+    return 5 * L * (math.log2(L) - 1)
+
+
+def row_flops(Px):
+    """One row of the real transform along x: a half-length complex transform (upper half zero), plus
+    the split of its H + 1 output bins (about 6 flops a bin)."""
+    H = Px // 2
+    return pruned_fft_flops(H) + 6 * (H + 1)
+
+
+def colmul_flops(L):
+    """One middle-stage line: forward transform (upper half of the input zero), the real symbol times
+    a complex value (2 flops a point), inverse transform (upper half of the output dropped)."""
+    return 2 * pruned_fft_flops(L) + 2 * L
 
 
 def stage_names(d):
@@ -195,15 +205,19 @@ def stage_bytes(d, n, P, eb):
 
 
 def stage_flops(d, n, P):
+    """Pruned algorithmic flops of each apply stage (the zero padding and the crop skip one radix-2
+    stage of every transform)."""
     if d == 2:
-        f = fft_flops_2d(n, P)
-        return [f["r2c"], f["colmul"], f["c2r"]]
+        nx, ny = n
+        Px, Py = P
+        rows = ny * row_flops(Px)
+        return [rows, (Px // 2 + 1) * colmul_flops(Py), rows]
     nx, ny, nz = n
     Px, Py, Pz = P
     H1 = Px // 2 + 1
-    rows = ny * nz * 2.5 * Px * math.log2(Px)
-    yf = H1 * nz * 5 * Py * math.log2(Py)
-    zc = H1 * Py * (2 * 5 * Pz * math.log2(Pz) + 2 * Pz)
+    rows = ny * nz * row_flops(Px)
+    yf = H1 * nz * pruned_fft_flops(Py)
+    zc = H1 * Py * colmul_flops(Pz)
     return [rows, yf, zc, yf, rows]
 
 
@@ -219,9 +233,11 @@ def oracle_apply_setup(d, N, alpha):
 
 
 def cpu_oracle_rate(d=2, N=NGRID, alpha=ALPHA, budget_s=15.0, min_applies=1):
+    from oracle import fast
     op, Ns = oracle_apply_setup(d, N, alpha)
     u = inp.normal_field(Ns, seed=2)
     M = u.size
+    op(u)  # warm-up (FFT plans, page faults)
     t0 = time.perf_counter()
     count = 0
     while count < min_applies or time.perf_counter() - t0 < budget_s:
@@ -230,14 +246,15 @@ def cpu_oracle_rate(d=2, N=NGRID, alpha=ALPHA, budget_s=15.0, min_applies=1):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": count * M / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{count} FP64 applies of the {N - 1}^{d} alpha={alpha} NumPy-FFT oracle "
-                      f"(circulant embedding, pocketfft single thread) in {dt:.1f} s"}
+    return {"value": count * M / dt, "unit": UNIT, "cores": fast.WORKERS, "cpu": cpu_model(), "kind": "oracle",
+            "sample": f"{count} FP64 applies of the {N - 1}^{d} alpha={alpha} oracle (circulant embedding, "
+                      f"SciPy pocketfft on {fast.WORKERS} threads) in {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    from oracle import fast
     D = args.dims
     NG, AL = (NGRID, ALPHA) if D == 2 else (NGRID_3D, ALPHA_3D)
     op, Ns = oracle_apply_setup(D, NG, AL)
@@ -255,8 +272,10 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{D}D {NG - 1}^{D} alpha={AL} FP64 apply, CPU oracle",
                                              "step": "1 apply", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} NumPy-FFT oracle applies after {args.warmup} warm-up"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": fast.WORKERS, "cpu": cpu_model(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} oracle applies (SciPy pocketfft, {fast.WORKERS} threads) "
+                                       f"after {args.warmup} warm-up"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -323,6 +342,7 @@ def main():
     ap.add_argument("--suite", default="apply", choices=["apply", "solvers"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the PCG half of the metric (profiling runs)")
     ap.add_argument("--dims", type=int, default=2, choices=[2, 3],
                     help="2: the 2047^2 workload (default); 3: 255^3, alpha = 1.0, 2 vectors per step")
     args = ap.parse_args()
@@ -381,29 +401,23 @@ def main():
     sf = stage_flops(D, plan.n, plan.P)
     dom = int(np.argmax(stage_ms))
     hbm, hbm_src = peaks()
-    if args.prec == "f64":
-        ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
-                "flops_per_launch": sf[dom] * BATCH}
-    elif args.prec == "df64":
-        # FFT flops counted as FP64-equivalent operations, each executed as a double-float sequence
-        # on the FP32 pipes; peak = FP32 issue rate / FP32 instructions per FP64-equivalent flop
-        ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
-        ipf = df64_instr_per_flop(names[dom], plan.P)
-        peak = FP32_ISSUE / ipf / 1e12
-        roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s (FP64-equivalent, double-float)", "frac": ach / peak,
-                "traffic": MEASURED_TRAFFIC.get((D, names[dom], args.prec)),
-                "peak_source": f"FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / {ipf:.2f} FP32 instructions "
-                               "per FP64-equivalent flop of this kernel's double-float butterflies",
-                "flops_per_launch": sf[dom] * BATCH}
-    else:
-        ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": MEASURED_TRAFFIC.get((D, names[dom], args.prec)),
-                "peak_source": f"{hbm_src} hbm_gbs", "bytes_per_launch": sb[dom] * BATCH}
+    # HBM roofline of the dominant kernel: its pass-model bytes (what the method must move through
+    # HBM in this stage) over its measured launch duration, against the measured copy bandwidth
+    ach = sb[dom] / (stage_ms[dom] / 1e3) / 1e9
+    roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": MEASURED_TRAFFIC.get((D, names[dom], args.prec)),
+            "peak_source": f"{hbm_src} hbm_gbs (of measured)" if hbm_src == "measured" else "fallback 6800 GB/s",
+            "bytes_per_launch": sb[dom] * BATCH}
+    # the same kernel's pruned algorithmic flops against the measured FP32 FMA rate (cuBLAS SGEMM);
+    # for the double-float engine each counted flop is an FP64-class operation executed as a
+    # sequence of FP32 instructions
+    fp32_peak = measure_fp32_fma_tflops(torch)
+    fl_ach = sf[dom] / (stage_ms[dom] / 1e3) / 1e12
+    roof["pruned_flops_vs_fp32_fma"] = {
+        "flops_per_launch": sf[dom] * BATCH, "achieved_tflops": fl_ach, "fp32_fma_tflops_measured": fp32_peak,
+        "frac": fl_ach / fp32_peak,
+        "note": "FP64-class flops executed as double-float FP32 sequences" if args.prec == "df64" else
+                ("native FP64 flops (FP64 pipe, about 1/62 of FP32)" if args.prec == "f64" else "FP32 flops")}
     roof["instances_per_launch"] = BATCH
     roof["launch_ms"] = stage_ms[dom] * BATCH
     apply_ms = sum(stage_ms)
@@ -438,6 +452,14 @@ def main():
                "h2d_bytes_per_step": BATCH * M * eb, "d2h_bytes_per_step": BATCH * M * eb, "steps": ksteps,
                "call": f"frlap_apply_host (pinned host buffers, chunks of {E2E_CHUNK})"}
 
+    pcg = None
+    if not args.no_pcg and rank == 0:
+        from paper_1804_02718_gb300 import learned
+        params, train_info = train_learned(fl, torch, learned)
+        pcg = {"training": train_info,
+               "2d_2047_alpha1.5": run_pcg_rows(fl, torch, params, 2, 2048, 1.5),
+               "3d_255_alpha1.5": run_pcg_rows(fl, torch, params, 3, 256, 1.5)}
+
     extras = {}
     if not args.no_extras and rank == 0:
         extras = run_extras(fl, torch, args)
@@ -467,6 +489,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "pcg": pcg,
             "extras": extras,
         }
         print(json.dumps(line), flush=True)
@@ -504,25 +527,87 @@ def run_extras(fl, torch, args):
     for name, prec in (("cufft_2047^2_f64", fl.FRLAP_F64), ("cufft_2047^2_f32", fl.FRLAP_F32)):
         out[name] = cufft_compare(fl, torch, prec, 8)
         torch.cuda.empty_cache()
-    # CG: 63^2 with f = 1 and 2047^2 with the Gaussian-sum f, plain FP64 CG vs FP32-inner refinement
-    for name, N, f_kind, solver in [("cg_63^2_f1_fp64", 64, "one", fl.FRLAP_SOLVE_CG),
-                                    ("cg_2047^2_gauss_fp64", 2048, "gauss", fl.FRLAP_SOLVE_CG),
-                                    ("ir_2047^2_gauss_fp32inner", 2048, "gauss", fl.FRLAP_SOLVE_IR)]:
-        h = 2.0 / N
-        prec = fl.FRLAP_MIXED if solver == fl.FRLAP_SOLVE_IR else fl.FRLAP_F64
-        plan = fl.Plan(2, ALPHA, h, (N, N), prec=prec)
-        f = inp.constant_field((N, N)) if f_kind == "one" else inp.gaussian_sum_field((N, N), h, seed=3)
-        ft = torch.from_numpy(f).cuda()
-        x = torch.zeros_like(ft)
-        fl.frlap_pcg_solve(plan, ft, x.clone(), rtol=1e-10, solver=solver, inner_rtol=1e-4, raise_on_error=False)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, it, rel, code = fl.frlap_pcg_solve(plan, ft, x, rtol=1e-10, solver=solver, inner_rtol=1e-4,
-                                              raise_on_error=False)
-        torch.cuda.synchronize()
-        out[name] = {"s": time.perf_counter() - t0, "iters": it, "relres": rel, "status": code}
-        del plan
+    return out
+
+
+def train_learned(fl, torch, learned):
+    """The learned preconditioner's training, outside every timed solve: residual -> A^-1 r pairs from
+    plain FP64 CG trajectories (frlap_cg_pairs) for Gaussian-sum right-hand sides at 8 alphas in
+    [0.5, 1.9] on 255^2 and its coarsening 127^2 (about 20k pairs), then Adam on the A-norm loss
+    (frlap_learn_grad / frlap_adam_step), all in libfrlap's kernels."""
+    t0 = time.perf_counter()
+    alphas = np.linspace(0.5, 1.9, 8)
+    sets = []
+    for N, seeds in ((256, (6, 7, 8, 9, 10, 11)), (128, (6, 7, 8, 9))):
+        for al in alphas:
+            rhs = [inp.gaussian_sum_field((N, N), 2.0 / N, seed=s) for s in seeds]
+            sets.append(learned.PairSet(2, float(al), N, rhs, K=1000))
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    npairs = sum(s.count for s in sets)
+    p0 = learned.init_params(0)
+    L0 = sum(learned.loss_and_grad(s, p0, 0, min(64, s.count))[0].item() for s in sets) / len(sets)
+    t1 = time.perf_counter()
+    params, hist = learned.train(sets, steps=800, batch=8, lr=2e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    L1 = sum(learned.loss_and_grad(s, params, 0, min(64, s.count))[0].item() for s in sets) / len(sets)
+    info = {"pairs": npairs, "pair_generation_s": t_pairs, "adam_steps": 800, "batch": 8, "train_s": t_train,
+            "loss_untrained": L0, "loss_trained": L1,
+            "pairs_from": "plain FP64 CG on 255^2 (6 rhs) and 127^2 (4 rhs), alpha = 0.5..1.9 (8 values)"}
+    for s_ in sets:
+        s_.plan.close()
+    del sets
+    torch.cuda.empty_cache()
+    return params, info
+
+
+def run_pcg_rows(fl, torch, params_trained, d, N, alpha, seed=1):
+    """The metric's second half: time to a true relative residual of 1e-10 on the fractional Poisson
+    problem with a seeded Gaussian-sum f, for plain FP64 CG and the preconditioned / mixed-precision
+    variants; each row also gives its solution error against a tighter reference (native FP64,
+    Strang-preconditioned CG to 1e-11, whose solution error is far below 1e-10 for this f)."""
+    from paper_1804_02718_gb300 import learned
+    h = 2.0 / N
+    Ns = (N,) * d
+    f = torch.from_numpy(inp.gaussian_sum_field(Ns, h, seed=seed)).cuda()
+    F64, DF, MX = fl.FRLAP_F64, fl.FRLAP_DF64, fl.FRLAP_MIXED_DF64
+    CG, IR = fl.FRLAP_SOLVE_CG, fl.FRLAP_SOLVE_IR
+    NONE, STR, LRN = fl.FRLAP_PRECOND_NONE, fl.FRLAP_PRECOND_STRANG, fl.FRLAP_PRECOND_LEARNED
+    ref_plan = fl.Plan(d, alpha, h, Ns, prec=F64)
+    fl.frlap_precond_strang(ref_plan)
+    x_ref, it_ref, rel_ref, code_ref = fl.frlap_pcg_solve(ref_plan, f, rtol=1e-11, precond=STR, raise_on_error=False)
+    del ref_plan
+    xr_norm = torch.linalg.norm(x_ref).item()
+    rows = [("plain_cg_fp64", F64, CG, NONE, None), ("plain_cg_df64", DF, CG, NONE, None),
+            ("pcg_strang_df64", DF, CG, STR, None),
+            ("pcg_learned_untrained_df64", DF, CG, LRN, "untrained"),
+            ("pcg_learned_trained_df64", DF, CG, LRN, "trained"),
+            ("ir_strang_fp32inner", MX, IR, STR, None),
+            ("ir_learned_untrained_fp32inner", MX, IR, LRN, "untrained"),
+            ("ir_learned_trained_fp32inner", MX, IR, LRN, "trained")]
+    out = {"workload": f"{d}D {N - 1}^{d} alpha={alpha} Gaussian-sum f (seed {seed}), rtol 1e-10 (true residual)",
+           "reference": {"iters": it_ref, "relres": rel_ref, "status": code_ref,
+                         "how": "native FP64 plan, Strang PCG to 1e-11"}}
+    for name, prec, solver, pre, which in rows:
+        plan = fl.Plan(d, alpha, h, Ns, prec=prec)
+        fl.frlap_plan_autotune(plan, 1)  # launch shapes (not part of the solve time)
+        if pre == STR:
+            fl.frlap_precond_strang(plan)
+        elif pre == LRN:
+            learned.install(plan, learned.init_params(0) if which == "untrained" else params_trained)
+        plan.workspace(fl.FRLAP_OP_PCG)
+        run = lambda: fl.frlap_pcg_solve(plan, f, rtol=1e-10, solver=solver, precond=pre, inner_rtol=1e-4,
+                                         raise_on_error=False)
+        run()  # warm-up: graph capture, caches
+        dt, (x, it, rel, code) = _timed(run)
+        err = torch.linalg.norm(x - x_ref).item() / xr_norm
+        out[name] = {"s": dt, "iters": it, "relres": rel, "status": code, "sol_err_vs_ref": err}
+        del plan, x
         torch.cuda.empty_cache()
+    base = out["plain_cg_fp64"]["s"]
+    out["speedup_vs_plain_fp64_cg"] = {k: base / v["s"] for k, v in out.items()
+                                       if isinstance(v, dict) and "s" in v and v["s"] > 0}
     return out
 
 

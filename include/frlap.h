@@ -60,6 +60,14 @@ typedef enum {
  * DF64: FP64 vectors in memory, FFT stages in double-float arithmetic (pairs
  * of FP32 numbers, about 48 significant bits), which GB300 runs several times
  * faster than FP64 at an accuracy within the FP64 tolerance of the apply.
+ * Double-float keeps FP32's exponent range: the FFT stages hold values up to
+ * about 3.4e38 (larger ones become infinite) and lose low-order bits below
+ * about 1e-31 (FP32's smallest normal number is 1.2e-38 and the low word sits
+ * 2^-24 below the high one).  A DF64 apply is therefore accurate to the FP64
+ * tolerance for inputs with 1e-25 <~ max|u_i| and lambda_max max|u_i| <~ 1e35;
+ * outside that range use an F64 plan.  frlap_pcg_solve scales the system by
+ * 1/||f|| before its double-float iterations, so its solves have no such limit;
+ * it returns FRLAP_ENAN if the right-hand side itself is not finite.
  * MIXED_DF64: MIXED with the FP64 side computed as in DF64.
  * In frlap_pcg_solve the iterations use the plan's engine, but the residuals
  * f - A x that restart a CG solve or decide convergence (the final check, and
@@ -195,10 +203,14 @@ frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void*
  * FRLAP_NOALLOC_MAX_BYTES, reserved on every GPU that loads the library until
  * the process exits.  The call allocates nothing.
  *  - Limit: plans whose frlap_workspace_bytes(plan, FRLAP_OP_APPLY) exceeds
- *    FRLAP_NOALLOC_MAX_BYTES are rejected with FRLAP_EINVAL and a message
- *    (2D: FP64 grids up to 1024^2 and FP32 up to 2047^2 fit; 3D FP64 up to 63^3).
+ *    FRLAP_NOALLOC_MAX_BYTES are rejected with FRLAP_EINVAL and a message.
+ *    In interior unknowns per axis (n = N - 1) for square and cubic grids:
+ *    2D FP64-class plans (F64, MIXED, DF64, MIXED_DF64) n <= 1024, 2D F32 n <= 2047,
+ *    3D FP64-class n <= 64, 3D F32 n <= 93.
  *  - The first call on a device looks up the array's device address on the
- *    current device; make that first call before any stream capture.
+ *    current device and caches it for the process; make that first call before
+ *    any stream capture.  cudaDeviceReset on a device invalidates the cached
+ *    address: do not call this entry point on that device afterwards.
  *  - All calls on a device share the array: two calls whose GPU work overlaps
  *    (unordered streams) race and give wrong results.  Calls ordered on one
  *    stream are safe; no state carries over from one call to the next. */
@@ -285,10 +297,14 @@ frlap_status frlap_mlp_multiplier(const frlap_plan* plan, const float* d_params,
 /* Scratch for frlap_learn_grad with a batch of B pairs. */
 size_t frlap_learn_workspace_bytes(const frlap_plan* plan, int B);
 
-/* Loss L = mean_b ||M^-1 r_b - e_b||^2 / ||e_b||^2 over B pairs (d_r, d_e: B
- * consecutive grid vectors of doubles, e_b = A^-1 r_b) and its gradient with
- * respect to the parameters: d_grad (FRLAP_MLP_NPARAM floats, overwritten),
- * d_loss (one double on the device).  FP64 spectra, FP32 network. */
+/* Preconditioner loss over B pairs (d_r, d_e: B consecutive grid vectors of
+ * doubles, e_b = A^-1 r_b) and its gradient with respect to the parameters.
+ * With z_b = M^-1 r_b, the loss is the A-norm error left by the best multiple
+ * of z_b (one preconditioned steepest-descent step; PCG is unchanged when M is
+ * scaled, so the loss is scale-free):
+ *   L = mean_b [1 - (r_b.z_b)^2 / ((z_b.A z_b)(r_b.e_b))],  r_b.e_b = ||e_b||_A^2.
+ * d_grad (FRLAP_MLP_NPARAM floats, overwritten), d_loss (one double on the
+ * device).  FP64 spectra, FP32 network. */
 frlap_status frlap_learn_grad(const frlap_plan* plan, const float* d_params, const double* d_r, const double* d_e,
                               int B, float* d_grad, double* d_loss, void* d_work, void* stream);
 

@@ -6,12 +6,18 @@ product but gives no construction; the construction here is the textbook one:
 the symmetric multilevel Toeplitz generator t_k = -c a_|k| (|k_r| <= n_r - 1) is
 placed circulantly in a box of P_r >= 2 n_r - 1 points per axis (zero elsewhere),
 its DFT lambda is real, and A u is the first n_r entries per axis of
-IDFT(lambda * DFT(zero-padded u)).  This module uses NumPy's pocketfft only and is
-checked against scheme.apply_dense in the tests.
+IDFT(lambda * DFT(zero-padded u)).  The DFTs are SciPy's pocketfft on all host
+cores (the library routine serves as the DFT step); the module is checked against
+scheme.apply_dense in the tests.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
+import scipy.fft as sfft
+
+WORKERS = os.cpu_count() or 1
 
 
 def embedding_sizes(shape, P=None):
@@ -40,7 +46,7 @@ def generator(coef: np.ndarray, c: float, shape, P=None) -> np.ndarray:
 
 def symbol(coef: np.ndarray, c: float, shape, P=None) -> np.ndarray:
     """lambda = DFT of the generator (real up to rounding, since t is real and even)."""
-    return np.fft.fftn(generator(coef, c, shape, P)).real
+    return sfft.fftn(generator(coef, c, shape, P), workers=WORKERS).real
 
 
 def apply_fft(coef: np.ndarray, c: float, u: np.ndarray, P=None, lam=None) -> np.ndarray:
@@ -49,8 +55,9 @@ def apply_fft(coef: np.ndarray, c: float, u: np.ndarray, P=None, lam=None) -> np
     P = embedding_sizes(shape, P)
     if lam is None:
         lam = symbol(coef, c, shape, P)
-    U = np.fft.fftn(u, s=P, axes=tuple(range(len(P))))
-    Y = np.fft.ifftn(lam * U)
+    U = sfft.fftn(u, s=P, axes=tuple(range(len(P))), workers=WORKERS)
+    U *= lam
+    Y = sfft.ifftn(U, workers=WORKERS, overwrite_x=True)
     return Y.real[tuple(slice(0, nr) for nr in shape)].copy()
 
 

@@ -21,6 +21,9 @@
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft as sfft
+
+from .fast import WORKERS
 
 
 def cg(apply, f: np.ndarray, x0=None, rtol: float = 1e-10, maxit: int = 100000, precond=None):
@@ -74,12 +77,12 @@ def strang_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
     """
     idx = [np.minimum(np.arange(nr), nr - np.arange(nr)) for nr in shape]
     col = -c * coef[np.ix_(*idx)]
-    return np.fft.fftn(col).real
+    return sfft.fftn(col, workers=WORKERS).real
 
 
 def strang_solve(lam_s: np.ndarray, r: np.ndarray) -> np.ndarray:
     """z = C^-1 r for the Strang circulant with eigenvalues lam_s."""
-    return np.fft.ifftn(np.fft.fftn(r) / lam_s).real
+    return sfft.ifftn(sfft.fftn(r, workers=WORKERS) / lam_s, workers=WORKERS).real
 
 
 def allen_cahn_cn_rhs(apply, ubar: np.ndarray, tau: float, delta: float, alpha: float) -> np.ndarray:

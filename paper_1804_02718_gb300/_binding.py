@@ -207,11 +207,18 @@ def _apply_dtype(plan: Plan):
     return torch.float32 if plan.prec == FRLAP_F32 else torch.float64
 
 
+def _check_vectors(plan, u, y, names=("u", "y")):
+    """Both grid vectors must hold exactly plan.M entries: the C ABI takes raw pointers and cannot
+    check their extent, so a short tensor would be read or written past its end on the GPU."""
+    for t, nm in zip((u, y), names):
+        if t is not None and t.numel() != plan.M:
+            raise ValueError(f"{nm} has {t.numel()} entries, the plan has {plan.M} unknowns")
+
+
 def frlap_apply(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch.Tensor = None, stream=None):
     """y = A u (FFT of the circulant embedding); dtype float64 (F64/MIXED plans) or float32 (F32 plans)."""
     dt = _apply_dtype(plan)
-    if u.numel() != plan.M:
-        raise ValueError(f"u has {u.numel()} entries, the plan has {plan.M} unknowns")
+    _check_vectors(plan, u, y)
     if y is None:
         y = torch.empty_like(u)
     if work is None:
@@ -221,12 +228,14 @@ def frlap_apply(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch
     return y
 
 
-NOALLOC_MAX_BYTES = 32 << 20
+NOALLOC_MAX_BYTES = 32 << 20  # FRLAP_NOALLOC_MAX_BYTES of include/frlap.h (tests/test_abi.py compares them)
 
 
 def frlap_apply_noalloc(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, stream=None):
-    """y = A u with the library's static scratch array (no workspace argument, no allocation in the call)."""
+    """y = A u with the library's static scratch array (no workspace argument, no allocation in the
+    library call; pass y to avoid torch allocating the output)."""
     dt = _apply_dtype(plan)
+    _check_vectors(plan, u, y)
     if y is None:
         y = torch.empty_like(u)
     _check(lib().frlap_apply_noalloc(plan.handle, _dev(u, dt, "u"), _dev(y, dt, "y"), _stream(stream)),
@@ -241,6 +250,7 @@ def frlap_apply_nstages(plan: Plan) -> int:
 def frlap_apply_profiled(plan: Plan, u: torch.Tensor, y: torch.Tensor, work: torch.Tensor, events, stream=None):
     """frlap_apply recording events[i] (torch.cuda.Event, already created) before stage i and after the last."""
     dt = _apply_dtype(plan)
+    _check_vectors(plan, u, y)
     ns = frlap_apply_nstages(plan)
     if len(events) != ns + 1:
         raise ValueError(f"need {ns + 1} events")
@@ -330,6 +340,7 @@ def frlap_plan_autotune(plan: Plan, nbatch: int = 8, stream=None):
 
 
 def frlap_apply_f32(plan: Plan, u: torch.Tensor, y: torch.Tensor = None, work: torch.Tensor = None, stream=None):
+    _check_vectors(plan, u, y)
     if y is None:
         y = torch.empty_like(u)
     if work is None:
@@ -343,6 +354,7 @@ def frlap_pcg_solve(plan: Plan, f: torch.Tensor, x: torch.Tensor = None, rtol: f
                     solver: int = FRLAP_SOLVE_CG, inner_rtol: float = 1e-4, work: torch.Tensor = None,
                     stream=None, raise_on_error: bool = True, precond: int = FRLAP_PRECOND_NONE):
     """Solve A x = f; returns (x, iterations, true relative residual, status code)."""
+    _check_vectors(plan, f, x, ("f", "x"))
     if x is None:
         x = torch.zeros_like(f)
     if work is None:
@@ -366,6 +378,7 @@ def frlap_precond_strang(plan: Plan, stream=None) -> int:
 
 def frlap_precond_apply(plan: Plan, precond: int, r: torch.Tensor, z: torch.Tensor = None, work=None, stream=None):
     """z = M^-1 r (FP32) for the plan's Strang or learned preconditioner."""
+    _check_vectors(plan, r, z, ("r", "z"))
     if z is None:
         z = torch.empty_like(r)
     if work is None:
@@ -436,6 +449,8 @@ def frlap_allen_cahn_batch(plans, us, tau: float, eps: float, nsteps: int, rtol:
     n = len(plans)
     if len(us) != n:
         raise ValueError("one u per plan")
+    for p, u in zip(plans, us):
+        _check_vectors(p, u, None)
     ph = (ctypes.c_void_p * n)(*[p.handle for p in plans])
     uh = (ctypes.c_void_p * n)(*[_dev(u, torch.float64, "u").value for u in us])
     if work is None:
@@ -460,6 +475,7 @@ def frlap_allen_cahn_batch_workspace_bytes(plans) -> int:
 def frlap_allen_cahn_step(plan: Plan, u: torch.Tensor, tau: float, eps: float, nsteps: int = 1,
                           rtol: float = 1e-10, work: torch.Tensor = None, stream=None) -> int:
     """nsteps semi-implicit steps in place on u; returns the total CG iterations."""
+    _check_vectors(plan, u, None)
     if work is None:
         work = plan.workspace(FRLAP_OP_AC)
     it = ctypes.c_int(0)
@@ -473,6 +489,7 @@ def frlap_allen_cahn_cn(plan: Plan, ubar: torch.Tensor, tau: float, delta: float
                         rtol: float = 1e-10, work: torch.Tensor = None, stream=None):
     """Crank-Nicolson steps of the paper's Allen-Cahn model for ubar = u + 1 (in place).
     Returns (total CG iterations, list of the masses h^d sum ubar after each step)."""
+    _check_vectors(plan, ubar, None, ("ubar", None))
     it = ctypes.c_int(0)
     mass = (ctypes.c_double * max(1, int(nsteps)))()
     if work is None:

@@ -26,6 +26,7 @@ frlap_status cuda_fail(cudaError_t e, const char* where) {
 
 size_t cg_work_bytes(const Plan& p, int eb);
 size_t ir_work_bytes(const Plan& p);
+size_t pcg_work_bytes(const Plan& p);
 size_t ac_work_bytes(const Plan& p);
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                             const float* mu, double inner_rtol, int* iters, double* relres, void* work,
@@ -242,8 +243,7 @@ size_t frlap_workspace_bytes(const frlap_plan* plan, int op) {
       return b;
     }
     case FRLAP_OP_PCG:
-      if (plan->prec == FRLAP_MIXED || plan->prec == FRLAP_MIXED_DF64) return ir_work_bytes(*plan);
-      return cg_work_bytes(*plan, eb);
+      return pcg_work_bytes(*plan);
     case FRLAP_OP_AC:
       return ac_work_bytes(*plan);
     default:
@@ -275,7 +275,8 @@ static frlap_status check_work(void* d_work) {
 
 frlap_status frlap_apply(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream) {
   if (!plan || !d_u || !d_y) return fail(FRLAP_EINVAL, "plan, d_u or d_y is NULL");
-  if (d_u == d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  if (ranges_overlap(d_u, d_y, vector_bytes(*plan, plan->prec == FRLAP_F32)))
+    return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
   cudaError_t e;
@@ -463,7 +464,8 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
 frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void* d_y, void* d_work, void* stream,
                                   void* const* events) {
   if (!plan || !d_u || !d_y || !events) return fail(FRLAP_EINVAL, "plan, d_u, d_y or events is NULL");
-  if (d_u == d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  if (ranges_overlap(d_u, d_y, vector_bytes(*plan, plan->prec == FRLAP_F32)))
+    return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
   cudaEvent_t const* ev = reinterpret_cast<cudaEvent_t const*>(events);
@@ -479,7 +481,7 @@ frlap_status frlap_apply_profiled(const frlap_plan* plan, const void* d_u, void*
 frlap_status frlap_apply_f32(const frlap_plan* plan, const float* d_u, float* d_y, void* d_work, void* stream) {
   if (!plan || !d_u || !d_y) return fail(FRLAP_EINVAL, "plan, d_u or d_y is NULL");
   if (plan->prec == FRLAP_F64) return fail(FRLAP_EINVAL, "frlap_apply_f32 needs an F32 or MIXED plan");
-  if ((const void*)d_u == (void*)d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
+  if (ranges_overlap(d_u, d_y, vector_bytes(*plan, true))) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
   cudaError_t e = apply_launch<float>(*plan, d_u, d_y, d_work, (cudaStream_t)stream, nullptr);
@@ -536,7 +538,7 @@ frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* st
 frlap_status frlap_precond_apply(const frlap_plan* plan, int precond, const float* d_r, float* d_z, void* d_work,
                                  void* stream) {
   if (!plan || !d_r || !d_z) return fail(FRLAP_EINVAL, "plan, d_r or d_z is NULL");
-  if ((const void*)d_r == (void*)d_z) return fail(FRLAP_EINVAL, "d_r and d_z must not overlap");
+  if (ranges_overlap(d_r, d_z, vector_bytes(*plan, true))) return fail(FRLAP_EINVAL, "d_r and d_z must not overlap");
   const float* mu = precond == FRLAP_PRECOND_STRANG ? plan->mu_strang
                     : precond == FRLAP_PRECOND_LEARNED ? plan->mu_learned : nullptr;
   if (!mu) return fail(FRLAP_EINVAL, "preconditioner not available on this plan");

@@ -208,6 +208,15 @@ cudaError_t symbol_axes_launch(const Plan& p, double* lam_oct, cudaStream_t s);
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// True if the byte ranges [a, a + bytes) and [b, b + bytes) share any byte.
+inline bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+// Bytes of one grid vector of the plan in the element type of its apply (float for F32 plans,
+// double otherwise).
+inline size_t vector_bytes(const Plan& p, bool f32) { return p.M * (f32 ? sizeof(float) : sizeof(double)); }
+
 }  // namespace frlap
 
 // the opaque handle of the C ABI is the plan itself

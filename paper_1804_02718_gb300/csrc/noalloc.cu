@@ -5,7 +5,10 @@
 // life of the process.  In host code its name is only a host-side stand-in, so
 // the device address is looked up once per device with cudaGetSymbolAddress
 // (with that device current) and cached; the first call on a device does that
-// look-up.  All calls on a device share the one array: calls whose work
+// look-up.  The cached address belongs to the device's current context: after
+// cudaDeviceReset on a device the array is re-created, possibly elsewhere, so this
+// entry point must not be called on that device again in the same process.
+// All calls on a device share the one array: calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on it.
 // Nothing needs clearing between calls: the first apply stage writes every
 // scratch entry that a later stage reads.
@@ -27,8 +30,8 @@ using namespace frlap;
 
 extern "C" frlap_status frlap_apply_noalloc(const frlap_plan* plan, const void* d_u, void* d_y, void* stream) {
   if (!plan || !d_u || !d_y) return fail(FRLAP_EINVAL, "plan, d_u or d_y is NULL");
-  if (d_u == d_y) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
   const bool f32 = plan->prec == FRLAP_F32;
+  if (ranges_overlap(d_u, d_y, vector_bytes(*plan, f32))) return fail(FRLAP_EINVAL, "d_u and d_y must not overlap");
   const size_t need = apply_work_bytes(*plan, f32 ? 4 : 8);
   if (need > (size_t)FRLAP_NOALLOC_MAX_BYTES)
     return fail(FRLAP_EINVAL, "frlap_apply_noalloc: this grid needs " + std::to_string(need) +

@@ -316,6 +316,19 @@ __global__ void k_sum_one_block(const double* __restrict__ x, size_t n, double s
   if (threadIdx.x == 0) *out = scale * t;
 }
 
+// out = sum x^2 over the grid (per-block partials, then the last block in block order)
+__global__ void k_sumsq(const double* __restrict__ x, size_t n, double* partials, unsigned* counter, double* out) {
+  double a = 0.0;
+  GRID_STRIDE(i, n) a += x[i] * x[i];
+  double ta, tb;
+  if (grid_sum2(a, 0.0, partials, counter, &ta, &tb)) *out = ta;
+}
+
+// dst = 2^e src (exact in FP64 away from overflow and subnormals; dst may equal src)
+__global__ void k_scale_pow2(const double* src, double* dst, size_t n, int e) {
+  GRID_STRIDE(i, n) dst[i] = ldexp(src[i], e);
+}
+
 // Allen-Cahn right-hand side u + tau (u - u^3)
 __global__ void k_ac_rhs(const double* __restrict__ u, double* rhs, size_t n, double tau) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -576,9 +589,51 @@ size_t ir_work_bytes(const Plan& p) {
 // CG workspace, two vectors (right-hand side, A ubar) and a slot for the mass of the Crank-Nicolson model
 size_t ac_work_bytes(const Plan& p) { return cg_work_bytes(p, 8) + 2 * vec_bytes(p, 8) + 256; }
 
+// Workspace of frlap_pcg_solve: the CG or refinement workspace, and on double-float plans the
+// scaled right-hand side (one FP64 vector) behind it.
+static size_t pcg_base_bytes(const Plan& p) {
+  if (p.prec == FRLAP_MIXED || p.prec == FRLAP_MIXED_DF64) return ir_work_bytes(p);
+  return cg_work_bytes(p, p.prec == FRLAP_F32 ? 4 : 8);
+}
+size_t pcg_work_bytes(const Plan& p) { return pcg_base_bytes(p) + (p.df64 ? vec_bytes(p, 8) : 0); }
+
+static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
+                                   const float* mu, double inner_rtol, int* iters, double* relres, void* work,
+                                   cudaStream_t st);
+
+// Double-float keeps FP32's exponent range, so on double-float plans the system is solved for
+// 2^-e f with 2^e the power of two at or below the rms of f (and x0 scaled alike), and x is
+// scaled back: every scaling is by a power of two, exact in FP64, so the solve is the same up
+// to the double-float range it now stays inside.
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                             const float* mu, double inner_rtol, int* iters, double* relres, void* work,
                             cudaStream_t st) {
+  if (!p.df64) return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
+  double* fs = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(work) + pcg_base_bytes(p));
+  const CgBufs b = carve(p, work, 8);
+  FRLAP_CUDA_TRY(cudaMemsetAsync(&b.S->counter, 0, sizeof(unsigned), st));
+  k_sumsq<<<vgrid(p.M), kThreads, 0, st>>>(f, p.M, b.partials, &b.S->counter, &b.S->alpha);
+  FRLAP_LAUNCH_CHECK("k_sumsq");
+  double ff = 0.0;
+  FRLAP_CUDA_TRY(cudaMemcpyAsync(&ff, &b.S->alpha, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!isfinite(ff)) return fail(FRLAP_ENAN, "non-finite value in the right-hand side");
+  const int e = ff > 0.0 ? ilogb(sqrt(ff / (double)p.M)) : 0;
+  if (e == 0) return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
+  k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(f, fs, p.M, -e);
+  k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(x, x, p.M, -e);
+  FRLAP_LAUNCH_CHECK("k_scale_pow2");
+  const frlap_status rc = pcg_solve_core(p, fs, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
+  k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(x, x, p.M, e);
+  cudaError_t ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "k_scale_pow2 (solution)");
+  return rc;
+}
+
+static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
+                                   const float* mu, double inner_rtol, int* iters, double* relres, void* work,
+                                   cudaStream_t st) {
   CgState hS;
   if (solver == FRLAP_SOLVE_CG) {
     // CG, then the true residual; if rounding left the true residual above rtol while the

@@ -55,3 +55,36 @@ def test_host_side_argument_checks(built):
     assert L.frlap_apply(None, None, None, None, None) == 1
     assert L.frlap_workspace_bytes(None, 0) == 0
     assert L.frlap_plan_destroy(None) == 0
+
+
+def test_noalloc_limit_matches_header():
+    """The binding's copy of FRLAP_NOALLOC_MAX_BYTES is the header's value."""
+    from paper_1804_02718_gb300 import _binding
+    src = open(os.path.join(ROOT, "include", "frlap.h")).read()
+    m = re.search(r"#define\s+FRLAP_NOALLOC_MAX_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", src)
+    assert m, "FRLAP_NOALLOC_MAX_BYTES not found in the header"
+    assert _binding.NOALLOC_MAX_BYTES == int(m.group(1)) << int(m.group(2))
+
+
+class _FakePlan:
+    """Stands in for a Plan on the host: only the attributes the binding's checks read."""
+
+    def __init__(self, M, prec=0):
+        self.M, self.prec, self.handle = M, prec, None
+
+
+@pytest.mark.parametrize("fn", ["frlap_apply", "frlap_apply_noalloc", "frlap_apply_f32"])
+def test_short_vectors_refused_before_any_launch(fn):
+    """A tensor of the wrong length is refused by the binding before the C call: the library only
+    gets raw pointers and would read or write past the tensor's end on the GPU."""
+    import torch
+    from paper_1804_02718_gb300 import _binding
+    plan = _FakePlan(100, prec=1 if fn == "frlap_apply_f32" else 0)
+    dt = torch.float32 if plan.prec == 1 else torch.float64
+    call = getattr(_binding, fn)
+    with pytest.raises(ValueError, match="u has 99 entries"):
+        call(plan, torch.zeros(99, dtype=dt))
+    with pytest.raises(ValueError, match="y has 50 entries"):
+        call(plan, torch.zeros(100, dtype=dt), torch.zeros(50, dtype=dt))
+    with pytest.raises(ValueError, match="f has 7 entries"):
+        _binding.frlap_pcg_solve(plan, torch.zeros(7, dtype=torch.float64))

@@ -1,43 +1,42 @@
-"""The bench's double-float roofline model (host logic, no GPU).
+"""The bench's roofline model (host logic, no GPU): pass-model bytes and pruned flops per stage.
 
-The peak of a double-float kernel is the FP32 issue rate over the FP32 instructions its butterflies
-take per FP64-equivalent flop.  These checks fix the counts of the smallest transforms by hand, from the
-operation costs (add 11, add without renormalisation 8, multiply 7, lazy complex product 32).
+The HBM roofline divides what each stage must move through HBM (read its input, write its output,
+and for the middle stage read the symbol once) by its measured duration.  These checks fix the counts
+of small cases by hand.
 """
-import math
-
 import bench
 
 
-def test_dft_building_blocks():
-    assert bench.DF_DFT4 == 4 * 2 * 8 + 4 * 2 * 11 == 152
-    assert bench.DF_DFT16 == 8 * 152 + 8 * 32 == 1472
-    assert bench.DF_DFT16_ZIN == 4 * 88 + 4 * 152 + 8 * 32 == 1216
-    assert bench.DF_DFT8 == 2 * 152 + 72 + 176 == 552
-    assert bench.DF_DFT8_ZIN == 176 + 72 + 176 == 424
+def test_stage_bytes_2d_by_hand():
+    # n = (3, 5), P = (8, 16): H1 = 5 row-spectrum bins, S1 holds 5 x 5 complex values
+    eb = 8
+    sb = bench.stage_bytes(2, (3, 5), (8, 16), eb)
+    s1 = 5 * 5 * 2 * eb
+    assert sb[0] == 15 * eb + s1                       # read u, write S1
+    assert sb[1] == 2 * s1 + 5 * 9 * eb                # read + write S1, read the 5 x 9 symbol octant
+    assert sb[2] == s1 + 15 * eb                       # read S1, write y
+    # per unknown at 2047^2 in FP64: the 88 B/unknown pass model
+    sb = bench.stage_bytes(2, (2047, 2047), (4096, 4096), 8)
+    assert abs(sum(sb) / 2047 ** 2 - 88) < 0.2
 
 
-def test_transform_counts_by_hand():
-    # L = 16: one radix-16 butterfly, no stage twiddles
-    assert bench.df_fft_instr(16, False) == 1472
-    assert bench.df_fft_instr(16, True) == 1216
-    # L = 32: two radix-16 butterflies, then 16 radix-2 butterflies with one twiddle product each
-    assert bench.df_fft_instr(32, False) == 2 * 1472 + 16 * (32 + 44)
-    # L = 64: radix-16 then radix-4 (3 twiddle products and one length-4 DFT per butterfly)
-    assert bench.df_fft_instr(64, False) == 4 * 1472 + 16 * (96 + 152)
-    # L = 128: radix-8 first, then one radix-16 stage with 15 stage twiddles per butterfly
-    assert bench.df_fft_instr(128, True) == 16 * 424 + 8 * (1472 + 480)
-    # L = 256: two radix-16 stages
-    assert bench.df_fft_instr(256, False) == 16 * 1472 + 16 * (1472 + 480)
+def test_stage_bytes_3d_by_hand():
+    eb = 4
+    sb = bench.stage_bytes(3, (3, 5, 7), (8, 16, 16), eb)
+    s1 = 5 * 5 * 7 * 2 * eb
+    s2 = 5 * 16 * 7 * 2 * eb
+    lam = 5 * 9 * 9 * eb
+    assert sb == [105 * eb + s1, s1 + s2, 2 * s2 + lam, s2 + s1, s1 + 105 * eb]
+    sb = bench.stage_bytes(3, (255, 255, 255), (512, 512, 512), 8)
+    assert abs(sum(sb) / 255 ** 3 - 217) < 2.0
 
 
-def test_instructions_per_flop_in_range():
-    # a radix-16 butterfly with stage twiddles: 1952 instructions for 5 * 16 * 4 = 320 flops
-    for P in [(4096, 4096), (512, 512, 512), (1024, 2048)]:
-        r = bench.df64_instr_per_flop("colmul", P)
-        assert 5.0 < r < 1952 / 320 + 0.5, (P, r)
-    assert bench.df64_instr_per_flop("colmul", (4096, 4096)) == (
-        bench.df_fft_instr(4096, True) + bench.df_fft_instr(4096, False) + 14 * 4096) / (10 * 4096 * 12 + 2 * 4096)
-    peak = bench.FP32_ISSUE / bench.df64_instr_per_flop("colmul", (4096, 4096)) / 1e12
-    assert 7.0 < peak < 7.6
-    assert math.isclose(bench.FP32_ISSUE, 152 * 128 * 2.07e9)
+def test_pruned_flops_by_hand():
+    # a transform of 16 points with half its input zero: 4 radix-2 stages, one trivial
+    assert bench.pruned_fft_flops(16) == 5 * 16 * 3
+    # a row of P_x = 32 real points: a half-length (16-point) pruned transform and 17 split bins
+    assert bench.row_flops(32) == 5 * 16 * 3 + 6 * 17
+    # a middle-stage line of 16 points: two pruned transforms and the symbol product
+    assert bench.colmul_flops(16) == 2 * 240 + 32
+    f = bench.stage_flops(2, (15, 15), (32, 16))
+    assert f == [15 * bench.row_flops(32), 17 * bench.colmul_flops(16), 15 * bench.row_flops(32)]

@@ -58,3 +58,31 @@ def test_allen_cahn_batch_reports_maxit(frlap):
     u2 = torch.from_numpy(inp.uniform_field((N, N), seed=3)).cuda()
     iters, status, code = frlap.frlap_allen_cahn_batch([plan], [u2], 1e-3, 0.05, 2, rtol=1e-10)
     assert code == 0
+
+
+def test_allen_cahn_batch_double_float_at_benchmark_grids(frlap):
+    """The double-float batched launch the solver suite times: DF64 plans at 255^2, 511^2 and 1023^2
+    with mixed alphas, 3 steps in one launch; every instance element by element against the oracle's
+    semi-implicit steps (CG to 1e-13) within 1e-10."""
+    tau, eps, nsteps = 1e-3, 0.05, 3
+    specs = [(256, 1.35), (512, 1.9), (1024, 1.6), (256, 1.8)]
+    plans, us, refs = [], [], []
+    for k, (N, alpha) in enumerate(specs):
+        h = 2.0 / N
+        a, c = scheme.coefficients(2, alpha, h, N), scheme.c_d_alpha(2, alpha)
+        u0 = inp.uniform_field((N, N), seed=5 + k)
+        op = fast.FastOperator(a, c, u0.shape)
+        u = u0.copy()
+        for _ in range(nsteps):
+            u, _, _ = solvers.allen_cahn_step(op, u, tau, eps, rtol=1e-13)
+        refs.append(u)
+        plans.append(frlap.Plan(2, alpha, h, (N, N), prec=frlap.FRLAP_DF64))
+        us.append(torch.from_numpy(u0).cuda())
+    frlap.frlap_plan_autotune(plans[0], 2)  # tuned launch shapes, as in the suite
+    iters, status, code = frlap.frlap_allen_cahn_batch(plans, us, tau, eps, nsteps, rtol=1e-12, maxit=500)
+    assert code == 0 and all(s == 0 for s in status)
+    for u, ref, (N, alpha) in zip(us, refs, specs):
+        diff = np.abs(u.cpu().numpy() - ref).max()
+        print(f"DF64 batch {N - 1}^2 alpha {alpha}: max |u - u_oracle| = {diff:.2e}")
+        assert diff <= 1e-10
+        assert np.abs(u.cpu().numpy()).max() <= 1.0

@@ -148,3 +148,27 @@ def test_allen_cahn_cn_matches_oracle(frlap, d, N, prec):
     assert np.abs(ub.cpu().numpy() - ref).max() <= 1e-10
     np.testing.assert_allclose(m, masses, rtol=1e-11)
     assert m[-1] < solvers.bubble_mass(ub0, h)  # the bubbles shrink
+
+
+@pytest.mark.parametrize("scale", [1e200, 1e-200])
+@pytest.mark.parametrize("prec,solver", [(3, 0), (4, 1)])
+def test_double_float_solve_outside_fp32_range(frlap, scale, prec, solver):
+    """Double-float keeps FP32's exponent range, so the solver scales the system by a power of two
+    before its double-float iterations: a right-hand side far outside FP32's range (1e200, 1e-200)
+    gives the scaled solution of the native FP64 solve."""
+    N, alpha = 128, 1.5
+    h = 2.0 / N
+    f = inp.gaussian_sum_field((N, N), h, seed=4)
+    p64 = frlap.Plan(2, alpha, h, (N, N), prec=frlap.FRLAP_F64)
+    x64, _, _, code64 = frlap.frlap_pcg_solve(p64, _t(f), rtol=1e-12)
+    assert code64 == 0
+    plan = frlap.Plan(2, alpha, h, (N, N), prec=prec)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f * scale), rtol=1e-12, solver=solver, inner_rtol=1e-4)
+    assert code == 0 and rel <= 1e-12
+    xs = x / scale
+    assert torch.isfinite(xs).all()
+    assert (torch.linalg.norm(xs - x64) / torch.linalg.norm(x64)).item() <= 1e-10
+    fbad = f.copy()
+    fbad[5, 5] = np.inf
+    _, _, _, code = frlap.frlap_pcg_solve(plan, _t(fbad), rtol=1e-10, solver=solver, raise_on_error=False)
+    assert code == 7  # FRLAP_ENAN, refused before any double-float iteration
