@@ -532,29 +532,42 @@ def run_extras(fl, torch, args):
 
 def train_learned(fl, torch, learned):
     """The learned preconditioner's training, outside every timed solve: residual -> A^-1 r pairs from
-    plain FP64 CG trajectories (frlap_cg_pairs) for Gaussian-sum right-hand sides at 8 alphas in
-    [0.5, 1.9] on 255^2 and its coarsening 127^2 (about 20k pairs), then Adam on the A-norm loss
-    (frlap_learn_grad / frlap_adam_step), all in libfrlap's kernels."""
+    plain FP64 CG trajectories (frlap_cg_pairs) at 8 alphas in [0.5, 1.9]: 2D on 255^2 and its
+    coarsening 127^2 (Gaussian-sum and N(0,1) right-hand sides), 3D on 63^3 and 31^3, about 25k pairs;
+    then Adam on the relative A-norm loss (frlap_learn_grad / frlap_adam_step), with the plain
+    solver as the judge: PCG iterations on held-out problems pick the parameters kept (the untrained
+    network included).  All in libfrlap's kernels."""
     t0 = time.perf_counter()
     alphas = np.linspace(0.5, 1.9, 8)
     sets = []
-    for N, seeds in ((256, (6, 7, 8, 9, 10, 11)), (128, (6, 7, 8, 9))):
+    for d, N, gseeds, nseeds in ((2, 256, (6, 7, 8, 9, 10, 11), ()), (2, 128, (6, 7), (8, 9)),
+                                 (3, 64, (6, 7), ()), (3, 32, (6,), (8,))):
         for al in alphas:
-            rhs = [inp.gaussian_sum_field((N, N), 2.0 / N, seed=s) for s in seeds]
-            sets.append(learned.PairSet(2, float(al), N, rhs, K=1000))
+            Ns = (N,) * d
+            rhs = [inp.gaussian_sum_field(Ns, 2.0 / N, seed=s) for s in gseeds] + \
+                  [inp.normal_field(Ns, seed=s) for s in nseeds]
+            sets.append(learned.PairSet(d, float(al), N, rhs, K=1000))
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
     npairs = sum(s.count for s in sets)
+    judge = learned.Judge([(2, al, 256, inp.gaussian_sum_field((256, 256), 2.0 / 256, seed=20 + k))
+                           for k, al in enumerate((0.7, 1.3, 1.9))] +
+                          [(3, 1.5, 64, inp.gaussian_sum_field((64, 64, 64), 2.0 / 64, seed=23))])
     p0 = learned.init_params(0)
     L0 = sum(learned.loss_and_grad(s, p0, 0, min(64, s.count))[0].item() for s in sets) / len(sets)
     t1 = time.perf_counter()
-    params, hist = learned.train(sets, steps=800, batch=8, lr=2e-3, seed=0)
+    params, hist, scores = learned.train(sets, steps=800, batch=8, lr=2e-3, seed=0, judge=judge, eval_every=50)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     L1 = sum(learned.loss_and_grad(s, params, 0, min(64, s.count))[0].item() for s in sets) / len(sets)
+    kept = min(scores, key=lambda t: (t[1], t[0]))
     info = {"pairs": npairs, "pair_generation_s": t_pairs, "adam_steps": 800, "batch": 8, "train_s": t_train,
-            "loss_untrained": L0, "loss_trained": L1,
-            "pairs_from": "plain FP64 CG on 255^2 (6 rhs) and 127^2 (4 rhs), alpha = 0.5..1.9 (8 values)"}
+            "loss_untrained": L0, "loss_kept": L1, "judge_iterations": scores, "kept_step": kept[0],
+            "pairs_from": "plain FP64 CG, alpha = 0.5..1.9 (8 values): 255^2 (6 Gaussian-sum rhs), 127^2 "
+                          "(2 Gaussian-sum, 2 N(0,1)), 63^3 (2 Gaussian-sum), 31^3 (1 + 1)",
+            "judge": "PCG iterations to 1e-10 on held-out 255^2 (alpha 0.7, 1.3, 1.9) and 63^3 (alpha 1.5) "
+                     "problems; step 0 is the untrained network"}
+    judge.close()
     for s_ in sets:
         s_.plan.close()
     del sets

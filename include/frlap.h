@@ -65,9 +65,10 @@ typedef enum {
  * about 1e-31 (FP32's smallest normal number is 1.2e-38 and the low word sits
  * 2^-24 below the high one).  A DF64 apply is therefore accurate to the FP64
  * tolerance for inputs with 1e-25 <~ max|u_i| and lambda_max max|u_i| <~ 1e35;
- * outside that range use an F64 plan.  frlap_pcg_solve scales the system by
- * 1/||f|| before its double-float iterations, so its solves have no such limit;
- * it returns FRLAP_ENAN if the right-hand side itself is not finite.
+ * outside that range use an F64 plan.  frlap_pcg_solve scales the system by the
+ * power of two at or below 1/max|f_i| before its double-float iterations (an
+ * exact scaling, undone on the solution), so its solves have no such limit; it
+ * returns FRLAP_ENAN if the right-hand side itself is not finite.
  * MIXED_DF64: MIXED with the FP64 side computed as in DF64.
  * In frlap_pcg_solve the iterations use the plan's engine, but the residuals
  * f - A x that restart a CG solve or decide convergence (the final check, and

@@ -14,12 +14,11 @@ multiplier is m(k) = exp(s(k)) / lambda(k), with lambda the real symbol of A's
 circulant embedding, so a zero network gives the inverse-embedding preconditioner.
 M^-1 r = R F^-1 (m . F R^T r) (R: restriction to the interior grid, F: the
 P-point DFT).  Training pairs (r_b, e_b = A^-1 r_b) come from the plain CG
-solver.  Because PCG is unchanged when M is scaled, the loss measures the error of
-the best multiple of z_b = M^-1 r_b in the A-norm:
-  L_b = min_c ||e_b - c z_b||_A^2 / ||e_b||_A^2 = 1 - a_b^2 / (b_b c_b),
+solver.  The loss is the relative A-norm error of z_b = M^-1 r_b as an
+approximation of e_b:
+  L_b = ||e_b - z_b||_A^2 / ||e_b||_A^2 = 1 - 2 a_b / c_b + b_b / c_b,
   a_b = r_b . z_b,  b_b = z_b . A z_b,  c_b = r_b . e_b (= ||e_b||_A^2),
-and L = mean_b L_b (the error reduction of one preconditioned steepest-descent step).
-With R^ = F R^T r, W^ = F R^T (A z) and prod(P) the DFT size,
+and L = mean_b L_b.  With R^ = F R^T r, W^ = F R^T (A z) and prod(P) the DFT size,
   d a_b / d m(k) = |R^(k)|^2 / prod(P),   d b_b / d m(k) = 2 Re(conj(W^(k)) R^(k)) / prod(P),
 summed over the mirror images of each octant entry.
 """
@@ -139,11 +138,11 @@ def loss_and_grad(theta, alpha, lam_oct, P, rs, es, apply_A):
         z = np.fft.ifftn(mfull * R, axes=axes).real[tuple(slice(0, n) for n in r.shape)]
         w = apply_A(z)
         a, b, c = float(np.sum(r * z)), float(np.sum(z * w)), float(np.sum(r * e))
-        L += (1.0 - a * a / (b * c)) / B
+        L += (1.0 - 2.0 * a / c + b / c) / B
         W = np.fft.fftn(w, s=Pa, axes=axes)
         da = np.abs(R) ** 2 / PP
         db = 2.0 * np.real(np.conj(W) * R) / PP
-        gfull += (-(2.0 * a / (b * c)) * da + (a * a / (b * b * c)) * db) / B
+        gfull += (-(2.0 / c) * da + (1.0 / c) * db) / B
     g_m = _fold(gfull, P)
     g_s = (g_m * m).reshape(-1)
     return L, mlp_backward(theta, cache, g_s)

@@ -316,12 +316,23 @@ __global__ void k_sum_one_block(const double* __restrict__ x, size_t n, double s
   if (threadIdx.x == 0) *out = scale * t;
 }
 
-// out = sum x^2 over the grid (per-block partials, then the last block in block order)
-__global__ void k_sumsq(const double* __restrict__ x, size_t n, double* partials, unsigned* counter, double* out) {
-  double a = 0.0;
-  GRID_STRIDE(i, n) a += x[i] * x[i];
-  double ta, tb;
-  if (grid_sum2(a, 0.0, partials, counter, &ta, &tb)) *out = ta;
+// *out = max_i |x_i| as the bit pattern of a non-negative double (whose unsigned order is the
+// numeric order), or the pattern of a quiet NaN if any x_i is not finite; *out must start at 0.
+// No squares are formed, so no value of x can overflow it.
+__global__ void k_maxabs(const double* __restrict__ x, size_t n, unsigned long long* out) {
+  double m = 0.0;
+  bool bad = false;
+  GRID_STRIDE(i, n) {
+    const double v = fabs(x[i]);
+    bad |= !isfinite(v);
+    m = v > m ? v : m;
+  }
+  unsigned long long b = bad ? 0x7ff8000000000000ull : (unsigned long long)__double_as_longlong(m);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_down_sync(0xffffffffu, b, o);
+    b = t > b ? t : b;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, b);
 }
 
 // dst = 2^e src (exact in FP64 away from overflow and subnormals; dst may equal src)
@@ -602,7 +613,7 @@ static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, do
                                    cudaStream_t st);
 
 // Double-float keeps FP32's exponent range, so on double-float plans the system is solved for
-// 2^-e f with 2^e the power of two at or below the rms of f (and x0 scaled alike), and x is
+// 2^-e f with 2^e the power of two at or below max |f_i| (and x0 scaled alike), and x is
 // scaled back: every scaling is by a power of two, exact in FP64, so the solve is the same up
 // to the double-float range it now stays inside.
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
@@ -611,14 +622,17 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
   if (!p.df64) return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
   double* fs = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(work) + pcg_base_bytes(p));
   const CgBufs b = carve(p, work, 8);
-  FRLAP_CUDA_TRY(cudaMemsetAsync(&b.S->counter, 0, sizeof(unsigned), st));
-  k_sumsq<<<vgrid(p.M), kThreads, 0, st>>>(f, p.M, b.partials, &b.S->counter, &b.S->alpha);
-  FRLAP_LAUNCH_CHECK("k_sumsq");
-  double ff = 0.0;
-  FRLAP_CUDA_TRY(cudaMemcpyAsync(&ff, &b.S->alpha, sizeof(double), cudaMemcpyDeviceToHost, st));
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(&b.S->alpha);
+  FRLAP_CUDA_TRY(cudaMemsetAsync(slot, 0, sizeof(unsigned long long), st));
+  k_maxabs<<<vgrid(p.M), kThreads, 0, st>>>(f, p.M, slot);
+  FRLAP_LAUNCH_CHECK("k_maxabs");
+  unsigned long long bits = 0;
+  FRLAP_CUDA_TRY(cudaMemcpyAsync(&bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, st));
   FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
-  if (!isfinite(ff)) return fail(FRLAP_ENAN, "non-finite value in the right-hand side");
-  const int e = ff > 0.0 ? ilogb(sqrt(ff / (double)p.M)) : 0;
+  double fmax = 0.0;
+  memcpy(&fmax, &bits, sizeof(fmax));
+  if (!isfinite(fmax)) return fail(FRLAP_ENAN, "non-finite value in the right-hand side");
+  const int e = fmax > 0.0 ? ilogb(fmax) : 0;
   if (e == 0) return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
   k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(f, fs, p.M, -e);
   k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(x, x, p.M, -e);

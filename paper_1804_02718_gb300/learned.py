@@ -1,9 +1,10 @@
 """Training and installation of the learned Fourier-multiplier preconditioner.
 
 Orchestration only: pair generation (frlap_cg_pairs), the loss and its gradient
-(frlap_learn_grad), the optimiser (frlap_adam_step) and inference
-(frlap_mlp_multiplier) all run in libfrlap's kernels; this module picks batches
-and keeps the loop going.  Model and loss are described in include/frlap.h.
+(frlap_learn_grad), the optimiser (frlap_adam_step), inference
+(frlap_mlp_multiplier) and the judge's solves (frlap_pcg_solve) all run in
+libfrlap's kernels; this module picks batches, keeps the loop going and keeps the
+parameters the judge scores best.  Model and loss are described in include/frlap.h.
 """
 from __future__ import annotations
 
@@ -60,13 +61,51 @@ def loss_and_grad(pset: PairSet, params: torch.Tensor, start: int, batch: int):
     return loss, grad
 
 
-def train(sets, steps: int = 300, batch: int = 8, lr: float = 2e-3, seed: int = 0, params: torch.Tensor = None):
-    """Adam on the A-norm preconditioner loss; minibatches are contiguous windows of one set's pairs."""
+class Judge:
+    """The plain solver as the judge: scores parameters by the flexible-PCG iterations their
+    multiplier needs to reach rtol on held-out problems (operators and right-hand sides not in the
+    training pairs); lower is better, a failed solve scores 10^6."""
+
+    def __init__(self, problems, rtol: float = 1e-10):
+        self.rtol = rtol
+        self.items = []
+        for d, alpha, N, f in problems:
+            plan = B.Plan(d, alpha, 2.0 / N, (N,) * d)
+            self.items.append((plan, torch.from_numpy(np.ascontiguousarray(f)).cuda()))
+
+    def __call__(self, params: torch.Tensor) -> int:
+        total = 0
+        for plan, f in self.items:
+            install(plan, params)
+            _, it, _, code = B.frlap_pcg_solve(plan, f, rtol=self.rtol, precond=B.FRLAP_PRECOND_LEARNED,
+                                               raise_on_error=False)
+            total += it if code == 0 else 10 ** 6
+        return total
+
+    def close(self):
+        for plan, _ in self.items:
+            plan.close()
+        self.items = []
+
+
+def train(sets, steps: int = 300, batch: int = 8, lr: float = 2e-3, seed: int = 0, params: torch.Tensor = None,
+          judge: Judge = None, eval_every: int = 50):
+    """Adam on the relative A-norm loss; minibatches are contiguous windows of one set's pairs.
+    With a judge, the parameters are scored before training and every eval_every steps, and the
+    best-scoring ones are returned (the starting point wins ties, so training never returns a
+    preconditioner the judge rates worse than the one it started from).
+    Returns (params, loss history, judge scores as (step, score))."""
     rng = np.random.default_rng(seed)
     params = init_params(seed) if params is None else params.clone()
     m1 = torch.zeros_like(params)
     m2 = torch.zeros_like(params)
     history = []
+    scores = []
+    best = None
+    if judge is not None:
+        sc = judge(params)
+        scores.append((0, sc))
+        best = (sc, params.clone())
     for t in range(1, steps + 1):
         s = sets[int(rng.integers(len(sets)))]
         b = min(batch, s.count)
@@ -74,7 +113,13 @@ def train(sets, steps: int = 300, batch: int = 8, lr: float = 2e-3, seed: int = 
         loss, grad = loss_and_grad(s, params, start, b)
         B.frlap_adam_step(params, grad, m1, m2, lr, t)
         history.append(loss)
-    return params, [float(v.item()) for v in history]
+        if judge is not None and (t % eval_every == 0 or t == steps):
+            sc = judge(params)
+            scores.append((t, sc))
+            if sc < best[0]:
+                best = (sc, params.clone())
+    out = best[1] if best is not None else params
+    return out, [float(v.item()) for v in history], scores
 
 
 def install(plan, params: torch.Tensor) -> torch.Tensor:
