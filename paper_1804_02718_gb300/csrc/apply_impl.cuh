@@ -81,23 +81,47 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool p
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // smem[l][spad(k)] = src[k * ld + line0 + l] for l < TL, k < total / TL (zero past nlines);
-// TL is a power of two.  Every element is an asynchronous copy, so a thread has all of its
-// loads in flight at once and no registers hold them; the caller synchronises the CTA.
+// TL is a power of two dividing blockDim.x.  Thread t serves line t mod TL and rows
+// k = t / TL + j (blockDim.x / TL), walking its source column with a pointer increment.  Every
+// element is an asynchronous copy, so a thread has all of its loads in flight at once and no
+// registers hold them; the caller synchronises the CTA.
 template <typename C>
 __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ src, int total, int TL, int LS,
                                                 size_t ld, int line0, int nlines) {
   const int logTL = __ffs(TL) - 1;
+  const int lt = threadIdx.x & (TL - 1);
+  const int kstep = (int)blockDim.x >> logTL;
+  const int kend = total >> logTL;
+  const bool ok = line0 + lt < nlines;
+  C* row = smem + (size_t)lt * LS;
+  int k = (int)threadIdx.x >> logTL;
+  const C* gp = src + (size_t)k * ld + line0 + lt;
+  const size_t gstep = (size_t)kstep * ld;
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx & (TL - 1), k = idx >> logTL;
-    const bool ok = line0 + l2 < nlines;
-    cp_async_elem<(int)sizeof(C)>(&smem[(size_t)l2 * LS + spad(k)], ok ? &src[(size_t)k * ld + line0 + l2] : src, ok);
-  }
+  for (; k < kend; k += kstep, gp += gstep) cp_async_elem<(int)sizeof(C)>(&row[spad(k)], ok ? gp : src, ok);
   cp_async_wait_all();
 }
 
+// Threads per CTA the apply kernels are compiled for.  FP32 kernels fit 64 registers a thread,
+// so 1024-thread CTAs cost them no registers and let the transposed stages hold twice as many
+// lines per CTA; the FP64 and double-float kernels need 128 registers (512 threads).
+template <typename T>
+constexpr int kMaxCta = std::is_same<T, float>::value ? 1024 : 512;
+
+// The real-data split of the first and last stages: computed per output element inside the
+// transposed store / the transform's register load (one complex product per element, no
+// shared-memory write-back), or in place per pair of bins (one product per pair, one more pass
+// over shared memory).  Per stage and engine, the faster measured form: the per-element form in
+// the forward stage of FP32 and double-float and in the inverse stage of FP32 (2047^2:
+// double-float r2c 99 -> 95 us, FP32 c2r 24 -> 22 us); the per-pair form where the extra
+// products cost more than the pass (native FP64; the double-float inverse, 75 against 86 us).
+template <typename T>
+constexpr bool kFusedSplitR2C = !std::is_same<T, double>::value;
+template <typename T>
+constexpr bool kFusedSplitC2R = std::is_same<T, float>::value;
+
 template <typename T, int REM, int LOGL = 0>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
   static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
@@ -125,14 +149,23 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
   // for q >= H/2 (m >= 8): the upper half of the transform input.
+  // A row that starts on a pair boundary is read one pair (x[2q], x[2q+1]) per load.
+  using IO2 = io_pair<T>;
+  const bool pair_aligned = (reinterpret_cast<uintptr_t>(src) % sizeof(IO2)) == 0;
   C v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
     const int q = lane + m * G;
     io_t<T> re = io_t<T>(0), im = io_t<T>(0);
     if (m < 8 && valid) {
-      if (2 * q < n) re = src[2 * q];
-      if (2 * q + 1 < n) im = src[2 * q + 1];
+      if (pair_aligned && 2 * q + 1 < n) {
+        const IO2 t = *reinterpret_cast<const IO2*>(src + 2 * q);
+        re = t.x;
+        im = t.y;
+      } else {
+        if (2 * q < n) re = src[2 * q];
+        if (2 * q + 1 < n) im = src[2 * q + 1];
+      }
     }
     v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
   }
@@ -140,30 +173,55 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_r2c_T(const io_
   line_sync<T>(logH);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
-  line_sync<T>(logH);
-  // unpack the half-length transform Z of the packed samples into X[k], k = 0..H:
-  // with a = Z[k], b = conj Z[H-k], E = (a + b)/2 and O = -i (a - b)/2,
-  // X[k] = E + W^k O and X[H-k] = conj(E - W^k O)  (W = exp(-2 pi i / 2H); one product per pair)
-  for (int k = lane; k <= H / 2; k += G) {
-    const int km = H - k;
-    const C a = buf[spad(k)];
-    const C b = conjg(buf[spad(km & (H - 1))]);
-    const C e = halve(a + b);
-    const C t = cmul(tw[k], halve(mul_i<-1>(a - b)));
-    buf[spad(k)] = e + t;
-    if (k != km) buf[spad(km)] = conjg(e - t);
-  }
-  __syncthreads();
+  // The half-length transform Z of the packed samples gives X[k], k = 0..H, by the real-data
+  // split: with a = Z[k mod H], b = conj Z[(H-k) mod H], E = (a + b)/2 and O = -i (a - b)/2,
+  // X[k] = E + W^k O (W = exp(-2 pi i / 2H)).
   const int total = TL * (H + 1);
   const int logTL = __ffs(TL) - 1;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx & (TL - 1), k = idx >> logTL;
-    if (line0 + l2 < nlines) out[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * LS + spad(k)];
+  // Transposed store: thread t serves line t mod TL of the tile and bins k = t / TL + j G of it
+  // (TL G threads), walking its output column with a pointer increment.
+  const int lt = threadIdx.x & (TL - 1);
+  const bool lt_ok = line0 + lt < nlines;
+  const C* trow = smem + (size_t)lt * LS;
+  const size_t gstep = (size_t)G * ldo;
+  if constexpr (kFusedSplitR2C<T>) {
+    // each output of the transposed store computes its own X[k] from the two bins it needs
+    // (one product per output, no write-back pass over shared memory)
+    __syncthreads();
+    if (lt_ok) {
+      int k = (int)threadIdx.x >> logTL;
+      C* gp = out + (size_t)k * ldo + line0 + lt;
+#pragma unroll 4
+      for (; k <= H; k += G, gp += gstep) {
+        const C a = trow[spad(k & (H - 1))];
+        const C b = conjg(trow[spad((H - k) & (H - 1))]);
+        *gp = halve(a + b) + cmul(tw[k], halve(mul_i<-1>(a - b)));
+      }
+    }
+  } else {
+    line_sync<T>(logH);
+    // in place, one product per pair: X[k] = E + W^k O and X[H-k] = conj(E - W^k O)
+    for (int k = lane; k <= H / 2; k += G) {
+      const int km = H - k;
+      const C a = buf[spad(k)];
+      const C b = conjg(buf[spad(km & (H - 1))]);
+      const C e = halve(a + b);
+      const C t = cmul(tw[k], halve(mul_i<-1>(a - b)));
+      buf[spad(k)] = e + t;
+      if (k != km) buf[spad(km)] = conjg(e - t);
+    }
+    __syncthreads();
+    if (lt_ok) {
+      int k = (int)threadIdx.x >> logTL;
+      C* gp = out + (size_t)k * ldo + line0 + lt;
+#pragma unroll 4
+      for (; k <= H; k += G, gp += gstep) *gp = trow[spad(k)];
+    }
   }
 }
 
 template <typename T, int REM, int LOGL = 0>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cplx<T>* __restrict__ in, io_t<T>* __restrict__ out, int nlines, int n, size_t ldi,
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restrict__ in, io_t<T>* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
   static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
@@ -191,30 +249,50 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2r_T(const cpl
   __syncthreads();
   C* buf = smem + (size_t)l * LS;
   // repack: Z[k] = A + i T with A = X[k] + conj X[H-k], T = W^{-k} (X[k] - conj X[H-k]), so that
-  // the unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1]); the partner is
-  // Z[H-k] = conj(A - i T)  (one product per pair)
-  for (int k = lane; k <= H / 2; k += G) {
-    const int km = H - k;
-    const C xk = buf[spad(k)];
-    const C b = conjg(buf[spad(km)]);
-    const C A = xk + b;
-    const C iT = mul_i<1>(cmulc(xk - b, tw[k]));
-    buf[spad(k)] = A + iT;
-    if (k != km && km != H) buf[spad(km)] = conjg(A - iT);
-  }
-  line_sync<T>(logH);
+  // the unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1])
   C v[16];
+  if constexpr (kFusedSplitC2R<T>) {
+    // straight into the registers the transform starts from (one product per element)
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
+    for (int m = 0; m < 16; ++m) {
+      const int k = lane + m * G;
+      const C xk = buf[spad(k)];
+      const C b = conjg(buf[spad(H - k)]);
+      v[m] = (xk + b) + mul_i<1>(cmulc(xk - b, tw[k]));
+    }
+  } else {
+    // in place, one product per pair; the partner is Z[H-k] = conj(A - i T)
+    for (int k = lane; k <= H / 2; k += G) {
+      const int km = H - k;
+      const C xk = buf[spad(k)];
+      const C b = conjg(buf[spad(km)]);
+      const C A = xk + b;
+      const C iT = mul_i<1>(cmulc(xk - b, tw[k]));
+      buf[spad(k)] = A + iT;
+      if (k != km && km != H) buf[spad(km)] = conjg(A - iT);
+    }
+    line_sync<T>(logH);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = buf[spad(lane + m * G)];
+  }
   fft_regs<T, 1, false, REM>(v, buf, logH, lane, tw, logP, true);
   // v[m] = y[2q] + i y[2q+1] (times P), q = lane + m G; n <= H keeps only m < 8
   if (line < nlines) {
     io_t<T>* dst = out + (size_t)line * ldo;
+    using IO2 = io_pair<T>;
+    const bool pair_aligned = (reinterpret_cast<uintptr_t>(dst) % sizeof(IO2)) == 0;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int q = lane + m * G;
-      if (2 * q < n) dst[2 * q] = to_io<T>(v[m].x);
-      if (2 * q + 1 < n) dst[2 * q + 1] = to_io<T>(v[m].y);
+      if (pair_aligned && 2 * q + 1 < n) {
+        IO2 t;
+        t.x = to_io<T>(v[m].x);
+        t.y = to_io<T>(v[m].y);
+        *reinterpret_cast<IO2*>(dst + 2 * q) = t;
+      } else {
+        if (2 * q < n) dst[2 * q] = to_io<T>(v[m].x);
+        if (2 * q + 1 < n) dst[2 * q + 1] = to_io<T>(v[m].y);
+      }
     }
   }
 }
@@ -243,7 +321,7 @@ __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int
 // LOGP > 0: the line length 2^LOGP is fixed at compile time (the logP / logPtab arguments are
 // ignored), so stage spans, lane counts and shared-memory strides fold into constants.
 template <typename T, int REM, int LOGP = 0>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
                          const int* __restrict__ skip, Batch bt) {
   static_assert(LOGP == 0 || (LOGP & 3) == REM, "k_colmul: REM = LOGP mod 4");
@@ -313,7 +391,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_colmul(cplx<T>*
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
 template <typename T, int REM, int LOGL = 0>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
   static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
@@ -351,18 +429,22 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_fwd(const 
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
   __syncthreads();
-  C* dst = out + g * gout;
-  const int total = TL * P;
+  // transposed store: thread t serves line t mod TL and rows k = t / TL + j G
   const int logTL = __ffs(TL) - 1;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l2 = idx & (TL - 1), k = idx >> logTL;
-    if (line0 + l2 < nlines) dst[(size_t)k * ldo + line0 + l2] = smem[(size_t)l2 * LS + spad(k)];
+  const int lt = threadIdx.x & (TL - 1);
+  if (line0 + lt < nlines) {
+    const C* trow = smem + (size_t)lt * LS;
+    int k = (int)threadIdx.x >> logTL;
+    C* gp = out + g * gout + (size_t)k * ldo + line0 + lt;
+    const size_t gstep = (size_t)G * ldo;
+#pragma unroll 4
+    for (; k < P; k += G, gp += gstep) *gp = trow[spad(k)];
   }
 }
 
 // transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
 template <typename T, int REM, int LOGL = 0>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
   static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
@@ -408,7 +490,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_c2cT_inv(const 
 
 // lines of length n (stride ld) -> zero-pad to P, forward FFT, write all P outputs (stride ldo)
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kMaxCta<T>, 1)
     k_col_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int ncols, int n, size_t ld, size_t ldo,
               int logP, int TL, const cplx<T>* __restrict__ tw, int logPtab) {
   using C = cplx<T>;
@@ -431,7 +513,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
 
 // lines of P spectrum values (stride ld) -> * multiplier, inverse FFT, crop to n, write (stride ldo)
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kMaxCta<T>, 1)
     k_col_mulinv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int ncols, int n, size_t ld, size_t ldo,
                  int logP, int TL, const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw,
                  int logPtab) {
@@ -471,7 +553,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1)
 // Lines per CTA for a line of `len` complex slots: as many as fit in
 // `budget` bytes of shared memory and 256 threads (at least one), rounded down to a
 // power of two, in whole warps.
-// (every apply kernel is compiled for at most 512 threads per CTA; CTAs of at most 256
+// (the apply kernels are compiled for 512 (FP32: 1024) threads per CTA; CTAs of at most 256
 // threads measured fastest: more independent CTAs per SM overlap their phases)
 int pick_tl(int len, int elem_bytes, int G, int budget, int max_lines, long long lines = 1LL << 40) {
   int tl = budget / (len * elem_bytes);
@@ -881,7 +963,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
 
 
 // Lines per CTA candidates of apply stage `st`: powers of two from whole warps up to the
-// compiled 512-thread bound, 64 lines, and 227 KB of shared memory.
+// compiled thread bound (kMaxCta), 64 lines, and 227 KB of shared memory.
 template <typename T>
 static int stage_line_length(const Plan& p, int st) {
   const int Hx = p.P[0] / 2;
@@ -910,7 +992,7 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
     int best = 0;
     float best_ms = 0.f;
     for (int t = 1; t <= 64 && e == cudaSuccess; t *= 2) {
-      if (t * G > 512 || (size_t)t * sline(L) * eb > 227 * 1024) break;
+      if (t * G > kMaxCta<T> || (size_t)t * sline(L) * eb > 227 * 1024) break;
       if (G < 32 && t < 32 / G) continue;
       p.tl_tuned[eng][st] = t;
       float ms = 0.f;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <cstring>
+#include <type_traits>
 
 #include <string>
 
@@ -62,6 +63,9 @@ __device__ __forceinline__ V ld_stream(const V* p) {
 template <typename T> struct io_t_ { using type = T; };
 template <> struct io_t_<dfl> { using type = double; };
 template <typename T> using io_t = typename io_t_<T>::type;
+
+// two consecutive grid values as one aligned vector (float2 / double2)
+template <typename T> using io_pair = typename std::conditional<sizeof(io_t<T>) == 4, float2, double2>::type;
 
 template <typename T> __device__ __forceinline__ T from_io(io_t<T> v) { return v; }
 template <> __device__ __forceinline__ dfl from_io<dfl>(double v) { return df_from(v); }
