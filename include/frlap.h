@@ -330,12 +330,22 @@ frlap_status frlap_cg_pairs(const frlap_plan* plan, const double* d_f, int K, do
  * Instances of equal shape share one launch per kernel.  d_u[i]: instance i's
  * grid vector (doubles), updated in place.  iters[i], status[i] (host arrays, may
  * be NULL): total CG iterations and frlap_status per instance.  The loop is bounded
- * (nsteps * (maxit + 2) + 8 passes; FRLAP_ETIMEOUT past that).  d_work:
+ * (nsteps * (maxit + 2) + 8 passes, or frlap_set_loop_pass_limit's lower cap;
+ * FRLAP_ETIMEOUT past that).  d_work:
  * frlap_allen_cahn_batch_workspace_bytes bytes.  Synchronises stream. */
 size_t frlap_allen_cahn_batch_workspace_bytes(int nbatch, const frlap_plan* const* plans);
 frlap_status frlap_allen_cahn_batch(int nbatch, const frlap_plan* const* plans, double* const* d_u, double tau,
                                     double eps, int nsteps, double rtol, int maxit, int* iters, int* status,
                                     void* d_work, void* stream);
+
+/* Process-wide cap on the passes of the graph-launched loops: the conditional WHILE
+ * node of frlap_pcg_solve's CG (after its first 8 iterations) and of
+ * frlap_allen_cahn_batch.  Each loop stops after min(its own bound, max_passes)
+ * passes; a loop that stops there with work left returns FRLAP_ETIMEOUT, leaving
+ * the context usable.  0 (the default) keeps the loops' own bounds.  For callers
+ * that want a hard bound on the GPU time of one call, and for tests of the
+ * time-out path.  The paper has no counterpart. */
+frlap_status frlap_set_loop_pass_limit(unsigned max_passes);
 
 /* The message for the last error on the calling thread ("" if none). */
 const char* frlap_last_error(void);

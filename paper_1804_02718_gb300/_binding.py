@@ -62,6 +62,7 @@ _SIGS = {
                                     ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P]),
     "frlap_allen_cahn_step": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), _P, _P]),
     "frlap_allen_cahn_cn": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
+    "frlap_set_loop_pass_limit": (_I, [ctypes.c_uint]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
 
@@ -498,3 +499,8 @@ def frlap_allen_cahn_cn(plan: Plan, ubar: torch.Tensor, tau: float, delta: float
                                      int(nsteps), float(rtol), ctypes.byref(it), mass,
                                      ctypes.c_void_p(work.data_ptr()), _stream(stream)), "frlap_allen_cahn_cn")
     return int(it.value), list(mass[:int(nsteps)])
+
+
+def frlap_set_loop_pass_limit(max_passes: int = 0):
+    """Cap the passes of the graph-launched solver loops (0 restores their own bounds)."""
+    _check(lib().frlap_set_loop_pass_limit(int(max_passes)), "frlap_set_loop_pass_limit")

@@ -12,8 +12,8 @@
 // solution into u and sets up the next step (or marks the instance finished),
 // then a kernel that keeps the loop going while any instance is unfinished.  The
 // loop count is bounded: each solve stops after maxit iterations, and the control
-// kernel also stops the loop after nsteps * (maxit + 2) + 8 passes, reporting
-// FRLAP_ETIMEOUT.
+// kernel also stops the loop after nsteps * (maxit + 2) + 8 passes (or the lower limit set by
+// frlap_set_loop_pass_limit), reporting FRLAP_ETIMEOUT.
 #include <math.h>
 
 #include <vector>
@@ -416,7 +416,7 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
       k_ac_dir<<<grid, kAcThreads, 0, s>>>(g.r, g.p, g.M, g.vs, g.S);
       k_ac_advance<<<grid, kAcThreads, 0, s>>>(g.u, g.x, g.r, g.p, g.M, g.vs, g.S, g.partials, nsteps, tau, rtol);
     }
-    const unsigned max_passes = (unsigned)nsteps * (unsigned)(maxit + 2) + 8u;
+    const unsigned max_passes = capped_passes((unsigned)nsteps * (unsigned)(maxit + 2) + 8u);
     k_ac_control<<<1, 256, 0, s>>>(S_all, nb, passes, max_passes, timeout, h);
     cudaGraph_t captured = nullptr;
     cudaError_t ecap = cudaGetLastError();

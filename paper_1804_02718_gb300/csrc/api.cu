@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -10,6 +11,9 @@
 namespace frlap {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned> g_pass_limit{0u};
+
+unsigned loop_pass_limit() { return g_pass_limit.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -82,6 +86,11 @@ using namespace frlap;
 extern "C" {
 
 const char* frlap_last_error(void) { return g_last_error.c_str(); }
+
+frlap_status frlap_set_loop_pass_limit(unsigned max_passes) {
+  g_pass_limit.store(max_passes, std::memory_order_relaxed);
+  return FRLAP_OK;
+}
 
 frlap_status frlap_c_dalpha(int d, double alpha, double* out) {
   if (d != 2 && d != 3) return fail(FRLAP_EINVAL, "d must be 2 or 3");

@@ -30,6 +30,14 @@ frlap_status cuda_fail(cudaError_t e, const char* where);
     if (e_ != cudaSuccess) return ::frlap::cuda_fail(e_, where);    \
   } while (0)
 
+// Upper bound on the passes of the graph-launched solver loops set by frlap_set_loop_pass_limit
+// (0: none); a loop's bound is min(its own derived bound, this one).
+unsigned loop_pass_limit();
+inline unsigned capped_passes(unsigned derived) {
+  const unsigned cap = loop_pass_limit();
+  return (cap > 0u && cap < derived) ? cap : derived;
+}
+
 // ---------------------------------------------------------------- complex
 template <typename T> struct cplx_t;
 template <> struct cplx_t<float> { using type = float2; };

@@ -525,7 +525,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   if (e == cudaSuccess) {
     cudaError_t eb = iteration(cs, launched);
     if (eb == cudaSuccess) {
-      k_cg_control<<<1, 1, 0, cs>>>(S, (unsigned)maxit + 2u, h);
+      k_cg_control<<<1, 1, 0, cs>>>(S, capped_passes((unsigned)maxit + 2u), h);
       eb = cudaGetLastError();
     }
     cudaGraph_t captured = nullptr;
@@ -540,6 +540,10 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   if (graph) cudaGraphDestroy(graph);
   if (cs) cudaStreamDestroy(cs);
   if (e != cudaSuccess) return cuda_fail(e, "graph-launched CG iterations");
+  if (!hS->done) {  // the loop ran out of passes (a limit set by frlap_set_loop_pass_limit)
+    hS->status = FRLAP_ETIMEOUT;
+    hS->done = 1;
+  }
   return FRLAP_OK;
 }
 

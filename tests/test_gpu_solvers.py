@@ -172,3 +172,46 @@ def test_double_float_solve_outside_fp32_range(frlap, scale, prec, solver):
     fbad[5, 5] = np.inf
     _, _, _, code = frlap.frlap_pcg_solve(plan, _t(fbad), rtol=1e-10, solver=solver, raise_on_error=False)
     assert code == 7  # FRLAP_ENAN, refused before any double-float iteration
+
+
+def test_loop_pass_limit_times_out_and_context_survives(frlap):
+    """FRLAP_ETIMEOUT from the graph-launched loops: a pass limit set from the host ends the CG loop
+    (after its first 8 plain iterations) and the batched Allen-Cahn loop early; each returns the
+    status and the context stays usable (the same solves succeed once the limit is lifted)."""
+    N, alpha = 64, 1.8
+    h = 2.0 / N
+    plan = frlap.Plan(2, alpha, h, (N, N))
+    f = _t(inp.gaussian_sum_field((N, N), h, seed=2))
+    try:
+        frlap.frlap_set_loop_pass_limit(3)
+        x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-12, raise_on_error=False)
+        assert code == 8 and it == 8 + 3, (code, it)  # FRLAP_ETIMEOUT
+        u = torch.from_numpy(inp.uniform_field((N, N), seed=3)).cuda()
+        iters, status, code = frlap.frlap_allen_cahn_batch([plan], [u], 1e-3, 0.05, 5, rtol=1e-12,
+                                                           raise_on_error=False)
+        assert code == 8, code
+    finally:
+        frlap.frlap_set_loop_pass_limit(0)
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-12)
+    assert code == 0 and rel <= 1e-12 and it > 11
+    u = torch.from_numpy(inp.uniform_field((N, N), seed=3)).cuda()
+    iters, status, code = frlap.frlap_allen_cahn_batch([plan], [u], 1e-3, 0.05, 5, rtol=1e-12)
+    assert code == 0 and all(s == 0 for s in status)
+
+
+def test_non_positive_multiplier_breaks_down(frlap):
+    """FRLAP_EBREAKDOWN injected from the host: a preconditioner multiplier that is not positive
+    (m = -1/lambda through the learned slot) makes r.z <= 0, which the solver reports before any
+    update; the context stays usable."""
+    N, alpha = 64, 1.3
+    h = 2.0 / N
+    plan = frlap.Plan(2, alpha, h, (N, N))
+    f = _t(inp.gaussian_sum_field((N, N), h, seed=5))
+    lam = plan.symbol() * float(np.prod(plan.P))
+    frlap.frlap_precond_set_symbol(plan, (-1.0 / lam).contiguous())
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-10, precond=frlap.FRLAP_PRECOND_LEARNED,
+                                             raise_on_error=False)
+    assert code == 6 and it == 0, (code, it)  # FRLAP_EBREAKDOWN
+    frlap.frlap_precond_set_symbol(plan, (1.0 / lam).contiguous())
+    x, it, rel, code = frlap.frlap_pcg_solve(plan, f, rtol=1e-10, precond=frlap.FRLAP_PRECOND_LEARNED)
+    assert code == 0 and rel <= 1e-10
