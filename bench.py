@@ -58,10 +58,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM traffic of one batched launch of the dominant kernel, by (dims, kernel, engine) (dram__bytes_read.sum +
-# dram__bytes_write.sum) from the ncu captures summarised under profiles/; an entry is dropped when its
+# DRAM traffic of one batched launch of the dominant kernel (8 vectors at 2047^2, 2 at 255^3), by (dims,
+# kernel, engine): dram__bytes_read.sum + dram__bytes_write.sum from the ncu captures summarised in
+# profiles/apply_2d_2047_batch8.md and profiles/apply_3d_255_batch2.md; an entry is dropped when its
 # kernel changes after the capture
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1279.2e6, (2, "colmul", "f32"): 593.7e6,
+                    (3, "colmul", "df64"): 2455.1e6, (3, "colmul", "f32"): 1258.5e6}
 
 
 def measure_fp32_fma_tflops(torch):
@@ -313,11 +315,13 @@ def time_applies(fl, torch, plan, U, Y, work, steps, warmup, d, barrier=None):
         barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include "timed/" selects these launches
     e0.record(stream)
     for k in range(steps):
         fl.frlap_apply_batch(plan, U, Y, work, events=evs[k])
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if barrier:
         barrier()
     total = e0.elapsed_time(e1)
