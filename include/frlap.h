@@ -326,7 +326,9 @@ frlap_status frlap_cg_pairs(const frlap_plan* plan, const double* d_f, int K, do
  * launch with on-device control: one conditional WHILE node whose body runs one CG
  * iteration for every instance still solving, then moves each instance whose solve
  * has ended to its next step.  Each step solves (I + tau eps^2 A_i) v =
- * u + tau (u - u^3) by CG from v = 0 to ||r|| <= rtol ||rhs|| or maxit iterations.
+ * u + tau (u - u^3) by CG to ||r|| <= rtol ||rhs|| or maxit iterations, the first
+ * step from v = 0 and every later one from the previous step's solution (its initial
+ * residual follows from the finished solve's residual, with no extra apply).
  * Instances of equal shape share one launch per kernel.  d_u[i]: instance i's
  * grid vector (doubles), updated in place.  iters[i], status[i] (host arrays, may
  * be NULL): total CG iterations and frlap_status per instance.  The loop is bounded
@@ -346,6 +348,22 @@ frlap_status frlap_allen_cahn_batch(int nbatch, const frlap_plan* const* plans, 
  * that want a hard bound on the GPU time of one call, and for tests of the
  * time-out path.  The paper has no counterpart. */
 frlap_status frlap_set_loop_pass_limit(unsigned max_passes);
+
+/* Bounds-checked builds (compiled with -DFRLAP_BOUNDS_CHECK; the package's build script makes
+ * them as libfrlap_bc.so).  There every global load and store of the apply kernels is first tested
+ * against the buffers its call registered (the call's vectors, workspace, symbol, twiddle tables and
+ * skip flags); an access outside all of them is not performed (a load gives zero) but counted.
+ * frlap_bounds_check_report returns in *violations the count since the previous report (summed
+ * over the FP32, FP64 and double-float kernels, then reset) and in *first_address (may be NULL) the
+ * lowest such address; *enabled (may be NULL) is 1 in a checked build, 0 otherwise (where
+ * *violations is always 0).  Synchronises the device.  A tool for tests, standing in for a memory
+ * checker; the paper has no counterpart. */
+frlap_status frlap_bounds_check_report(int* enabled, unsigned long long* violations, unsigned long long* first_address);
+
+/* Checked builds only: probes the checker itself on library-owned memory (8 loads inside a
+ * registered range, 5 just past it, which the checks must skip) and returns in *flagged the
+ * accesses it flagged: 5 when it works.  FRLAP_EINVAL in ordinary builds. */
+frlap_status frlap_bounds_check_selftest(unsigned long long* flagged);
 
 /* The message for the last error on the calling thread ("" if none). */
 const char* frlap_last_error(void);

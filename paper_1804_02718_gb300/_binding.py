@@ -13,7 +13,8 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfrlap.so")
+# FRLAP_LIBRARY selects another build of the same library (the bounds-checked libfrlap_bc.so)
+LIB_PATH = os.environ.get("FRLAP_LIBRARY") or os.path.join(_HERE, "libfrlap.so")
 
 FRLAP_F64, FRLAP_F32, FRLAP_MIXED, FRLAP_DF64, FRLAP_MIXED_DF64 = 0, 1, 2, 3, 4
 FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_OP_AC = 0, 1, 2
@@ -63,6 +64,9 @@ _SIGS = {
     "frlap_allen_cahn_step": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), _P, _P]),
     "frlap_allen_cahn_cn": (_I, [_P, _P, _D, _D, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
     "frlap_set_loop_pass_limit": (_I, [ctypes.c_uint]),
+    "frlap_bounds_check_report": (_I, [ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_ulonglong),
+                                       ctypes.POINTER(ctypes.c_ulonglong)]),
+    "frlap_bounds_check_selftest": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
 
@@ -504,3 +508,20 @@ def frlap_allen_cahn_cn(plan: Plan, ubar: torch.Tensor, tau: float, delta: float
 def frlap_set_loop_pass_limit(max_passes: int = 0):
     """Cap the passes of the graph-launched solver loops (0 restores their own bounds)."""
     _check(lib().frlap_set_loop_pass_limit(int(max_passes)), "frlap_set_loop_pass_limit")
+
+
+def frlap_bounds_check_report():
+    """(enabled, violations since the last report, lowest violating address or 0)."""
+    en = ctypes.c_int(0)
+    v = ctypes.c_ulonglong(0)
+    f = ctypes.c_ulonglong(0)
+    _check(lib().frlap_bounds_check_report(ctypes.byref(en), ctypes.byref(v), ctypes.byref(f)),
+           "frlap_bounds_check_report")
+    return bool(en.value), int(v.value), int(f.value)
+
+
+def frlap_bounds_check_selftest() -> int:
+    """Checked builds: the number of deliberately out-of-range probes the checker flagged (5 expected)."""
+    n = ctypes.c_ulonglong(0)
+    _check(lib().frlap_bounds_check_selftest(ctypes.byref(n)), "frlap_bounds_check_selftest")
+    return int(n.value)

@@ -2,8 +2,8 @@
 //
 // Every instance i (its own plan: alpha, grid) advances nsteps steps of
 //   (I + tau eps^2 A_i) u^{n+1} = u^n + tau (u^n - (u^n)^3),
-// each step solved by CG from x0 = 0 to ||r|| <= rtol ||rhs|| (at most maxit
-// iterations).  Instances of the same shape form a group whose vectors are
+// each step solved by CG to ||r|| <= rtol ||rhs|| (at most maxit iterations), the
+// first from x0 = 0 and every later one from the previous step's solution.  Instances of the same shape form a group whose vectors are
 // stacked, so each kernel below handles a whole group (blockIdx.y = instance).
 //
 // Control flow lives on the device.  The graph is one conditional WHILE node whose
@@ -79,9 +79,42 @@ __device__ __forceinline__ bool inst_sum(double v, double* partials, unsigned* c
 
 #define INST_LOOP(i, n) for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
 
-// end of a solve (or start): u <- x, rhs = u + tau (u - u^3), x = 0, r = p = rhs
+// two per-instance sums (partial arrays pa, pb); true in thread 0 of the instance's last block
+__device__ __forceinline__ bool inst_sum2(double a, double b, double* pa, double* pb, unsigned* counter,
+                                          double* ta, double* tb) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  const double sa = bsum(a, red);
+  const double sb = bsum(b, red);
+  if (threadIdx.x == 0) {
+    pa[blockIdx.x] = sa;
+    pb[blockIdx.x] = sb;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  double xa = 0.0, xb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    xa += *((volatile double*)&pa[i]);
+    xb += *((volatile double*)&pb[i]);
+  }
+  const double va = bsum(xa, red);
+  const double vb = bsum(xb, red);
+  if (threadIdx.x == 0) {
+    *ta = va;
+    *tb = vb;
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+// Start of a solve.  The first step: rhs = u + tau (u - u^3), x = 0, r = p = rhs.  After a solve:
+// u <- x, and the next step starts from x = u^{n+1} itself (warm start).  Its initial residual
+// needs no apply: the finished solve's recursive residual is r = rhs_old - B x, so
+// rhs_new - B x = rhs_new - rhs_old + r, with rhs_old recomputed from the old u.
 __global__ void k_ac_advance(double* u, double* x, double* r, double* p, size_t M, size_t vs, AcState* S,
-                             double* partials, int nsteps, double tau, double rtol) {
+                             double* partials, double* partials2, int nsteps, double tau, double rtol) {
   const int b = blockIdx.y;
   AcState* st = S + b;
   if (!st->done || st->finished) return;
@@ -91,32 +124,42 @@ __global__ void k_ac_advance(double* u, double* x, double* r, double* p, size_t 
   x += b * vs;
   r += b * vs;
   p += b * vs;
-  double acc = 0.0;
+  double acc_r = 0.0, acc_h = 0.0;
   INST_LOOP(i, M) {
-    double v = u[i];
-    if (!fresh) {
-      v = x[i];
-      u[i] = v;
-    }
-    if (!last_step) {
+    if (fresh) {
+      const double v = u[i];
       const double rh = v + tau * (v - v * v * v);
       x[i] = 0.0;
       r[i] = rh;
       p[i] = rh;
-      acc += rh * rh;
+      acc_r += rh * rh;
+      acc_h += rh * rh;
+    } else {
+      const double uo = u[i], v = x[i];
+      u[i] = v;
+      if (!last_step) {
+        const double rh_old = uo + tau * (uo - uo * uo * uo);
+        const double rh = v + tau * (v - v * v * v);
+        const double r0 = rh - rh_old + r[i];
+        r[i] = r0;
+        p[i] = r0;
+        acc_r += r0 * r0;
+        acc_h += rh * rh;
+      }
     }
   }
-  double tot;
-  if (inst_sum(acc, partials + (size_t)b * gridDim.x, &st->counter, &tot)) {
+  double tot_r, tot_h;
+  if (inst_sum2(acc_r, acc_h, partials + (size_t)b * gridDim.x, partials2 + (size_t)b * gridDim.x, &st->counter,
+                &tot_r, &tot_h)) {
     if (!fresh) st->step += 1;
     st->fresh = 0;
     if (st->step >= nsteps) {
       st->finished = 1;
     } else {
-      st->rr = tot;
-      st->tol2 = rtol * rtol * tot;
+      st->rr = tot_r;
+      st->tol2 = rtol * rtol * tot_h;
       st->iters = 0;
-      st->done = (tot <= st->tol2) ? 1 : 0;
+      st->done = (tot_r <= st->tol2) ? 1 : 0;
     }
   }
 }
@@ -239,6 +282,7 @@ struct Group {
   double* q;
   void* awork;          // [B][apply work]
   double* partials;     // [B][kAcBlocks]
+  double* partials2;    // [B][kAcBlocks] (the second sum of k_ac_advance)
   AcState* S;           // points into the global state array
 };
 
@@ -282,7 +326,7 @@ size_t group_bytes(const Group& g) {
   const Plan& p = *g.plan;
   const size_t B = g.idx.size();
   return B * (align256(p.lam_count * 8) + 5 * align256(p.M * 8) + apply_work_bytes(p, 8) +
-              align256(kAcBlocks * sizeof(double)));
+              2 * align256(kAcBlocks * sizeof(double)));
 }
 
 }  // namespace
@@ -323,6 +367,8 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
     g.awork = w;
     w += B * g.work_stride;
     g.partials = reinterpret_cast<double*>(w);
+    w += B * align256(kAcBlocks * sizeof(double));
+    g.partials2 = reinterpret_cast<double*>(w);
     w += B * align256(kAcBlocks * sizeof(double));
     g.S = S_all + soff;
     soff += (int)B;
@@ -414,7 +460,8 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
       k_ac_pq<<<grid, kAcThreads, 0, s>>>(g.p, g.q, g.M, g.vs, g.S, g.partials, sc);
       k_ac_update<<<grid, kAcThreads, 0, s>>>(g.x, g.r, g.p, g.q, g.M, g.vs, g.S, g.partials, maxit);
       k_ac_dir<<<grid, kAcThreads, 0, s>>>(g.r, g.p, g.M, g.vs, g.S);
-      k_ac_advance<<<grid, kAcThreads, 0, s>>>(g.u, g.x, g.r, g.p, g.M, g.vs, g.S, g.partials, nsteps, tau, rtol);
+      k_ac_advance<<<grid, kAcThreads, 0, s>>>(g.u, g.x, g.r, g.p, g.M, g.vs, g.S, g.partials, g.partials2, nsteps,
+                                                tau, rtol);
     }
     const unsigned max_passes = capped_passes((unsigned)nsteps * (unsigned)(maxit + 2) + 8u);
     k_ac_control<<<1, 256, 0, s>>>(S_all, nb, passes, max_passes, timeout, h);

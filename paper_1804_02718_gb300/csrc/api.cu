@@ -87,6 +87,39 @@ extern "C" {
 
 const char* frlap_last_error(void) { return g_last_error.c_str(); }
 
+frlap_status frlap_bounds_check_report(int* enabled, unsigned long long* violations,
+                                       unsigned long long* first_address) {
+  if (!violations) return fail(FRLAP_EINVAL, "violations is NULL");
+  unsigned long long total = 0ull, first = ~0ull;
+  cudaError_t (*collect[3])(unsigned long long*, unsigned long long*) = {bc_collect<float>, bc_collect<double>,
+                                                                         bc_collect<dfl>};
+  for (auto fn : collect) {
+    unsigned long long c = 0ull, f = ~0ull;
+    FRLAP_CUDA_TRY(fn(&c, &f));
+    total += c;
+    if (f < first) first = f;
+  }
+#ifdef FRLAP_BOUNDS_CHECK
+  if (enabled) *enabled = 1;
+#else
+  if (enabled) *enabled = 0;
+#endif
+  *violations = total;
+  if (first_address) *first_address = total ? first : 0ull;
+  return FRLAP_OK;
+}
+
+frlap_status frlap_bounds_check_selftest(unsigned long long* flagged) {
+  if (!flagged) return fail(FRLAP_EINVAL, "flagged is NULL");
+#ifdef FRLAP_BOUNDS_CHECK
+  FRLAP_CUDA_TRY(bc_selftest(flagged));
+  return FRLAP_OK;
+#else
+  *flagged = 0ull;
+  return fail(FRLAP_EINVAL, "not a bounds-checked build (compile with -DFRLAP_BOUNDS_CHECK)");
+#endif
+}
+
 frlap_status frlap_set_loop_pass_limit(unsigned max_passes) {
   g_pass_limit.store(max_passes, std::memory_order_relaxed);
   return FRLAP_OK;

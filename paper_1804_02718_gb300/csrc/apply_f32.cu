@@ -10,4 +10,6 @@ template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void
 
 template cudaError_t autotune_engine<float>(Plan&, int, float*, float*, void*, cudaStream_t);
 
+template cudaError_t bc_collect<float>(unsigned long long*, unsigned long long*);
+
 }  // namespace frlap

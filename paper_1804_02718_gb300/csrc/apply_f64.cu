@@ -38,4 +38,43 @@ template cudaError_t spectrum_inverse<double>(const Plan&, const double2*, const
 
 template cudaError_t autotune_engine<double>(Plan&, int, double*, double*, void*, cudaStream_t);
 
+template cudaError_t bc_collect<double>(unsigned long long*, unsigned long long*);
+
+#ifdef FRLAP_BOUNDS_CHECK
+static __device__ double g_bc_probe[16];
+
+// 8 loads inside the registered range, 5 just past it (still inside g_bc_probe, so harmless
+// whether or not the checks skip them), one store to the registered sink
+__global__ void k_bc_selftest(const double* buf, double* sink) {
+  double s = 0.0;
+  for (int i = 0; i < 8; ++i) s += FRLAP_GLD(buf + i);
+  for (int i = 8; i < 13; ++i) s += FRLAP_GLD(buf + i);
+  FRLAP_GST(sink, s);
+}
+#endif
+
+cudaError_t bc_selftest(unsigned long long* flagged) {
+#ifdef FRLAP_BOUNDS_CHECK
+  unsigned long long c = 0, f = 0;
+  cudaError_t e = bc_collect<double>(&c, &f);  // reset
+  double* probe = nullptr;
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&probe), g_bc_probe);
+  if (e != cudaSuccess) return e;
+  BcRanges r;
+  r.add(probe, 8 * sizeof(double));
+  r.add(probe + 15, sizeof(double));
+  if ((e = r.commit(nullptr)) != cudaSuccess) return e;
+  k_bc_selftest<<<1, 1>>>(probe, probe + 15);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+  e = bc_collect<double>(&c, &f);
+  *flagged = c;
+  if (e == cudaSuccess && c > 0 && f != reinterpret_cast<unsigned long long>(probe + 8)) *flagged = ~0ull;
+  return e;
+#else
+  *flagged = 0ull;
+  return cudaErrorNotSupported;
+#endif
+}
+
 }  // namespace frlap

@@ -34,6 +34,25 @@ struct Batch {
   int skip = 0;
 };
 
+#ifdef FRLAP_BOUNDS_CHECK
+__global__ void k_bc_register(BcTable t) { g_bc_table = t; }
+
+// The byte ranges one launching call may touch, registered on its stream before its kernels.
+struct BcRanges {
+  BcTable t = {};
+  void add(const void* p, size_t bytes) {
+    if (!p || bytes == 0 || t.n >= kBcMaxRanges) return;
+    t.lo[t.n] = reinterpret_cast<unsigned long long>(p);
+    t.hi[t.n] = t.lo[t.n] + bytes;
+    ++t.n;
+  }
+  cudaError_t commit(cudaStream_t s) const {
+    k_bc_register<<<1, 1, 0, s>>>(t);
+    return cudaGetLastError();
+  }
+};
+#endif
+
 // Where a middle-stage column finds its multiplier line.  Column index: 2D kx, 3D kx * P_y + ky.
 struct LamMap {
   int d;       // 2 or 3
@@ -57,7 +76,7 @@ __device__ __forceinline__ void load_line(C* buf, const C* __restrict__ src, int
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = lane + (j0 + u) * G;
-      t[u] = (valid && i < n) ? src[i] : czero<C>();
+      t[u] = (valid && i < n) ? FRLAP_GLD(src + i) : czero<C>();
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) buf[spad(lane + (j0 + u) * G)] = t[u];
@@ -98,7 +117,10 @@ __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ s
   const C* gp = src + (size_t)k * ld + line0 + lt;
   const size_t gstep = (size_t)kstep * ld;
 #pragma unroll 4
-  for (; k < kend; k += kstep, gp += gstep) cp_async_elem<(int)sizeof(C)>(&row[spad(k)], ok ? gp : src, ok);
+  for (; k < kend; k += kstep, gp += gstep) {
+    const bool okk = ok && FRLAP_GOK(gp);
+    cp_async_elem<(int)sizeof(C)>(&row[spad(k)], okk ? gp : src, okk);
+  }
   cp_async_wait_all();
 }
 
@@ -138,7 +160,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
-  if (skip && *skip) return;
+  if (skip && FRLAP_GLD(skip)) return;
   const int H = 1 << logH, G = H >> 4;
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int line0 = blockIdx.x * TL;
@@ -159,12 +181,12 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
     io_t<T> re = io_t<T>(0), im = io_t<T>(0);
     if (m < 8 && valid) {
       if (pair_aligned && 2 * q + 1 < n) {
-        const IO2 t = *reinterpret_cast<const IO2*>(src + 2 * q);
+        const IO2 t = FRLAP_GLD(reinterpret_cast<const IO2*>(src + 2 * q));
         re = t.x;
         im = t.y;
       } else {
-        if (2 * q < n) re = src[2 * q];
-        if (2 * q + 1 < n) im = src[2 * q + 1];
+        if (2 * q < n) re = FRLAP_GLD(src + 2 * q);
+        if (2 * q + 1 < n) im = FRLAP_GLD(src + 2 * q + 1);
       }
     }
     v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
@@ -195,7 +217,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
       for (; k <= H; k += G, gp += gstep) {
         const C a = trow[spad(k & (H - 1))];
         const C b = conjg(trow[spad((H - k) & (H - 1))]);
-        *gp = halve(a + b) + cmul(tw[k], halve(mul_i<-1>(a - b)));
+        FRLAP_GST(gp, halve(a + b) + cmul(FRLAP_GLD(tw + k), halve(mul_i<-1>(a - b))));
       }
     }
   } else {
@@ -206,7 +228,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
       const C a = buf[spad(k)];
       const C b = conjg(buf[spad(km & (H - 1))]);
       const C e = halve(a + b);
-      const C t = cmul(tw[k], halve(mul_i<-1>(a - b)));
+      const C t = cmul(FRLAP_GLD(tw + k), halve(mul_i<-1>(a - b)));
       buf[spad(k)] = e + t;
       if (k != km) buf[spad(km)] = conjg(e - t);
     }
@@ -215,7 +237,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
       int k = (int)threadIdx.x >> logTL;
       C* gp = out + (size_t)k * ldo + line0 + lt;
 #pragma unroll 4
-      for (; k <= H; k += G, gp += gstep) *gp = trow[spad(k)];
+      for (; k <= H; k += G, gp += gstep) FRLAP_GST(gp, trow[spad(k)]);
     }
   }
 }
@@ -238,7 +260,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
-  if (skip && *skip) return;
+  if (skip && FRLAP_GLD(skip)) return;
   const int H = 1 << logH, G = H >> 4;
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int line0 = blockIdx.x * TL;
@@ -258,7 +280,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
       const int k = lane + m * G;
       const C xk = buf[spad(k)];
       const C b = conjg(buf[spad(H - k)]);
-      v[m] = (xk + b) + mul_i<1>(cmulc(xk - b, tw[k]));
+      v[m] = (xk + b) + mul_i<1>(cmulc(xk - b, FRLAP_GLD(tw + k)));
     }
   } else {
     // in place, one product per pair; the partner is Z[H-k] = conj(A - i T)
@@ -267,7 +289,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
       const C xk = buf[spad(k)];
       const C b = conjg(buf[spad(km)]);
       const C A = xk + b;
-      const C iT = mul_i<1>(cmulc(xk - b, tw[k]));
+      const C iT = mul_i<1>(cmulc(xk - b, FRLAP_GLD(tw + k)));
       buf[spad(k)] = A + iT;
       if (k != km && km != H) buf[spad(km)] = conjg(A - iT);
     }
@@ -288,10 +310,10 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
         IO2 t;
         t.x = to_io<T>(v[m].x);
         t.y = to_io<T>(v[m].y);
-        *reinterpret_cast<IO2*>(dst + 2 * q) = t;
+        FRLAP_GST(reinterpret_cast<IO2*>(dst + 2 * q), t);
       } else {
-        if (2 * q < n) dst[2 * q] = to_io<T>(v[m].x);
-        if (2 * q + 1 < n) dst[2 * q + 1] = to_io<T>(v[m].y);
+        if (2 * q < n) FRLAP_GST(dst + 2 * q, to_io<T>(v[m].x));
+        if (2 * q + 1 < n) FRLAP_GST(dst + 2 * q + 1, to_io<T>(v[m].y));
       }
     }
   }
@@ -313,7 +335,7 @@ __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int i = lane + m * G;
-    if (i < n) out[i] = CONJ ? conjg(v[m]) : v[m];
+    if (i < n) FRLAP_GST(out + i, CONJ ? conjg(v[m]) : v[m]);
   }
 }
 
@@ -338,7 +360,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
-  if (skip && *skip) return;
+  if (skip && FRLAP_GLD(skip)) return;
   const int P = 1 << logP, G = P >> 4;
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
   const int col = blockIdx.x * TL + l;
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __res
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
-  if (skip && *skip) return;
+  if (skip && FRLAP_GLD(skip)) return;
   const int P = 1 << logP, G = P >> 4;
   const int g = blockIdx.x / tiles, tile = blockIdx.x % tiles;
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
@@ -422,7 +444,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __res
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
     const int i = lane + m * G;
-    v[m] = (m < 8 && valid && i < n) ? src[i] : czero<C>();
+    v[m] = (m < 8 && valid && i < n) ? FRLAP_GLD(src + i) : czero<C>();
   }
   fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
   line_sync<T>(logP);
@@ -438,7 +460,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __res
     C* gp = out + g * gout + (size_t)k * ldo + line0 + lt;
     const size_t gstep = (size_t)G * ldo;
 #pragma unroll 4
-    for (; k < P; k += G, gp += gstep) *gp = trow[spad(k)];
+    for (; k < P; k += G, gp += gstep) FRLAP_GST(gp, trow[spad(k)]);
   }
 }
 
@@ -461,7 +483,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_inv(const cplx<T>* __res
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
-  if (skip && *skip) return;
+  if (skip && FRLAP_GLD(skip)) return;
   const int P = 1 << logP, G = P >> 4;
   const int g = blockIdx.x / tiles, tile = blockIdx.x % tiles;
   const int l = threadIdx.x / G, lane = threadIdx.x % G;
@@ -482,7 +504,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_inv(const cplx<T>* __res
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int i = lane + m * G;
-      if (i < n) dst[i] = v[m];
+      if (i < n) FRLAP_GST(dst + i, v[m]);
     }
   }
 }
@@ -507,7 +529,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1)
   fft_line<T, -1, true, false>(buf, logP, lane, tw, logPtab);
   if (valid) {
     C* dst = out + (size_t)col * ldo;
-    for (int i = lane; i < P; i += G) dst[i] = buf[spad(i)];
+    for (int i = lane; i < P; i += G) FRLAP_GST(dst + i, buf[spad(i)]);
   }
 }
 
@@ -540,13 +562,13 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1)
   }
   for (int k = lane; k < P; k += G) {
     const int kf = min(k, P - k);
-    buf[spad(k)] = valid ? lam[lam_base + (size_t)kf * lam_stride] * src[k] : czero<C>();
+    buf[spad(k)] = valid ? FRLAP_GLD(lam + lam_base + (size_t)kf * lam_stride) * FRLAP_GLD(src + k) : czero<C>();
   }
   __syncthreads();
   fft_line<T, 1, false, true>(buf, logP, lane, tw, logPtab);
   if (valid) {
     C* dst = out + (size_t)col * ldo;
-    for (int i = lane; i < n; i += G) dst[i] = buf[spad(i)];
+    for (int i = lane; i < n; i += G) FRLAP_GST(dst + i, buf[spad(i)]);
   }
 }
 
@@ -688,6 +710,20 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   const size_t ld1 = (size_t)nrows;  // S1 k-stride: all (z, y) rows
   // per-instance workspace: S1 and S2 of one apply, in complex elements
   const size_t wstride = apply_work_bytes(p, sizeof(T)) / eb;
+#ifdef FRLAP_BOUNDS_CHECK
+  {
+    BcRanges r;
+    const size_t vext = ((size_t)(B - 1) * vstride + p.M) * sizeof(io_t<T>);
+    r.add(u, vext);
+    r.add(y, vext);
+    r.add(work, (size_t)B * apply_work_bytes(p, sizeof(T)));
+    r.add(lam, ((size_t)(B - 1) * lam_stride + p.lam_count) * sizeof(T));
+    for (int a = 0; a < p.d; ++a) r.add(tw[a], (size_t)twiddle_entries(p.P[a]) * sizeof(C));
+    if (skip) r.add(skip, ((size_t)(B - 1) * skip_stride + 1) * sizeof(int));
+    cudaError_t e = r.commit(s);
+    if (e != cudaSuccess) return e;
+  }
+#endif
   if (B > 1) S2 = S1 + align256(p.s1_elems * eb) / eb;
   Batch b_in;   // u -> S1
   b_in.in = vstride;
@@ -841,6 +877,17 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
   const int budget = 96 * 1024;
   const C* tw[3];
   for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
+#ifdef FRLAP_BOUNDS_CHECK
+  {
+    BcRanges r;
+    r.add(u, p.M * sizeof(T));
+    r.add(SP, spectrum_elems(p) * sizeof(C));
+    r.add(work, apply_work_bytes(p, sizeof(T)));
+    for (int a = 0; a < p.d; ++a) r.add(tw[a], (size_t)twiddle_entries(p.P[a]) * sizeof(C));
+    cudaError_t e = r.commit(s);
+    if (e != cudaSuccess) return e;
+  }
+#endif
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -902,6 +949,18 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
   const int budget = 96 * 1024;
   const C* tw[3];
   for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
+#ifdef FRLAP_BOUNDS_CHECK
+  {
+    BcRanges r;
+    r.add(SP, spectrum_elems(p) * sizeof(C));
+    r.add(mult, p.lam_count * sizeof(T));
+    r.add(y, p.M * sizeof(T));
+    r.add(work, apply_work_bytes(p, sizeof(T)));
+    for (int a = 0; a < p.d; ++a) r.add(tw[a], (size_t)twiddle_entries(p.P[a]) * sizeof(C));
+    cudaError_t e = r.commit(s);
+    if (e != cudaSuccess) return e;
+  }
+#endif
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -1012,6 +1071,24 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
   }
   for (int i = 0; i <= ns; ++i) cudaEventDestroy(ev[i]);
   return e;
+}
+
+template <typename T>
+cudaError_t bc_collect(unsigned long long* count, unsigned long long* first) {
+#ifdef FRLAP_BOUNDS_CHECK
+  BcState st;
+  cudaError_t e = cudaMemcpyFromSymbol(&st, g_bc_state, sizeof(st));
+  if (e != cudaSuccess) return e;
+  const BcState z = {0ull, ~0ull};
+  e = cudaMemcpyToSymbol(g_bc_state, &z, sizeof(z));
+  *count = st.count;
+  *first = st.first;
+  return e;
+#else
+  *count = 0ull;
+  *first = ~0ull;
+  return cudaSuccess;
+#endif
 }
 
 }  // namespace frlap

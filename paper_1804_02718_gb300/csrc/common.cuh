@@ -45,6 +45,44 @@ template <> struct cplx_t<double> { using type = double2; };
 template <> struct cplx_t<dfl> { using type = cdf; };
 template <typename T> using cplx = typename cplx_t<T>::type;
 
+#ifdef FRLAP_BOUNDS_CHECK
+constexpr int kBcMaxRanges = 12;
+// the global byte ranges [lo, hi) the current launch may touch
+struct BcTable {
+  unsigned long long lo[kBcMaxRanges], hi[kBcMaxRanges];
+  int n;
+};
+// accesses outside every range: how many, and the lowest such address
+struct BcState {
+  unsigned long long count, first;
+};
+// One copy per translation unit (file-scope statics): each apply translation unit registers and
+// reports its own (apply_impl.cuh).
+static __device__ BcTable g_bc_table;
+static __device__ BcState g_bc_state = {0ull, ~0ull};
+
+__device__ __forceinline__ bool bc_ok(const void* p, size_t bytes) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  if (g_bc_table.n == 0) return true;  // a translation unit that registers no ranges (symbol generation)
+  for (int i = 0; i < g_bc_table.n; ++i)
+    if (a >= g_bc_table.lo[i] && a + bytes <= g_bc_table.hi[i]) return true;
+  atomicAdd(&g_bc_state.count, 1ull);
+  atomicMin(&g_bc_state.first, a);
+  return false;
+}
+template <typename V>
+__device__ __forceinline__ V bc_ld(const V* p) {
+  V v;
+  if (bc_ok(p, sizeof(V))) v = *p;
+  else memset(&v, 0, sizeof(V));
+  return v;
+}
+template <typename V>
+__device__ __forceinline__ void bc_st(V* p, const V& v) {
+  if (bc_ok(p, sizeof(V))) *p = v;
+}
+#endif
+
 // Load of data a kernel reads once (cache-streaming: evict-first in L1 and L2), so that the
 // twiddle tables keep the L1.  8- and 16-byte values: float2 / float4 / double2 / cdf; 4 and 8
 // byte scalars.
@@ -52,6 +90,12 @@ template <typename V>
 __device__ __forceinline__ V ld_stream(const V* p) {
   static_assert(sizeof(V) == 4 || sizeof(V) == 8 || sizeof(V) == 16, "ld_stream: 4, 8 or 16 bytes");
   V r;
+#ifdef FRLAP_BOUNDS_CHECK
+  if (!bc_ok(p, sizeof(V))) {
+    memset(&r, 0, sizeof(V));
+    return r;
+  }
+#endif
   if constexpr (sizeof(V) == 4) {
     const float t = __ldcs(reinterpret_cast<const float*>(p));
     memcpy(&r, &t, 4);
@@ -64,6 +108,24 @@ __device__ __forceinline__ V ld_stream(const V* p) {
   }
   return r;
 }
+
+// ---------------------------------------------------------------- bounds-checked build
+// With -DFRLAP_BOUNDS_CHECK every global load and store of the apply kernels goes through
+// FRLAP_GLD / FRLAP_GST / FRLAP_GOK, which test the accessed bytes against the buffers the
+// launching call registered (apply_impl.cuh: the call's vectors, workspace, symbol, twiddle
+// tables and skip flags).  An access outside all of them is counted, its address kept, and
+// the access is skipped (a load returns zero): nothing faults.  Without the macro the three
+// expand to the plain accesses.
+#ifdef FRLAP_BOUNDS_CHECK
+#define FRLAP_GLD(p) ::frlap::bc_ld(p)
+#define FRLAP_GST(p, v) ::frlap::bc_st((p), (v))
+#define FRLAP_GOK(p) ::frlap::bc_ok((p), sizeof(*(p)))
+#else
+#define FRLAP_GLD(p) (*(p))
+#define FRLAP_GST(p, v) (*(p) = (v))
+#define FRLAP_GOK(p) true
+#endif
+
 
 // storage type of the real grid vectors and of the symbol for each compute type:
 // FP32 and FP64 compute and store in their own type; double-float computes in
@@ -170,6 +232,14 @@ struct Plan {
   // frlap_plan_autotune; 0 = the built-in choice
   int tl_tuned[3][5] = {};
 };
+
+// Bounds-checked builds: accesses outside the registered ranges since the last call, summed per
+// engine's translation unit (the counters are reset); ordinary builds report zero.
+template <typename T>
+cudaError_t bc_collect(unsigned long long* count, unsigned long long* first);
+// Bounds-checked builds: registers one 8-double range and probes 8 loads inside it and 5 just past
+// it (memory the library owns, so the probes are safe even unchecked); *flagged = accesses flagged.
+cudaError_t bc_selftest(unsigned long long* flagged);
 
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
 // T = compute type (float, double or dfl); vectors are io_t<T>, symbol overrides are T

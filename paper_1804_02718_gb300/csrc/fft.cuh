@@ -178,7 +178,7 @@ __device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict
   const int Ns = 1 << logNs;
   const cplx<T>* st = tw + (1 << logPtab) + 15 * (Ns - 1) - Ns + k;
 #pragma unroll
-  for (int r = 1; r < 16; ++r) w[r] = st[r * Ns];
+  for (int r = 1; r < 16; ++r) w[r] = FRLAP_GLD(st + r * Ns);
 }
 
 // Barrier between the read and write halves of a stage.  The G = L/16 lanes of a line
@@ -247,7 +247,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int logL, int Ns, int lo
       } else {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C wr = tw[(r * k) << sh];
+          const C wr = FRLAP_GLD(tw + ((r * k) << sh));
           v[b * R + r] = (SIGN < 0) ? cmul(v[b * R + r], wr) : cmulc(v[b * R + r], wr);
         }
       }
@@ -371,7 +371,7 @@ __device__ __forceinline__ void regs_last_stage(cplx<T>* v, int lane, int G, con
     for (int r = 0; r < R; ++r) {
       t[r] = v[b + r * B];
       if (r > 0) {
-        const C wr = tw[(r * j) << shift];
+        const C wr = FRLAP_GLD(tw + ((r * j) << shift));
         t[r] = (SIGN < 0) ? cmul_lazy(t[r], wr) : cmulc_lazy(t[r], wr);
       }
     }
