@@ -240,8 +240,7 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
     if (p->df64) {
       if (cudaMalloc(&p->twdf[r], ntw * sizeof(cdf)) != cudaSuccess)
         return cleanup(FRLAP_ENOMEM, "plan allocation failed");
-      e = to_df_launch(reinterpret_cast<const double*>(p->tw64[r]), reinterpret_cast<dfl*>(p->twdf[r]),
-                       2 * (size_t)ntw, s);
+      e = to_cdf_launch(p->tw64[r], p->twdf[r], (size_t)ntw, s);
       if (e != cudaSuccess) return cleanup(FRLAP_ECUDA, std::string("twiddles: ") + cudaGetErrorString(e));
     }
   }

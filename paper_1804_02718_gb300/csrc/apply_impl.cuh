@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
   // The half-length transform Z of the packed samples gives X[k], k = 0..H, by the real-data
   // split: with a = Z[k mod H], b = conj Z[(H-k) mod H], E = (a + b)/2 and O = -i (a - b)/2,
   // X[k] = E + W^k O (W = exp(-2 pi i / 2H)).
-  const int total = TL * (H + 1);
   const int logTL = __ffs(TL) - 1;
   // Transposed store: thread t serves line t mod TL of the tile and bins k = t / TL + j G of it
   // (TL G threads), walking its output column with a pointer increment.
@@ -308,12 +307,12 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
       const int q = lane + m * G;
       if (pair_aligned && 2 * q + 1 < n) {
         IO2 t;
-        t.x = to_io<T>(v[m].x);
-        t.y = to_io<T>(v[m].y);
+        t.x = to_io<T>(re(v[m]));
+        t.y = to_io<T>(im(v[m]));
         FRLAP_GST(reinterpret_cast<IO2*>(dst + 2 * q), t);
       } else {
-        if (2 * q < n) FRLAP_GST(dst + 2 * q, to_io<T>(v[m].x));
-        if (2 * q + 1 < n) FRLAP_GST(dst + 2 * q + 1, to_io<T>(v[m].y));
+        if (2 * q < n) FRLAP_GST(dst + 2 * q, to_io<T>(re(v[m])));
+        if (2 * q + 1 < n) FRLAP_GST(dst + 2 * q + 1, to_io<T>(im(v[m])));
       }
     }
   }

@@ -405,7 +405,20 @@ __global__ void k_to_df(const double* __restrict__ src, dfl* dst, size_t n) {
 }
 }  // namespace
 
-// double-float copies of a symbol (n values) or of a twiddle table (n complex values = 2n doubles)
+namespace {
+__global__ void k_to_cdf(const double2* __restrict__ src, cdf* dst, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = make_cdf(df_from(src[i].x), df_from(src[i].y));
+}
+}  // namespace
+
+// double-float copy of a complex table (twiddles), n values, in the paired layout of cdf
+cudaError_t to_cdf_launch(const double2* src, cdf* dst, size_t n, cudaStream_t st) {
+  k_to_cdf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+// double-float copies of a symbol (n values)
 cudaError_t to_df_launch(const double* src, dfl* dst, size_t n, cudaStream_t st) {
   k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
   return cudaGetLastError();

@@ -142,29 +142,49 @@ template <> __device__ __forceinline__ dfl from_io<dfl>(double v) { return df_fr
 template <typename T> __device__ __forceinline__ io_t<T> to_io(T v) { return v; }
 template <> __device__ __forceinline__ double to_io<dfl>(dfl v) { return df_to(v); }
 
-template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
-  C c; c.x = a; c.y = b; return c;
-}
+// the real type of a complex type
+template <typename C> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+template <> struct real_of<cdf> { using type = dfl; };
+template <typename C> using real_t = typename real_of<C>::type;
+
+__host__ __device__ __forceinline__ float2 make_cplx(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 make_cplx(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ cdf make_cplx(dfl a, dfl b) { return make_cdf(a, b); }
+template <typename C> __host__ __device__ __forceinline__ C mk(real_t<C> a, real_t<C> b) { return make_cplx(a, b); }
 template <typename C> __host__ __device__ __forceinline__ C czero() {
-  using T = decltype(C::x);
+  using T = real_t<C>;
   return mk<C>(T(0), T(0));
 }
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// real and imaginary parts
+__device__ __forceinline__ float re(float2 a) { return a.x; }
+__device__ __forceinline__ float im(float2 a) { return a.y; }
+__device__ __forceinline__ double re(double2 a) { return a.x; }
+__device__ __forceinline__ double im(double2 a) { return a.y; }
+__device__ __forceinline__ dfl re(cdf a) { return cdf_re(a); }
+__device__ __forceinline__ dfl im(cdf a) { return cdf_im(a); }
+// FP32 complex sums as single paired instructions (each component rounded as the scalar add;
+// a - b as b * (-1) + a, whose product is exact)
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return __fmul2_rn(make_float2(s, s), a); }
 // Sums that only feed another sum: plain for FP32 / FP64; without the closing renormalisation
 // for double-float (dfloat.cuh).
-__device__ __forceinline__ float2 add_lazy(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 sub_lazy(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 add_lazy(float2 a, float2 b) { return a + b; }
+__device__ __forceinline__ float2 sub_lazy(float2 a, float2 b) { return a - b; }
 __device__ __forceinline__ double2 add_lazy(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 sub_lazy(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 // a / 2, exactly (a power-of-two scaling of each component)
-__device__ __forceinline__ float2 halve(float2 a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+__device__ __forceinline__ float2 halve(float2 a) { return __fmul2_rn(a, make_float2(0.5f, 0.5f)); }
 __device__ __forceinline__ double2 halve(double2 a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
 __device__ __forceinline__ cdf halve(cdf a) {
-  return cdf{dfl(0.5f * a.x.hi, 0.5f * a.x.lo), dfl(0.5f * a.y.hi, 0.5f * a.y.lo)};
+  cdf r;
+  r.hi = p_mul(a.hi, p_bcast(0.5f));
+  r.lo = p_mul(a.lo, p_bcast(0.5f));
+  return r;
 }
 __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 
@@ -188,12 +208,26 @@ __device__ __forceinline__ double2 cmul_lazy(double2 a, double2 b) { return cmul
 __device__ __forceinline__ float2 cmulc_lazy(float2 a, float2 b) { return cmulc(a, b); }
 __device__ __forceinline__ double2 cmulc_lazy(double2 a, double2 b) { return cmulc(a, b); }
 template <typename C> __device__ __forceinline__ C conjg(C a) { a.y = -a.y; return a; }
+template <> __device__ __forceinline__ cdf conjg<cdf>(cdf a) { return cdf_conj(a); }
 // multiply by -i (forward) or +i (inverse): sign = -1 gives -i*a
 template <int SIGN, typename C> __device__ __forceinline__ C mul_i(C a) {
   C r;
   if (SIGN < 0) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
   return r;
 }
+template <int SIGN> __device__ __forceinline__ cdf mul_i_cdf(cdf a) {
+  cdf r;
+  if (SIGN < 0) {
+    r.hi = make_float2(a.hi.y, -a.hi.x);
+    r.lo = make_float2(a.lo.y, -a.lo.x);
+  } else {
+    r.hi = make_float2(-a.hi.y, a.hi.x);
+    r.lo = make_float2(-a.lo.y, a.lo.x);
+  }
+  return r;
+}
+template <> __device__ __forceinline__ cdf mul_i<-1, cdf>(cdf a) { return mul_i_cdf<-1>(a); }
+template <> __device__ __forceinline__ cdf mul_i<1, cdf>(cdf a) { return mul_i_cdf<1>(a); }
 
 // ---------------------------------------------------------------- plan
 struct Plan {
@@ -285,6 +319,7 @@ cudaError_t scale_symbol_launch(double* lam64, float* lam32, size_t n, double s,
 template <typename To>
 cudaError_t line_symbol_launch(const Plan& p, const double* oct, To* dst, double s, cudaStream_t st);
 cudaError_t to_df_launch(const double* src, dfl* dst, size_t n, cudaStream_t st);
+cudaError_t to_cdf_launch(const double2* src, cdf* dst, size_t n, cudaStream_t st);
 // even DFT of the octant along every axis (used for both the operator and preconditioner symbols)
 cudaError_t symbol_axes_launch(const Plan& p, double* lam_oct, cudaStream_t s);
 

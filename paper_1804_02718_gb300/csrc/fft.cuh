@@ -70,18 +70,13 @@ __device__ __forceinline__ cplx<T> w16(int m) {
 // radix-2 combine of dft8 after the even (v[0,2,4,6]) and odd (v[1,3,5,7]) length-4 DFTs
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft8_combine(C* v) {
-  using T = decltype(C::x);
+  using T = real_t<C>;
   constexpr T r2 = T(0.70710678118654752440);
   C o1 = v[3], o2 = v[5], o3 = v[7];
-  // W8^1 = (1 + SIGN i)/sqrt2, W8^2 = SIGN i, W8^3 = (-1 + SIGN i)/sqrt2
-  C t1, t3;
-  if (SIGN < 0) {
-    t1 = mk<C>(r2 * (o1.x + o1.y), r2 * (o1.y - o1.x));
-    t3 = mk<C>(r2 * (o3.y - o3.x), -(r2 * (o3.y + o3.x)));
-  } else {
-    t1 = mk<C>(r2 * (o1.x - o1.y), r2 * (o1.y + o1.x));
-    t3 = mk<C>(-(r2 * (o3.x + o3.y)), r2 * (o3.x - o3.y));
-  }
+  // W8^1 = (1 + SIGN i)/sqrt2, W8^2 = SIGN i, W8^3 = (-1 + SIGN i)/sqrt2:
+  // W8^1 o = r2 (o + SIGN i o), W8^3 o = r2 (SIGN i o - o)
+  const C t1 = r2 * (o1 + mul_i<SIGN>(o1));
+  const C t3 = r2 * (mul_i<SIGN>(o3) - o3);
   C t2 = mul_i<SIGN>(o2);
   C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
   v[0] = e0 + o0; v[4] = e0 - o0;
@@ -101,7 +96,7 @@ __device__ __forceinline__ void dft8(C* v) {
 // twiddles by W16^{j2 k1} and the length-4 DFTs over j2 (second half of dft16)
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft16_tail(C* v) {
-  using T = decltype(C::x);
+  using T = real_t<C>;
   // v[4 k1 + j2] = A_{j2}[k1]; twiddle by W16^{j2 k1}
 #pragma unroll
   for (int k1 = 1; k1 < 4; ++k1)
