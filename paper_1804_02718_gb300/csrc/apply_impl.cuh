@@ -319,9 +319,9 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
 }
 
 // The cropped output of k_colmul: column blockIdx.x * TL + tid / G, elements lane + m G < n
-// (m < 8; n <= P/2), conjugated if CONJ.  The thread's column and lane are re-derived from
+// (m < 8; n <= P/2).  The thread's column and lane are re-derived from
 // the special registers here, not kept live across both transforms (that spilled).
-template <bool CONJ, typename C>
+template <typename C>
 __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int ncols, int n, size_t ld, int logP,
                                            int TL) {
   unsigned tid;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int i = lane + m * G;
-    if (i < n) FRLAP_GST(out + i, CONJ ? conjg(v[m]) : v[m]);
+    if (i < n) FRLAP_GST(out + i, v[m]);
   }
 }
 
@@ -380,34 +380,19 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
     const int kx = c >> map.logPy, ky = c & (map.Py - 1);
     return lam + ((size_t)kx * map.Hy1 + min(ky, map.Py - ky)) * map.Hz1;
   };
-  if constexpr (!std::is_same<T, dfl>::value) {
-    fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
-    const T* __restrict__ lrow = symbol_row();
+  // Forward transform with the zero-input first stage, multiply, inverse transform.  (Double-float
+  // once ran the inverse as conj(FFT(conj(.))) to execute a single copy of the stage code, which the
+  // instruction cache favoured; with its arithmetic in paired instructions the code is half the size
+  // and the two copies measured faster: 255^3 colmul 1.017 -> 0.992 ms.)
+  fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
+  const T* __restrict__ lrow = symbol_row();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int k = lane + m * G;
-      v[m] = ld_stream(&lrow[min(k, P - k)]) * v[m];
-    }
-    fft_regs<T, 1, false, REM>(v, buf, logP, lane, tw, logPtab, true);
-    store_line<false>(v, data, ncols, n, ld, logP, TL);
-  } else {
-    // Double-float: the inverse transform runs as conj(FFT(conj(.))), so both transforms
-    // execute one copy of the forward code.  The double-float stages are long enough that
-    // two copies miss in the instruction cache (measured 6% slower); for FP32 the loop
-    // costs more in register spills than it saves.
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-      fft_regs<T, -1, false, REM>(v, buf, logP, lane, tw, logPtab, pass == 1);
-      if (pass == 1) break;
-      const T* __restrict__ lrow = symbol_row();
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int k = lane + m * G;
-        v[m] = conjg(ld_stream(&lrow[min(k, P - k)]) * v[m]);
-      }
-    }
-    store_line<true>(v, data, ncols, n, ld, logP, TL);
+  for (int m = 0; m < 16; ++m) {
+    const int k = lane + m * G;
+    v[m] = ld_stream(&lrow[min(k, P - k)]) * v[m];
   }
+  fft_regs<T, 1, false, REM>(v, buf, logP, lane, tw, logPtab, true);
+  store_line(v, data, ncols, n, ld, logP, TL);
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
