@@ -349,6 +349,19 @@ frlap_status frlap_allen_cahn_batch(int nbatch, const frlap_plan* const* plans, 
  * time-out path.  The paper has no counterpart. */
 frlap_status frlap_set_loop_pass_limit(unsigned max_passes);
 
+/* The first apply stage of the FP64 and double-float engines stages its input rows in shared
+ * memory by bulk asynchronous copies and waits for each on an mbarrier.  Every such wait is
+ * bounded (about a second); a wait that gives up is counted, and that kernel returns without
+ * storing its remaining tiles (the call's result is then wrong).  frlap_async_wait_report returns
+ * in *timeouts the count since the previous report (summed over the engines, then reset).
+ * Synchronises the device.  A tool for tests and health checks; the paper has no counterpart. */
+frlap_status frlap_async_wait_report(unsigned long long* timeouts);
+/* The give-up path of that wait: one warp waits on an mbarrier phase that nothing completes (no
+ * arrival, no copy in flight) until the bound runs out (about a second) and records it.  Returns in
+ * *timeouts the waits that gave up (1 expected; the counter is reset before and after), leaving the
+ * context usable.  Synchronises the device.  For tests. */
+frlap_status frlap_async_wait_selftest(unsigned long long* timeouts);
+
 /* Bounds-checked builds (compiled with -DFRLAP_BOUNDS_CHECK; the package's build script makes
  * them as libfrlap_bc.so).  There every global load and store of the apply kernels is first tested
  * against the buffers its call registered (the call's vectors, workspace, symbol, twiddle tables and

@@ -14,5 +14,6 @@ from ._binding import (  # noqa: F401
     frlap_c_dalpha, frlap_coeffs, frlap_pcg_solve, frlap_precond_strang, frlap_precond_set_symbol, frlap_precond_apply,
     frlap_mlp_multiplier, frlap_learn_workspace_bytes, frlap_learn_grad, frlap_adam_step, frlap_cg_pairs, MLP_NPARAM,
     frlap_allen_cahn_batch, frlap_allen_cahn_batch_workspace_bytes, frlap_plan_create, frlap_plan_destroy,
-    frlap_workspace_bytes, frlap_set_loop_pass_limit, frlap_bounds_check_report, frlap_bounds_check_selftest, lib,
+    frlap_workspace_bytes, frlap_set_loop_pass_limit, frlap_bounds_check_report, frlap_bounds_check_selftest,
+    frlap_async_wait_report, frlap_async_wait_selftest, lib,
 )

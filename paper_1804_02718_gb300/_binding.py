@@ -67,6 +67,8 @@ _SIGS = {
     "frlap_bounds_check_report": (_I, [ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_ulonglong),
                                        ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_bounds_check_selftest": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "frlap_async_wait_report": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "frlap_async_wait_selftest": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
 
@@ -518,6 +520,20 @@ def frlap_bounds_check_report():
     _check(lib().frlap_bounds_check_report(ctypes.byref(en), ctypes.byref(v), ctypes.byref(f)),
            "frlap_bounds_check_report")
     return bool(en.value), int(v.value), int(f.value)
+
+
+def frlap_async_wait_report() -> int:
+    """Bounded asynchronous-copy waits of the apply kernels that gave up since the last report."""
+    n = ctypes.c_ulonglong(0)
+    _check(lib().frlap_async_wait_report(ctypes.byref(n)), "frlap_async_wait_report")
+    return int(n.value)
+
+
+def frlap_async_wait_selftest() -> int:
+    """Runs one bounded wait that nothing completes; returns the waits that gave up (1 expected)."""
+    n = ctypes.c_ulonglong(0)
+    _check(lib().frlap_async_wait_selftest(ctypes.byref(n)), "frlap_async_wait_selftest")
+    return int(n.value)
 
 
 def frlap_bounds_check_selftest() -> int:

@@ -87,6 +87,25 @@ extern "C" {
 
 const char* frlap_last_error(void) { return g_last_error.c_str(); }
 
+frlap_status frlap_async_wait_report(unsigned long long* timeouts) {
+  if (!timeouts) return fail(FRLAP_EINVAL, "timeouts is NULL");
+  unsigned long long total = 0ull;
+  cudaError_t (*collect[3])(unsigned long long*) = {wait_collect<float>, wait_collect<double>, wait_collect<dfl>};
+  for (auto fn : collect) {
+    unsigned long long c = 0ull;
+    FRLAP_CUDA_TRY(fn(&c));
+    total += c;
+  }
+  *timeouts = total;
+  return FRLAP_OK;
+}
+
+frlap_status frlap_async_wait_selftest(unsigned long long* timeouts) {
+  if (!timeouts) return fail(FRLAP_EINVAL, "timeouts is NULL");
+  FRLAP_CUDA_TRY(wait_selftest(timeouts));
+  return FRLAP_OK;
+}
+
 frlap_status frlap_bounds_check_report(int* enabled, unsigned long long* violations,
                                        unsigned long long* first_address) {
   if (!violations) return fail(FRLAP_EINVAL, "violations is NULL");

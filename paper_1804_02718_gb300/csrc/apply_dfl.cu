@@ -11,5 +11,6 @@ template cudaError_t apply_launch<dfl>(const Plan&, const double*, double*, void
 template cudaError_t autotune_engine<dfl>(Plan&, int, double*, double*, void*, cudaStream_t);
 
 template cudaError_t bc_collect<dfl>(unsigned long long*, unsigned long long*);
+template cudaError_t wait_collect<dfl>(unsigned long long*);
 
 }  // namespace frlap

@@ -11,5 +11,6 @@ template cudaError_t apply_launch<float>(const Plan&, const float*, float*, void
 template cudaError_t autotune_engine<float>(Plan&, int, float*, float*, void*, cudaStream_t);
 
 template cudaError_t bc_collect<float>(unsigned long long*, unsigned long long*);
+template cudaError_t wait_collect<float>(unsigned long long*);
 
 }  // namespace frlap

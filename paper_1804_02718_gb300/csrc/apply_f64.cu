@@ -39,6 +39,7 @@ template cudaError_t spectrum_inverse<double>(const Plan&, const double2*, const
 template cudaError_t autotune_engine<double>(Plan&, int, double*, double*, void*, cudaStream_t);
 
 template cudaError_t bc_collect<double>(unsigned long long*, unsigned long long*);
+template cudaError_t wait_collect<double>(unsigned long long*);
 
 #ifdef FRLAP_BOUNDS_CHECK
 static __device__ double g_bc_probe[16];
@@ -75,6 +76,26 @@ cudaError_t bc_selftest(unsigned long long* flagged) {
   *flagged = 0ull;
   return cudaErrorNotSupported;
 #endif
+}
+
+// The give-up path of the bounded mbarrier wait: one warp waits on a phase that nothing
+// completes (no arrival, no copy in flight), gives up after the wait's bound, and records it.
+__global__ void k_wait_selftest() {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1ull);
+}
+
+cudaError_t wait_selftest(unsigned long long* timeouts) {
+  unsigned long long c = 0;
+  cudaError_t e = wait_collect<double>(&c);  // reset
+  if (e != cudaSuccess) return e;
+  k_wait_selftest<<<1, 32>>>();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+  return wait_collect<double>(timeouts);
 }
 
 }  // namespace frlap

@@ -88,16 +88,64 @@ __device__ __forceinline__ void load_line(C* buf, const C* __restrict__ src, int
 // cp_async_wait_all(); a CTA barrier after it makes them visible to the other threads.
 template <int BYTES>
 __device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool pred) {
-  static_assert(BYTES == 8 || BYTES == 16, "cp_async_elem: 8 or 16 bytes");
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp_async_elem: 4, 8 or 16 bytes");
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int sz = pred ? BYTES : 0;
   if constexpr (BYTES == 16)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
-  else
+  else if constexpr (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---- bulk asynchronous copies completing on an mbarrier (the TMA unit's untiled copy)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned arrivals) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(arrivals) : "memory");
+  // the initialised barrier is visible to the asynchronous proxy that completes its transactions
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// One arrival that also raises the phase's expected transaction count by `bytes`.
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), `bytes` a multiple of 16; the
+// bytes count against bar's expected transactions.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Waits until the phase of `bar` with the given parity has completed.  Each try suspends the
+// thread for at most about kWaitHintNs; after kWaitTries tries (about a second) it gives up and
+// returns false.
+constexpr unsigned kWaitHintNs = 1000;
+constexpr int kWaitTries = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (int i = 0; i < kWaitTries; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(kWaitHintNs)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Waits that gave up (one copy per translation unit; wait_collect reads and resets it).
+static __device__ unsigned long long g_wait_timeouts = 0ull;
 
 // smem[l][spad(k)] = src[k * ld + line0 + l] for l < TL, k < total / TL (zero past nlines);
 // TL is a power of two dividing blockDim.x.  Thread t serves line t mod TL and rows
@@ -142,55 +190,44 @@ constexpr bool kFusedSplitR2C = !std::is_same<T, double>::value;
 template <typename T>
 constexpr bool kFusedSplitC2R = std::is_same<T, float>::value;
 
-template <typename T, int REM, int LOGL = 0>
-__global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
-                        size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
-                        const int* __restrict__ skip, Batch bt) {
-  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
-  if constexpr (LOGL > 0) {  // transform length fixed at compile time
-    logH = LOGL;
-    logP = LOGL + 1;
+// The first stage runs as the persistent k_r2c_pf (its input rows' loads overlap the previous
+// tile's arithmetic) in the FP64 and double-float engines for transforms of up to 1024 points,
+// as measured: double-float 255^3 r2c 235 -> 221 us per 2-vector launch, while the 2048-point
+// rows of 2047^2 keep k_r2c_T (71 against 77 us per vector).  FP32 keeps k_r2c_T everywhere: its
+// first stage is bound by shared-memory and store throughput, not load latency (persistent form
+// at 255^3: 44.7 -> 51.0 us per launch; at 2047^2: 21.3 -> 21.0 us per vector).  -1: never.
+template <typename T>
+constexpr int kR2CPersistentMaxLogH = std::is_same<T, float>::value ? -1 : 10;
+template <typename T>
+inline bool use_r2c_pf(int logH, const void* u) {
+  return logH <= kR2CPersistentMaxLogH<T> && (reinterpret_cast<uintptr_t>(u) % sizeof(io_t<T>)) == 0;
+}
+constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA
+
+// Multiprocessors of the current device (cached per device).
+inline int device_sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
   }
-  {
-    const size_t bi = blockIdx.y;
-    in += bi * bt.in;
-    out += bi * bt.out;
-    if (skip) skip += bi * bt.skip;
-  }
+  return cached[dev];
+}
+
+// The rest of the first stage for one tile of TL rows, once each thread holds its row's packed
+// samples in v (lane's q = lane + m G, see k_r2c_T): the half-length transform, the real-data
+// split and the transposed store of bins 0..H into out[k * ldo + line].
+template <typename T, int REM>
+__device__ __forceinline__ void r2c_tile(cplx<T>* v, cplx<T>* smem, cplx<T>* __restrict__ out, int nlines, size_t ldo,
+                                         int logH, int TL, const cplx<T>* __restrict__ tw, int logP, int line0, int l,
+                                         int lane) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* smem = reinterpret_cast<C*>(smem_raw);
-  if (skip && FRLAP_GLD(skip)) return;
   const int H = 1 << logH, G = H >> 4;
-  const int l = threadIdx.x / G, lane = threadIdx.x % G;
-  const int line0 = blockIdx.x * TL;
-  const int line = line0 + l;
-  const bool valid = line < nlines;
   const int LS = sline(H);
   C* buf = smem + (size_t)l * LS;
-  const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
-  // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
-  // for q >= H/2 (m >= 8): the upper half of the transform input.
-  // A row that starts on a pair boundary is read one pair (x[2q], x[2q+1]) per load.
-  using IO2 = io_pair<T>;
-  const bool pair_aligned = (reinterpret_cast<uintptr_t>(src) % sizeof(IO2)) == 0;
-  C v[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int q = lane + m * G;
-    io_t<T> re = io_t<T>(0), im = io_t<T>(0);
-    if (m < 8 && valid) {
-      if (pair_aligned && 2 * q + 1 < n) {
-        const IO2 t = FRLAP_GLD(reinterpret_cast<const IO2*>(src + 2 * q));
-        re = t.x;
-        im = t.y;
-      } else {
-        if (2 * q < n) re = FRLAP_GLD(src + 2 * q);
-        if (2 * q + 1 < n) im = FRLAP_GLD(src + 2 * q + 1);
-      }
-    }
-    v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
-  }
   fft_regs<T, -1, true, REM>(v, buf, logH, lane, tw, logP, false);
   line_sync<T>(logH);
 #pragma unroll
@@ -238,6 +275,180 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
 #pragma unroll 4
       for (; k <= H; k += G, gp += gstep) FRLAP_GST(gp, trow[spad(k)]);
     }
+  }
+}
+
+template <typename T, int REM, int LOGL = 0>
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
+                        size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
+                        const int* __restrict__ skip, Batch bt) {
+  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
+  if constexpr (LOGL > 0) {  // transform length fixed at compile time
+    logH = LOGL;
+    logP = LOGL + 1;
+  }
+  {
+    const size_t bi = blockIdx.y;
+    in += bi * bt.in;
+    out += bi * bt.out;
+    if (skip) skip += bi * bt.skip;
+  }
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && FRLAP_GLD(skip)) return;
+  const int H = 1 << logH, G = H >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int line0 = blockIdx.x * TL;
+  const int line = line0 + l;
+  const bool valid = line < nlines;
+  const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
+  // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
+  // for q >= H/2 (m >= 8): the upper half of the transform input.
+  // A row that starts on a pair boundary is read one pair (x[2q], x[2q+1]) per load.
+  using IO2 = io_pair<T>;
+  const bool pair_aligned = (reinterpret_cast<uintptr_t>(src) % sizeof(IO2)) == 0;
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int q = lane + m * G;
+    io_t<T> re = io_t<T>(0), im = io_t<T>(0);
+    if (m < 8 && valid) {
+      if (pair_aligned && 2 * q + 1 < n) {
+        const IO2 t = FRLAP_GLD(reinterpret_cast<const IO2*>(src + 2 * q));
+        re = t.x;
+        im = t.y;
+      } else {
+        if (2 * q < n) re = FRLAP_GLD(src + 2 * q);
+        if (2 * q + 1 < n) im = FRLAP_GLD(src + 2 * q + 1);
+      }
+    }
+    v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
+  }
+  r2c_tile<T, REM>(v, smem, out, nlines, ldo, logH, TL, tw, logP, line0, l, lane);
+}
+
+// Staging area of k_r2c_pf: the TL n elements of a tile's rows (E bytes each), shifted by the
+// tile start's offset from a 16-byte boundary (0..16/E - 1 elements), rounded up to 16 bytes;
+// then the mbarrier.
+template <int E>
+__host__ __device__ __forceinline__ int r2c_stage_elems(int TL, int n) {
+  constexpr int A = 16 / E;
+  return (TL * n + 2 * A - 2) / A * A;
+}
+// Byte offset of the staging area: after the TL transform lines, rounded up to 16 bytes (an
+// FP32 line of sline(H) complex elements is 8 bytes past a 16-byte boundary when TL is odd).
+template <typename T>
+__host__ __device__ __forceinline__ size_t r2c_stage_offset(int TL, int H) {
+  return ((size_t)TL * sline(H) * sizeof(cplx<T>) + 15) & ~(size_t)15;
+}
+template <typename T>
+size_t r2c_pf_smem_bytes(int TL, int H, int n) {
+  constexpr int E = (int)sizeof(io_t<T>);
+  return r2c_stage_offset<T>(TL, H) + (size_t)r2c_stage_elems<E>(TL, n) * E + 16;
+}
+
+// Persistent form of k_r2c_T for rows whose TL rows per tile are contiguous (row stride n).
+// CTA c takes the tiles t = c, c + gridDim.x, ... of all instances (t = instance * tiles +
+// tile).  A tile's rows reach a shared-memory staging area by one bulk asynchronous copy,
+// completing on an mbarrier, that thread 0 issues as soon as every thread holds the previous
+// tile's samples in registers: the copy runs during that tile's transform and transposed
+// store, so the loads' latency leaves the critical path.  The bulk copy moves the
+// 16-byte-aligned interior of the tile's span; the elements before and after it (a span that
+// does not start or end on a 16-byte boundary) are element-sized cp.async copies.
+template <typename T, int REM, int LOGL = 0>
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_pf(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n,
+                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
+                         const int* __restrict__ skip, Batch bt, int ninst) {
+  static_assert(LOGL == 0 || (LOGL & 3) == REM, "REM = LOGL mod 4");
+  if constexpr (LOGL > 0) {  // transform length fixed at compile time
+    logH = LOGL;
+    logP = LOGL + 1;
+  }
+  using C = cplx<T>;
+  using IO = io_t<T>;
+  constexpr int E = (int)sizeof(IO);
+  constexpr int A = 16 / E;  // elements per 16 bytes
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  const int H = 1 << logH, G = H >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  IO* stage = reinterpret_cast<IO*>(smem_raw + r2c_stage_offset<T>(TL, H));  // 16-byte aligned
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage + r2c_stage_elems<E>(TL, n));
+  const int ntiles = (nlines + TL - 1) / TL;
+  const long long total = (long long)ntiles * ninst;
+  // tile t: its instance, first row, and the address of its first element
+  auto tile_src = [&](long long t, int& b, int& line0) {
+    b = (int)(t / ntiles);
+    line0 = (int)(t - (long long)b * ntiles) * TL;
+    return in + (size_t)b * bt.in + (size_t)line0 * n;
+  };
+  // thread 0: start the copies of tile t into the staging area (element j at stage[j + off])
+  auto issue = [&](long long t) {
+    int b, line0;
+    const IO* src = tile_src(t, b, line0);
+    if (skip && FRLAP_GLD(skip + (size_t)b * bt.skip)) {  // a skipped instance: nothing to copy
+      mbar_arrive_tx(bar, 0u);
+      return;
+    }
+    const int cnt = min(TL, nlines - line0) * n;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    const int off = (int)((a & 15) / E);
+    const uintptr_t a1 = (a + 15) & ~(uintptr_t)15, e0 = (a + (uintptr_t)cnt * E) & ~(uintptr_t)15;
+    unsigned bytes = e0 > a1 ? (unsigned)(e0 - a1) : 0u;
+    const int h = min((int)((a1 - a) / E), cnt);                         // elements before the bulk part
+    const int tl0 = bytes ? (int)((e0 - a) / E) : h;                     // first element after it
+#ifdef FRLAP_BOUNDS_CHECK
+    if (bytes && !bc_ok(reinterpret_cast<const void*>(a1), bytes)) bytes = 0u;
+#endif
+    for (int j = 0; j < h; ++j) cp_async_elem<E>(stage + j + off, src + j, FRLAP_GOK(src + j));
+    for (int j = tl0; j < cnt; ++j) cp_async_elem<E>(stage + j + off, src + j, FRLAP_GOK(src + j));
+    mbar_arrive_tx(bar, bytes);
+    if (bytes) bulk_g2s(stage + h + off, reinterpret_cast<const void*>(a1), bytes, bar);
+  };
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  long long t = blockIdx.x;
+  if (threadIdx.x == 0 && t < total) issue(t);
+  unsigned parity = 0;
+  for (; t < total; t += gridDim.x) {
+    cp_async_wait_all();  // thread 0's element copies of this tile
+    const bool ok = mbar_wait(bar, parity);
+    parity ^= 1;
+    if (!__syncthreads_and(ok)) {  // the staging copy did not complete in time: record and stop
+      if (threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1ull);
+      return;
+    }
+    int b, line0;
+    const IO* src = tile_src(t, b, line0);
+    const bool skipped = skip && FRLAP_GLD(skip + (size_t)b * bt.skip);
+    const int off = (int)((reinterpret_cast<uintptr_t>(src) & 15) / E);
+    const bool valid = line0 + l < nlines;
+    // packed samples z[q] = x[2q] + i x[2q+1] of row line0 + l, as in k_r2c_T
+    const IO* row = stage + (size_t)l * n + off;
+    const bool pair_aligned = ((l * n + off) & 1) == 0;
+    using IO2 = io_pair<T>;
+    C v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = lane + m * G;
+      IO re = IO(0), im = IO(0);
+      if (m < 8 && valid) {
+        if (pair_aligned && 2 * q + 1 < n) {
+          const IO2 p2 = *reinterpret_cast<const IO2*>(row + 2 * q);
+          re = p2.x;
+          im = p2.y;
+        } else {
+          if (2 * q < n) re = row[2 * q];
+          if (2 * q + 1 < n) im = row[2 * q + 1];
+        }
+      }
+      v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
+    }
+    __syncthreads();  // the staging area is free: start the next tile's copy
+    if (threadIdx.x == 0 && t + gridDim.x < total) issue(t + gridDim.x);
+    if (!skipped)
+      r2c_tile<T, REM>(v, smem, out + (size_t)b * bt.out, nlines, ldo, logH, TL, tw, logP, line0, l, lane);
   }
 }
 
@@ -665,6 +876,31 @@ static const T* symbol_table(const Plan& p) {
   else return p.lamdf;
 }
 
+// The first stage as the persistent k_r2c_pf: as many CTAs as fit on the device at once, or one
+// per tile if there are fewer tiles.
+template <typename T>
+cudaError_t launch_r2c_pf(const io_t<T>* u, cplx<T>* S1, int nrows, int nx, size_t ld1, int logH, int tl, size_t sm,
+                          const cplx<T>* tw, const int* skip, Batch b_in, int B, cudaStream_t s) {
+  if constexpr (kR2CPersistentMaxLogH<T> < 0) {
+    return cudaErrorNotSupported;
+  } else {
+    const int G = 1 << (logH - 4);
+    return with_line_shape<T, std::is_same<T, float>::value>(logH, [&](auto tag) {
+      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+      cudaError_t e = set_smem(k_r2c_pf<T, REM, LL>, sm);
+      if (e != cudaSuccess) return e;
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_r2c_pf<T, REM, LL>, tl * G, sm);
+      if (e != cudaSuccess) return e;
+      const long long tiles = (long long)((nrows + tl - 1) / tl) * B;
+      const long long slots = (long long)(occ > 0 ? occ : 1) * device_sm_count();
+      const int grid = (int)(tiles < slots ? tiles : slots);
+      k_r2c_pf<T, REM, LL><<<grid, tl * G, sm, s>>>(u, S1, nrows, nx, ld1, logH, tl, tw, logH + 1, skip, b_in, B);
+      return cudaGetLastError();
+    });
+  }
+}
+
 template <typename T>
 static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
                                   cudaStream_t s, const int* skip, int skip_stride, cudaEvent_t const* ev,
@@ -724,7 +960,17 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   b_out.skip = skip_stride;
 
   // ---- stage 1: rows of u -> S1[kx][row]
-  {
+  if (use_r2c_pf<T>(logPx - 1, u)) {
+    const int G = Hx >> 4;
+    const int q = G < 32 ? 32 / G : 1;
+    int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
+    while (tl > q && r2c_pf_smem_bytes<T>(tl, Hx, nx) > kMaxSmem) tl /= 2;
+    const size_t sm = r2c_pf_smem_bytes<T>(tl, Hx, nx);
+    cudaError_t e;
+    if ((e = mark()) != cudaSuccess) return e;
+    e = launch_r2c_pf<T>(u, S1, nrows, nx, ld1, logPx - 1, tl, sm, tw[0], skip, b_in, B, s);
+    if (e != cudaSuccess) return e;
+  } else {
     const int G = Hx >> 4;
     const int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
@@ -1035,7 +1281,9 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
     int best = 0;
     float best_ms = 0.f;
     for (int t = 1; t <= 64 && e == cudaSuccess; t *= 2) {
-      if (t * G > kMaxCta<T> || (size_t)t * sline(L) * eb > 227 * 1024) break;
+      const size_t smem = (st == 0 && use_r2c_pf<T>(p.logP[0] - 1, u)) ? r2c_pf_smem_bytes<T>(t, L, p.n[0])
+                                                         : (size_t)t * sline(L) * eb;
+      if (t * G > kMaxCta<T> || smem > kMaxSmem) break;
       if (G < 32 && t < 32 / G) continue;
       p.tl_tuned[eng][st] = t;
       float ms = 0.f;
@@ -1054,6 +1302,17 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
     p.tl_tuned[eng][st] = best;
   }
   for (int i = 0; i <= ns; ++i) cudaEventDestroy(ev[i]);
+  return e;
+}
+
+template <typename T>
+cudaError_t wait_collect(unsigned long long* count) {
+  unsigned long long c = 0ull;
+  cudaError_t e = cudaMemcpyFromSymbol(&c, g_wait_timeouts, sizeof(c));
+  if (e != cudaSuccess) return e;
+  const unsigned long long z = 0ull;
+  e = cudaMemcpyToSymbol(g_wait_timeouts, &z, sizeof(z));
+  *count = c;
   return e;
 }
 

@@ -267,6 +267,12 @@ struct Plan {
   int tl_tuned[3][5] = {};
 };
 
+// Bounded waits of the apply kernels on their asynchronous copies (mbarrier phases) that gave up
+// since the last call, per engine's translation unit (the counter is reset).  A kernel whose wait
+// gives up records it and returns without storing that tile's results.
+template <typename T>
+cudaError_t wait_collect(unsigned long long* count);
+
 // Bounds-checked builds: accesses outside the registered ranges since the last call, summed per
 // engine's translation unit (the counters are reset); ordinary builds report zero.
 template <typename T>
@@ -274,6 +280,8 @@ cudaError_t bc_collect(unsigned long long* count, unsigned long long* first);
 // Bounds-checked builds: registers one 8-double range and probes 8 loads inside it and 5 just past
 // it (memory the library owns, so the probes are safe even unchecked); *flagged = accesses flagged.
 cudaError_t bc_selftest(unsigned long long* flagged);
+// Runs one bounded mbarrier wait that nothing completes; *timeouts = waits that gave up (1 expected).
+cudaError_t wait_selftest(unsigned long long* timeouts);
 
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
 // T = compute type (float, double or dfl); vectors are io_t<T>, symbol overrides are T

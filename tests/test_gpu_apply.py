@@ -270,10 +270,13 @@ def test_apply_host_matches_batch(frlap, d, Ns, prec, pinned):
     assert torch.equal(Y1, Y)
 
 
-@pytest.mark.parametrize("d,Ns,prec", [(2, (256, 192), 3), (3, (32, 24, 40), 2), (2, (128, 128), 1)])
+@pytest.mark.parametrize("d,Ns,prec", [(2, (256, 192), 3), (3, (32, 24, 40), 2), (2, (128, 128), 1),
+                                       (2, (600, 40), 1), (2, (600, 40), 3)])
 def test_autotune_keeps_results(frlap, d, Ns, prec):
     """frlap_plan_autotune picks a power-of-two lines-per-CTA count for every stage of each engine the
-    plan uses; the launch shape does not change the arithmetic, so applies stay bit for bit the same."""
+    plan uses; the launch shape does not change the arithmetic, so applies stay bit for bit the same.
+    The (600, 40) cases reach one line per CTA in the first stage's search (1024-point rows, 64 lanes
+    a line), where an FP32 CTA's transform lines end 8 bytes past a 16-byte boundary."""
     h = 2.0 / max(Ns)
     plan = frlap.Plan(d, 1.4, h, Ns, prec=prec)
     dt = torch.float32 if prec == 1 else torch.float64
@@ -288,3 +291,43 @@ def test_autotune_keeps_results(frlap, d, Ns, prec):
     assert torch.equal(frlap.frlap_apply_batch(plan, U), Y0)
     if y32 is not None:
         assert torch.equal(frlap.frlap_apply_f32(plan, U[0].float().contiguous()), y32)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-12)])
+def test_persistent_first_stage_many_tiles(frlap, prec, tol):
+    """The persistent first stage of the FP64 and double-float engines (rows staged by bulk
+    asynchronous copies): odd row length (tiles alternate between 16-byte-aligned and 8-byte-offset
+    starts, so the edge elements take the 8-byte path), an odd vector length (instances alternate
+    too), and more tiles than resident CTAs (each CTA walks several tiles).  Every instance matches
+    the oracle, equals the one-vector apply bit for bit, and no staging wait gave up."""
+    Ns = (130, 100, 90)
+    h = 2.0 / max(Ns)
+    a_ref, c = _oracle(3, 1.2, h, Ns)
+    us = [inp.normal_field(Ns, seed=80 + b) for b in range(3)]
+    op = fast.FastOperator(a_ref, c, us[0].shape)
+    plan = frlap.Plan(3, 1.2, h, Ns, prec=prec)
+    frlap.frlap_async_wait_report()  # reset
+    U = _t(np.stack(us))
+    Y = frlap.frlap_apply_batch(plan, U)
+    for b, u in enumerate(us):
+        y = Y[b].cpu().numpy()
+        assert np.linalg.norm(y - op(u)) <= tol * op.lam_max * np.linalg.norm(u), b
+        assert torch.equal(Y[b], frlap.frlap_apply(plan, U[b].clone()))
+    assert frlap.frlap_async_wait_report() == 0
+
+
+def test_bounded_wait_gives_up_and_context_survives(frlap):
+    """The give-up path of the apply kernels' bounded mbarrier wait: a wait on a phase that nothing
+    completes runs out (about a second), is counted, and leaves the context usable."""
+    frlap.frlap_async_wait_report()  # reset
+    assert frlap.frlap_async_wait_selftest() == 1
+    assert frlap.frlap_async_wait_report() == 0
+    Ns = (40, 30, 20)
+    h = 2.0 / max(Ns)
+    a_ref, c = _oracle(3, 0.9, h, Ns)
+    u = inp.normal_field(Ns, seed=91)
+    op = fast.FastOperator(a_ref, c, u.shape)
+    plan = frlap.Plan(3, 0.9, h, Ns, prec=frlap.FRLAP_DF64)
+    y = frlap.frlap_apply(plan, _t(u)).cpu().numpy()
+    assert np.linalg.norm(y - op(u)) <= 1e-12 * op.lam_max * np.linalg.norm(u)
+    assert frlap.frlap_async_wait_report() == 0
