@@ -66,11 +66,12 @@ MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1282.2e6, (2, "colmul", "f32"): 593.9
                     (3, "colmul", "df64"): 2435.9e6, (3, "colmul", "f32"): 1219.0e6}
 
 
-def measure_fp32_fma_tflops(torch):
+def measure_fp32_fma_tflops(torch, tf32=False):
     """The FP32 FMA-pipe rate of this GPU, measured: cuBLAS SGEMM (TF32 off, so it runs on the CUDA
-    cores' FMA pipes) of 8192^3, best of 5, 2 n^3 flops each."""
+    cores' FMA pipes) of 8192^3, best of 5, 2 n^3 flops each.  With tf32=True the same GEMM on the
+    tensor cores in TF32 (the rate a split-TF32 tensor-core DFT stage would run at)."""
     prev = torch.backends.cuda.matmul.allow_tf32
-    torch.backends.cuda.matmul.allow_tf32 = False
+    torch.backends.cuda.matmul.allow_tf32 = bool(tf32)
     try:
         n = 8192
         a = torch.randn(n, n, device="cuda")
@@ -526,6 +527,18 @@ def run_extras(fl, torch, args):
                      "frac_of_hbm_model": sum(sb) / (ms / 1e3) / 1e9 / hbm,
                      "kernels_ms": [round(v, 5) for v in st]}
         del plan, U, Y, work
+        torch.cuda.empty_cache()
+    out["tf32_gemm_tflops_measured"] = round(measure_fp32_fma_tflops(torch, tf32=True), 1)
+    # plan creation (coefficients, symbol, twiddles; host wall time, synchronised), after a small warm-up plan
+    fl.Plan(3, 1.0, 2.0 / 16, (16, 16, 16), prec=fl.FRLAP_DF64)
+    torch.cuda.synchronize()
+    for name, d, N in (("plan_create_s_2047^2", 2, NGRID), ("plan_create_s_255^3", 3, 256),
+                       ("plan_create_s_511^3", 3, 512)):
+        t0 = time.perf_counter()
+        plan = fl.Plan(d, ALPHA if d == 2 else 1.0, 2.0 / N, (N,) * d, prec=fl.FRLAP_DF64)
+        torch.cuda.synchronize()
+        out[name] = round(time.perf_counter() - t0, 4)
+        del plan
         torch.cuda.empty_cache()
     # cuFFT (torch.fft) on the same embedding, as a timed comparison (not on the product path)
     for name, prec in (("cufft_2047^2_f64", fl.FRLAP_F64), ("cufft_2047^2_f32", fl.FRLAP_F32)):

@@ -84,8 +84,12 @@ __global__ void k_element_weights(double* w, int N, double p, const double* __re
     k[r] = (int)(rest % N);
     rest /= N;
   }
-  int dist = k[0];
-  for (int r = 1; r < D; ++r) dist = max(dist, k[r]);
+  // |xi|^-p and the tensor rule are symmetric under permutations of the coordinates, so
+  // w_k = w_{sorted k}: only elements with k[0] <= k[1] (<= k[2]) are integrated here, and
+  // k_fill_permuted copies them to the others (2D: half, 3D: a sixth of the work).
+  for (int r = 0; r + 1 < D; ++r)
+    if (k[r] > k[r + 1]) return;
+  int dist = k[D - 1];
   if (dist == 0) return;  // origin element: k_pyramid
   const int qi = q_index(dist);
   int off[kNumQ + 1] = {0, 4, 9, 17, 31, 51, 83};
@@ -122,6 +126,38 @@ __global__ void k_element_weights(double* w, int N, double p, const double* __re
     }
   }
   w[e] = acc;
+}
+
+// w[e] = w[index of the sorted coordinates of element e], for every element whose coordinates are
+// not in ascending order (k_element_weights integrated only the sorted ones)
+template <int D>
+__global__ void k_fill_permuted(double* w, int N) {
+  const size_t total = (D == 2) ? (size_t)N * N : (size_t)N * N * N;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int k[3] = {0, 0, 0};
+  size_t rest = e;
+  for (int r = 0; r < D; ++r) {
+    k[r] = (int)(rest % N);
+    rest /= N;
+  }
+  bool sorted = true;
+  for (int r = 0; r + 1 < D; ++r) sorted = sorted && k[r] <= k[r + 1];
+  if (sorted) return;
+  // sort ascending (at most three entries)
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j + 1 < D - i; ++j)
+      if (k[j] > k[j + 1]) {
+        const int t = k[j];
+        k[j] = k[j + 1];
+        k[j + 1] = t;
+      }
+  size_t src = 0, stride = 1;
+  for (int r = 0; r < D; ++r) {
+    src += (size_t)k[r] * stride;
+    stride *= N;
+  }
+  w[e] = w[src];
 }
 
 // pyramid reductions: out[0] = w_0 = d/(d-p) int_{[0,1]^(d-1)} (1+|s|^2)^(-p/2),
@@ -339,8 +375,13 @@ cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int N, do
   k_gauss<<<1, 128, 0, s>>>(gn, gw);
   const int bs = 256;
   const unsigned gridw = (unsigned)((nel + bs - 1) / bs);
-  if (d == 2) k_element_weights<2><<<gridw, bs, 0, s>>>(w, N, p, gn, gw);
-  else k_element_weights<3><<<gridw, bs, 0, s>>>(w, N, p, gn, gw);
+  if (d == 2) {
+    k_element_weights<2><<<gridw, bs, 0, s>>>(w, N, p, gn, gw);
+    k_fill_permuted<2><<<gridw, bs, 0, s>>>(w, N);
+  } else {
+    k_element_weights<3><<<gridw, bs, 0, s>>>(w, N, p, gn, gw);
+    k_fill_permuted<3><<<gridw, bs, 0, s>>>(w, N);
+  }
   k_pyramid<<<1, 256, 0, s>>>(d, p, alpha, N, gn, gw, pyr, w);
   if (d == 2) k_assemble<2><<<nparts, 256, 0, s>>>(w, N, gamma, hscale, pyr, coef, partial);
   else k_assemble<3><<<nparts, 256, 0, s>>>(w, N, gamma, hscale, pyr, coef, partial);

@@ -172,8 +172,23 @@ __device__ __forceinline__ void twiddles16(cplx<T>* w, const cplx<T>* __restrict
                                            int logPtab) {
   const int Ns = 1 << logNs;
   const cplx<T>* st = tw + (1 << logPtab) + 15 * (Ns - 1) - Ns + k;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: six loads, W^{rk} for r = 1, 2, 3, 4, 8, 12, and W^{(r0 + 4 r1) k} = W^{r0 k} W^{4 r1 k}
+    // for the nine others (one rounded product of two rounded entries each); the global loads
+    // are the first and last FP32 stages' largest L1 cost
 #pragma unroll
-  for (int r = 1; r < 16; ++r) w[r] = FRLAP_GLD(st + r * Ns);
+    for (int r = 1; r < 4; ++r) {
+      w[r] = FRLAP_GLD(st + r * Ns);
+      w[4 * r] = FRLAP_GLD(st + 4 * r * Ns);
+    }
+#pragma unroll
+    for (int r1 = 1; r1 < 4; ++r1)
+#pragma unroll
+      for (int r0 = 1; r0 < 4; ++r0) w[r0 + 4 * r1] = cmul(w[r0], w[4 * r1]);
+  } else {
+#pragma unroll
+    for (int r = 1; r < 16; ++r) w[r] = FRLAP_GLD(st + r * Ns);
+  }
 }
 
 // Barrier between the read and write halves of a stage.  The G = L/16 lanes of a line
