@@ -249,11 +249,26 @@ __device__ __forceinline__ void r2c_tile(cplx<T>* v, cplx<T>* smem, cplx<T>* __r
     if (lt_ok) {
       int k = (int)threadIdx.x >> logTL;
       C* gp = out + (size_t)k * ldo + line0 + lt;
+      if constexpr (std::is_same<T, float>::value) {
+        // FP32: the thread's bins are k0 + j G, and W^{k0 + j G} = W^{k0} W_32^j (one table load)
+        const C w0 = FRLAP_GLD(tw + k);
+#pragma unroll
+        for (int j = 0; j <= 16; ++j) {
+          const int kj = k + j * G;
+          if (kj <= H) {
+            const C a = trow[spad(kj & (H - 1))];
+            const C b = conjg(trow[spad((H - kj) & (H - 1))]);
+            const C wk = j == 0 ? w0 : cmul(w0, make_float2(c_w32.re[j], c_w32.im[j]));
+            FRLAP_GST(gp + (size_t)j * gstep, halve(a + b) + cmul(wk, halve(mul_i<-1>(a - b))));
+          }
+        }
+      } else {
 #pragma unroll 4
-      for (; k <= H; k += G, gp += gstep) {
-        const C a = trow[spad(k & (H - 1))];
-        const C b = conjg(trow[spad((H - k) & (H - 1))]);
-        FRLAP_GST(gp, halve(a + b) + cmul(FRLAP_GLD(tw + k), halve(mul_i<-1>(a - b))));
+        for (; k <= H; k += G, gp += gstep) {
+          const C a = trow[spad(k & (H - 1))];
+          const C b = conjg(trow[spad((H - k) & (H - 1))]);
+          FRLAP_GST(gp, halve(a + b) + cmul(FRLAP_GLD(tw + k), halve(mul_i<-1>(a - b))));
+        }
       }
     }
   } else {
@@ -484,13 +499,16 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
   // the unnormalised inverse half-length transform gives P (y[2j] + i y[2j+1])
   C v[16];
   if constexpr (kFusedSplitC2R<T>) {
-    // straight into the registers the transform starts from (one product per element)
+    // straight into the registers the transform starts from (one product per element); the
+    // twiddle of bin lane + m G is W^{lane} W_32^m (one table load per thread)
+    const C w0 = FRLAP_GLD(tw + lane);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int k = lane + m * G;
       const C xk = buf[spad(k)];
       const C b = conjg(buf[spad(H - k)]);
-      v[m] = (xk + b) + mul_i<1>(cmulc(xk - b, FRLAP_GLD(tw + k)));
+      const C wk = m == 0 ? w0 : cmul(w0, mk<C>(c_w32.re[m], c_w32.im[m]));
+      v[m] = (xk + b) + mul_i<1>(cmulc(xk - b, wk));
     }
   } else {
     // in place, one product per pair; the partner is Z[H-k] = conj(A - i T)

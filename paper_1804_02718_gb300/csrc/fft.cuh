@@ -29,6 +29,35 @@ __host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 // Slots per line for logical indices 0..L (L itself is used by the real-data transforms).
 __host__ __device__ __forceinline__ int sline(int L) { return L + (L >> 4) + 1; }
 
+// cos x (sine = false) or sin x (sine = true) for |x| <= pi by the Taylor series, at compile
+// time: 40 terms leave a remainder far below double rounding.
+constexpr double taylor_cs(double x, bool sine) {
+  double term = sine ? x : 1.0, sum = term;
+  for (int k = 1; k < 40; ++k) {
+    const double a = sine ? 2.0 * k : 2.0 * k - 1.0, b = sine ? 2.0 * k + 1.0 : 2.0 * k;
+    term *= -x * x / (a * b);
+    sum += term;
+  }
+  return sum;
+}
+// W_32^j = exp(-2 pi i j / 32), j = 0..16, rounded to FP32 (the twiddle tables' sign convention).
+// With G = P/32 lanes per line of a P-point table, W_P^{k + j G} = W_P^k W_32^j: the real-data
+// splits of the FP32 first and last stages form their per-bin twiddles from one table entry per
+// thread and these constants, which the unrolled loops read as constant-bank operands.
+struct W32Table {
+  float re[17], im[17];
+};
+constexpr W32Table make_w32_table() {
+  W32Table t{};
+  for (int j = 0; j <= 16; ++j) {
+    const double x = 3.14159265358979323846 * j / 16.0;
+    t.re[j] = (float)taylor_cs(x, false);
+    t.im[j] = (float)-taylor_cs(x, true);
+  }
+  return t;
+}
+static __constant__ W32Table c_w32 = make_w32_table();
+
 
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft2(C& a, C& b) {
