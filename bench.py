@@ -44,7 +44,9 @@ NGRID = 2048
 BATCH = 8  # vectors per step of the 2D workload
 BATCH_2D = BATCH
 NGRID_3D, ALPHA_3D, BATCH_3D = 256, 1.0, 2
-E2E_CHUNK = 1  # vectors per chunk of the host-buffer pipeline (1, 2, 4, 8 measured 6.9, 6.6, 5.8, 4.7 G unknowns/s)
+# vectors per chunk of the host-buffer pipeline, per engine, as measured at 2047^2 (chunks of 1, 2, 4, 8):
+# double-float 10.3, 9.6, 8.4, 6.3 G unknowns/s; FP32 16.9, 24.7, 21.7, 17.1 (copies ~200 GB/s each way)
+E2E_CHUNK = {"df64": 1, "f64": 1, "f32": 2}
 METRIC = "apply unknowns/s & %HBM peak; PCG time to 1e-10 of FP64 sol vs plain FP64 CG"
 UNIT = "unknowns/s"
 
@@ -437,25 +439,25 @@ def main():
         # copies in and out overlapped with the applies of the neighbouring chunks
         Uh = U.cpu().pin_memory()
         Yh = torch.empty_like(Uh).pin_memory()
-        hwork = fl.frlap_apply_host_workspace_bytes(plan, E2E_CHUNK)
+        hwork = fl.frlap_apply_host_workspace_bytes(plan, E2E_CHUNK[args.prec])
         hraw = torch.empty(hwork + 256, dtype=torch.uint8, device="cuda")
         hoff = (-hraw.data_ptr()) % 256
         hw = hraw[hoff:hoff + hwork]
         ksteps = max(2, min(args.steps, 10))
         for _ in range(2):
-            fl.frlap_apply_host(plan, Uh, Yh, chunk=E2E_CHUNK, work=hw)
+            fl.frlap_apply_host(plan, Uh, Yh, chunk=E2E_CHUNK[args.prec], work=hw)
         torch.cuda.synchronize()
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(ksteps):
-            fl.frlap_apply_host(plan, Uh, Yh, chunk=E2E_CHUNK, work=hw)
+            fl.frlap_apply_host(plan, Uh, Yh, chunk=E2E_CHUNK[args.prec], work=hw)
         z.record()
         torch.cuda.synchronize()
         ems = a.elapsed_time(z)
         del hraw, hw
         e2e = {"value": world * ksteps * BATCH * M / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": BATCH * M * eb, "d2h_bytes_per_step": BATCH * M * eb, "steps": ksteps,
-               "call": f"frlap_apply_host (pinned host buffers, chunks of {E2E_CHUNK})"}
+               "call": f"frlap_apply_host (pinned host buffers, chunks of {E2E_CHUNK[args.prec]})"}
 
     pcg = None
     if not args.no_pcg and rank == 0:

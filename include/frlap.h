@@ -166,7 +166,8 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
  * streams while chunk i is applied (the two slots compute on `stream` and on an
  * internal stream, so consecutive chunks' kernels may overlap).  For the copies to overlap,
  * h_u and h_y must be pinned (page-locked); pageable buffers give the same
- * result with serialised copies.  d_work: frlap_apply_host_workspace_bytes(plan,
+ * result with serialised copies.  h_u and h_y must not overlap.  d_work:
+ * frlap_apply_host_workspace_bytes(plan,
  * chunk) bytes, 256-byte aligned.  Synchronises `stream`: h_y is complete on
  * return.  1 <= chunk <= 65535, nbatch >= 1, else FRLAP_EINVAL. */
 /* Autotuner of the apply's launch shapes.  For each stage of the apply, and for each

@@ -435,6 +435,7 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   if (rc != FRLAP_OK) return rc;
   const size_t eb = plan->prec == FRLAP_F32 ? 4 : 8;
   const size_t vbytes = plan->M * eb;
+  if (ranges_overlap(h_u, h_y, (size_t)nbatch * vbytes)) return fail(FRLAP_EINVAL, "h_u and h_y must not overlap");
   unsigned char* w = reinterpret_cast<unsigned char*>(d_work);
   unsigned char* du[2];
   unsigned char* dy[2];

@@ -268,6 +268,14 @@ def test_apply_host_matches_batch(frlap, d, Ns, prec, pinned):
     assert torch.equal(Y, Yd.cpu())
     Y1 = frlap.frlap_apply_host(plan, U, chunk=8)  # one chunk holding the whole batch
     assert torch.equal(Y1, Y)
+    # overlapping host ranges are refused before anything is enqueued
+    import ctypes
+    lib = frlap.lib()
+    nbytes = frlap.frlap_apply_host_workspace_bytes(plan, 2)
+    work = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    w = ctypes.c_void_p(work.data_ptr() + (-work.data_ptr()) % 256)
+    p = ctypes.c_void_p
+    assert lib.frlap_apply_host(plan.handle, 5, 2, p(U.data_ptr()), p(U[1].data_ptr()), w, None) == 1
 
 
 @pytest.mark.parametrize("d,Ns,prec", [(2, (256, 192), 3), (3, (32, 24, 40), 2), (2, (128, 128), 1),
