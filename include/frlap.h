@@ -12,7 +12,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - d is 2 or 3.  N[r] (r = 0 is x, 1 is y, 2 is z) is the number of mesh
- *    intervals along axis r, 2 <= N[r] <= 4096 (2D) or 1024 (3D), so there are n_r = N[r] - 1 interior
+ *    intervals along axis r, 2 <= N[r] <= 8192 (2D) or 1024 (3D), so there are n_r = N[r] - 1 interior
  *    unknowns along axis r.  The grid vector u is stored x fastest: a C-order
  *    array [n_z][n_y][n_x] (3D) or [n_y][n_x] (2D), as in eq. product / A3D.
  *    h > 0 is the mesh size; the coefficient table uses N_max = max_r N[r]
@@ -306,7 +306,8 @@ size_t frlap_learn_workspace_bytes(const frlap_plan* plan, int B);
  * scaled, so the loss is scale-free):
  *   L = mean_b [1 - (r_b.z_b)^2 / ((z_b.A z_b)(r_b.e_b))],  r_b.e_b = ||e_b||_A^2.
  * d_grad (FRLAP_MLP_NPARAM floats, overwritten), d_loss (one double on the
- * device).  FP64 spectra, FP32 network. */
+ * device).  FP64 spectra, FP32 network.  Plans with an embedding of more than
+ * 8192 points along an axis (2D N[r] > 4096) are refused with FRLAP_EINVAL. */
 frlap_status frlap_learn_grad(const frlap_plan* plan, const float* d_params, const double* d_r, const double* d_e,
                               int B, float* d_grad, double* d_loss, void* d_work, void* stream);
 

@@ -66,10 +66,11 @@ static frlap_status check_params(int d, double alpha, double gamma, double h, co
   if (!(gamma > alpha && gamma <= 2.0)) return fail(FRLAP_EINVAL, "gamma must lie in (alpha, 2]");
   if (!(h > 0.0) || !isfinite(h)) return fail(FRLAP_EINVAL, "h must be positive and finite");
   if (!N) return fail(FRLAP_EINVAL, "N is NULL");
-  // 2D: N <= 4096 (FFT lines of up to 8192 points); 3D: N <= 1024
-  const int Nlim = (d == 2) ? 4096 : 1024;
+  // 2D: N <= 8192 (embeddings of up to 16384 points; the 16384-point middle stage runs as two
+  // 8192-point halves, the rows as 8192-point half-length transforms); 3D: N <= 1024
+  const int Nlim = (d == 2) ? 8192 : 1024;
   for (int r = 0; r < d; ++r)
-    if (N[r] < 2 || N[r] > Nlim) return fail(FRLAP_EINVAL, "each N[r] must lie in [2, 4096] (2D) or [2, 1024] (3D)");
+    if (N[r] < 2 || N[r] > Nlim) return fail(FRLAP_EINVAL, "each N[r] must lie in [2, 8192] (2D) or [2, 1024] (3D)");
   return FRLAP_OK;
 }
 
@@ -228,7 +229,9 @@ frlap_status frlap_plan_create(int d, double alpha, double gamma, double h, cons
   const int Hx1 = p->P[0] / 2 + 1;
   const size_t nrows = (size_t)p->n[1] * (d == 3 ? p->n[2] : 1);
   p->s1_elems = (size_t)Hx1 * nrows;
-  p->s2_elems = (d == 3) ? (size_t)Hx1 * p->P[1] * p->n[2] : 0;
+  // 3D: the transposed y spectra; 2D with a 16384-point y embedding: the even half of the split
+  // middle stage (same layout as S1)
+  p->s2_elems = (d == 3) ? (size_t)Hx1 * p->P[1] * p->n[2] : (p->P[1] > kMaxLine ? p->s1_elems : 0);
 
   cudaStream_t s = (cudaStream_t)stream;
   double* coef = nullptr;
@@ -627,6 +630,9 @@ frlap_status frlap_learn_grad(const frlap_plan* plan, const float* d_params, con
   if (!plan || !d_params || !d_r || !d_e || !d_grad || !d_loss) return fail(FRLAP_EINVAL, "NULL argument");
   if (B < 1) return fail(FRLAP_EINVAL, "B must be >= 1");
   if (plan->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "training needs an F64 or MIXED plan (FP64 spectra)");
+  for (int r = 0; r < plan->d; ++r)
+    if (plan->P[r] > kMaxLine)
+      return fail(FRLAP_EINVAL, "training spectra need embeddings of at most 8192 points per axis (2D N <= 4096)");
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
   cudaError_t e = learn_grad_launch(*plan, d_params, d_r, d_e, B, d_grad, d_loss, d_work, (cudaStream_t)stream);

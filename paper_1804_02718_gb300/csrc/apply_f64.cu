@@ -12,7 +12,7 @@ extern template cudaError_t apply_launch<dfl>(const Plan&, const double*, double
 size_t apply_work_bytes(const Plan& p, int real_bytes) {
   const size_t cb = 2 * (size_t)real_bytes;
   size_t b = align256(p.s1_elems * cb);
-  if (p.d == 3) b += align256(p.s2_elems * cb);
+  b += align256(p.s2_elems * cb);
   return b;
 }
 

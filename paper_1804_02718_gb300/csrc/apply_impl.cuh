@@ -547,6 +547,68 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
   }
 }
 
+// The middle stage of 2D plans with a P = 16384-point y embedding (n_y up to 8191), as two
+// transforms of the longest line length the kernels hold, L = P/2 = 8192 points, split by the
+// parity of the frequency.  The column v is zero past n_y <= L, so
+//   X[2m]   = sum_{j<L} v_j W_L^{jm}                 (the even half: the L-point DFT of v),
+//   X[2m+1] = sum_{j<L} (v_j W_P^j) W_L^{jm}         (the odd half: of v times W_P^j),
+// and the inverse, sum_k lambda_k X_k W_P^{-jk} (1/P is part of lambda), is
+//   y_j = IDFT_L(lambda_{2m} X[2m])_j + W_P^{-j} IDFT_L(lambda_{2m+1} X[2m+1])_j
+// with unnormalised inverse transforms.  ODD = false computes the even half into tmp (same layout
+// as the columns); ODD = true the odd half, adds tmp, and writes the column in place.  The
+// transforms read the P-point twiddle table: its stage entries W_{16 Ns}^{rk} do not depend on P,
+// and the last (radix-2) stage reads every second plain entry.
+template <typename T, bool ODD>
+__global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul_split(cplx<T>* __restrict__ data, cplx<T>* __restrict__ tmp,
+                                                                int ncols, int n, size_t ld, int TL,
+                                                                const T* __restrict__ lam, int Hy1,
+                                                                const cplx<T>* __restrict__ tw,
+                                                                const int* __restrict__ skip, Batch bt) {
+  constexpr int logL = 13, L = 1 << logL, P = 2 * L, G = L >> 4, REM = logL & 3, logPtab = logL + 1;
+  {
+    const size_t bi = blockIdx.y;
+    data += bi * bt.in;
+    tmp += bi * bt.out;
+    lam += bi * bt.lam;
+    if (skip) skip += bi * bt.skip;
+  }
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  if (skip && FRLAP_GLD(skip)) return;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int col = blockIdx.x * TL + l;
+  const bool valid = col < ncols;
+  C* buf = smem + (size_t)l * sline(L);
+  C* line = data + (size_t)(valid ? col : 0) * ld;
+  C* tline = tmp + (size_t)(valid ? col : 0) * ld;
+  // lane holds elements j = lane + m G, m = 0..15 (all of them: n can exceed L/2)
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int j = lane + m * G;
+    v[m] = (valid && j < n) ? ld_stream(&line[j]) : czero<C>();
+    if constexpr (ODD) v[m] = cmul(v[m], FRLAP_GLD(tw + j));
+  }
+  fft_regs<T, -1, false, REM>(v, buf, logL, lane, tw, logPtab, false);
+  const T* __restrict__ lrow = lam + (size_t)(valid ? col : 0) * Hy1;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int k = 2 * (lane + m * G) + (ODD ? 1 : 0);  // frequency of this output, folded below
+    v[m] = ld_stream(&lrow[min(k, P - k)]) * v[m];
+  }
+  fft_regs<T, 1, false, REM>(v, buf, logL, lane, tw, logPtab, true);
+  if (!valid) return;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int j = lane + m * G;
+    if (j < n) {
+      if constexpr (ODD) FRLAP_GST(line + j, cmulc(v[m], FRLAP_GLD(tw + j)) + FRLAP_GLD(tline + j));
+      else FRLAP_GST(tline + j, v[m]);
+    }
+  }
+}
+
 // The cropped output of k_colmul: column blockIdx.x * TL + tid / G, elements lane + m G < n
 // (m < 8; n <= P/2).  The thread's column and lane are re-derived from
 // the special registers here, not kept live across both transforms (that spilled).
@@ -1011,7 +1073,24 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   map.Py = p.P[1];
   map.Hy1 = p.P[1] / 2 + 1;
   map.Hz1 = p.d == 3 ? p.P[2] / 2 + 1 : 1;
-  if (p.d == 2) {
+  if (p.d == 2 && p.P[1] > kMaxLine) {
+    // 16384-point y embedding: the even and the odd half of the middle stage (k_colmul_split)
+    constexpr int L = kMaxLine, G = L >> 4;
+    const int tl = pick_tl_tuned(tuned[1], sline(L), eb, G, budget, (long long)(Hx + 1) * B);
+    const size_t sm = (size_t)tl * sline(L) * eb;
+    const int ncols = Hx + 1;
+    const int grid = (ncols + tl - 1) / tl;
+    Batch b_split = b_ws;  // columns in S1, the even half in S2 (same per-instance stride)
+    cudaError_t e;
+    if ((e = mark()) != cudaSuccess) return e;
+    if ((e = set_smem(k_colmul_split<T, false>, sm)) != cudaSuccess) return e;
+    if ((e = set_smem(k_colmul_split<T, true>, sm)) != cudaSuccess) return e;
+    k_colmul_split<T, false><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, ncols, ny, ld1, tl, lam, map.Hy1, tw[1], skip,
+                                                              b_split);
+    k_colmul_split<T, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, ncols, ny, ld1, tl, lam, map.Hy1, tw[1], skip,
+                                                             b_split);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (p.d == 2) {
     const int G = p.P[1] >> 4;
     const int tl = pick_tl_tuned(tuned[1], sline(p.P[1]), eb, G, budget, (long long)(Hx + 1) * B);
     const size_t sm = (size_t)tl * sline(p.P[1]) * eb;
@@ -1274,7 +1353,7 @@ cudaError_t spectrum_inverse(const Plan& p, const cplx<T>* SP, const T* mult, T*
 template <typename T>
 static int stage_line_length(const Plan& p, int st) {
   const int Hx = p.P[0] / 2;
-  if (p.d == 2) return st == 1 ? p.P[1] : Hx;
+  if (p.d == 2) return st == 1 ? (p.P[1] > kMaxLine ? kMaxLine : p.P[1]) : Hx;
   if (st == 0 || st == 4) return Hx;
   return st == 2 ? p.P[2] : p.P[1];
 }

@@ -315,6 +315,41 @@ __global__ void __launch_bounds__(512) k_sym_axis(double* lam, size_t nlines, in
     for (int j = lane; j <= H; j += G) lam[base + (size_t)j * stride] = buf[spad(j)].x;
 }
 
+// k_sym_axis for P = 2 L points with L = 8192, the longest line the FFT kernels hold: one line per
+// CTA, split by output parity.  With t the P-periodic even extension of the line's generator,
+//   g(2m)   = sum_{k<L} (t_k + t_{k+L}) W_L^{km},
+//   g(2m+1) = sum_{k<L} (t_k - t_{k+L}) W_P^k W_L^{km},
+// two L-point transforms (the P-point table serves them, see fft_line).  The line's P/2 + 1 input
+// values are first copied to shared memory, since the outputs overwrite them in place.
+__global__ void __launch_bounds__(512) k_sym_axis_split(double* lam, size_t nlines, size_t stride, size_t inner,
+                                                        const double2* __restrict__ tw) {
+  constexpr int logL = 13, L = 1 << logL, P = 2 * L, H = L, G = L >> 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  double* t = reinterpret_cast<double*>(smem_raw + (size_t)sline(L) * sizeof(double2));  // t_0 .. t_{P/2}
+  const int lane = threadIdx.x;
+  const size_t line = blockIdx.x;
+  if (line >= nlines) return;
+  const size_t base = (line / inner) * inner * (size_t)(H + 1) + (line % inner);
+  for (int j = lane; j <= H; j += G) t[j] = lam[base + (size_t)j * stride];
+  __syncthreads();
+  for (int parity = 0; parity < 2; ++parity) {
+    for (int k = lane; k < L; k += G) {
+      // t_{k + L} = t_{P - k - L} = t_{L - k} by the even extension (k + L <= P - 1)
+      const double a = t[k], b = t[L - k];
+      buf[spad(k)] = parity == 0 ? make_double2(a + b, 0.0) : cmul(make_double2(a - b, 0.0), tw[k]);
+    }
+    __syncthreads();
+    fft_line<double, -1>(buf, logL, lane, tw, logL + 1);
+    // outputs j = 2m + parity <= P/2, m < L
+    for (int m = lane; m < L; m += G) {
+      const int j = 2 * m + parity;
+      if (j <= H) lam[base + (size_t)j * stride] = buf[spad(m)].x;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_scale_copy(double* lam64, float* lam32, size_t n, double s) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -416,6 +451,17 @@ cudaError_t symbol_axes_launch(const Plan& p, double* lam, cudaStream_t s) {
   for (int r = 0; r < p.d; ++r) {
     const int P = p.P[r];
     const int logP = p.logP[r];
+    if (P > kMaxLine) {  // two half-length transforms per line (k_sym_axis_split)
+      size_t stride = 1;
+      for (int q = 0; q < r; ++q) stride *= H1[q];
+      const size_t nlines = total / H1[r];
+      const size_t sm = (size_t)sline(kMaxLine) * 16 + (size_t)(P / 2 + 1) * 8;
+      e = cudaFuncSetAttribute(k_sym_axis_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      k_sym_axis_split<<<(unsigned)nlines, kMaxLine / 16, sm, s>>>(lam, nlines, stride, stride, p.tw64[r]);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      continue;
+    }
     const int G = P >> 4;
     int tl = (48 * 1024) / (sline(P) * 16);
     if (tl < 1) tl = 1;

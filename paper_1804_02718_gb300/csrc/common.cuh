@@ -230,6 +230,10 @@ template <> __device__ __forceinline__ cdf mul_i<-1, cdf>(cdf a) { return mul_i_
 template <> __device__ __forceinline__ cdf mul_i<1, cdf>(cdf a) { return mul_i_cdf<1>(a); }
 
 // ---------------------------------------------------------------- plan
+// Longest FFT line the transform kernels hold (one line of 2^13 points per 2^9 threads); longer
+// 2D embeddings (16384 points) split their middle stage into two halves of this length.
+constexpr int kMaxLine = 8192;
+
 struct Plan {
   int d;
   int N[3];        // mesh intervals per axis (x, y, z); unused axes = 2

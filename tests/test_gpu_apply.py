@@ -339,3 +339,31 @@ def test_bounded_wait_gives_up_and_context_survives(frlap):
     y = frlap.frlap_apply(plan, _t(u)).cpu().numpy()
     assert np.linalg.norm(y - op(u)) <= 1e-12 * op.lam_max * np.linalg.norm(u)
     assert frlap.frlap_async_wait_report() == 0
+
+
+@pytest.mark.parametrize("Ns", [(40, 4200), (4200, 40)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (3, 1e-12)])
+def test_apply_16384_point_embeddings(frlap, Ns, prec, tol):
+    """2D axes with N > 4096 embed in 16384 points: along y the middle stage runs as its even and odd
+    frequency halves (two 8192-point transforms), along x the rows are 8192-point half-length
+    transforms, and the symbol's axis transform is split the same way.  Against the oracle, for a
+    batch of two (bit for bit the one-vector apply) and after autotuning."""
+    h = 2.0 / max(Ns)
+    a_ref, c = _oracle(2, 1.3, h, Ns)
+    us = [inp.normal_field(Ns, seed=95 + b) for b in range(2)]
+    op = fast.FastOperator(a_ref, c, us[0].shape)
+    plan = frlap.Plan(2, 1.3, h, Ns, prec=prec)
+    assert max(plan.P) == 16384
+    dt = torch.float32 if prec == 1 else torch.float64
+    U = _t(np.stack(us), dt)
+    Y = frlap.frlap_apply_batch(plan, U)
+    for b, u in enumerate(us):
+        y = Y[b].double().cpu().numpy()
+        assert np.linalg.norm(y - op(u)) <= tol * op.lam_max * np.linalg.norm(u), b
+        assert torch.equal(Y[b], frlap.frlap_apply(plan, U[b].clone()))
+    frlap.frlap_plan_autotune(plan, 2)
+    assert torch.equal(frlap.frlap_apply_batch(plan, U), Y)
+    if prec != 1:
+        lam_ref = fast.symbol(a_ref, c, us[0].shape, P=tuple(reversed(plan.P)))
+        oct_ref = lam_ref[tuple(slice(0, p // 2 + 1) for p in reversed(plan.P))] / np.prod(plan.P)
+        assert np.abs(plan.symbol().cpu().numpy() - oct_ref).max() <= 1e-14 * np.abs(oct_ref).max()

@@ -2,10 +2,11 @@
 Sec. 5.2), the operator's consistency errors (Tables Table1 and Table2, Example 5.1.1) and the second-
 order rate of Example 5.1.2 in 2D and 3D.
 
-Everything here runs through libfrlap: the fine-mesh f (the scheme on N = 4096, h =
-2^-11, double-float apply), the coarse coefficients and the coarse CG solves; only the
-analytic u comes from the host.  With h_ref = 2^-11 instead of the paper's 2^-12 the
-errors move by about (h_ref/h)^p relative, hence tolerances that grow with h.
+Everything here runs through libfrlap: the fine-mesh reference (the scheme on N = 8192, the paper's
+h = 2^-12, double-float apply; its 16384-point embedding runs the split middle stage), the coarse
+coefficients and the coarse solves; only the analytic u comes from the host.  All six printed mesh
+sizes h = 1/16 .. 1/512 are checked to the tables' printed precision: four significant digits, a
+relative rounding of at most 5e-4 (REL below adds 1e-4).
 """
 import json
 import os
@@ -20,8 +21,9 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLES = json.load(open(os.path.join(HERE, "golden", "paper_poisson_tables.json")))
-NREF = 4096
-TOL = [1e-3, 2e-3, 5e-3, 1.5e-2]  # h = 1/16, 1/32, 1/64, 1/128
+NREF = 8192
+NS = (32, 64, 128, 256, 512, 1024)  # h = 1/16 .. 1/512 on (-1, 1)^2
+REL = 6e-4
 
 
 @pytest.mark.parametrize("table", ["tab1", "tab2"])
@@ -33,19 +35,21 @@ def test_poisson_table_on_gpu(frlap, table, alpha):
     u_fine = torch.from_numpy(inp.bubble_field((NREF, NREF), href, s)).cuda()
     f_fine = frlap.frlap_apply(fine, u_fine)
     del fine
-    for k, N in enumerate((32, 64, 128, 256)):
+    for k, N in enumerate(NS):
         h = 2.0 / N
         st = NREF // N
         fc = f_fine[st - 1::st, st - 1::st].contiguous()
         plan = frlap.Plan(2, alpha, h, (N, N))
-        # ask for 1e-13; near the FP64 rounding floor (alpha = 1.4 at 255^2) accept what CG reaches
-        uh, it, rel, code = frlap.frlap_pcg_solve(plan, fc, rtol=1e-13, raise_on_error=False)
+        frlap.frlap_precond_strang(plan)
+        # ask for 1e-13; near the FP64 rounding floor (alpha = 1.4 from 255^2) accept what PCG reaches
+        uh, it, rel, code = frlap.frlap_pcg_solve(plan, fc, rtol=1e-13, raise_on_error=False,
+                                                  precond=frlap.FRLAP_PRECOND_STRANG)
         assert code in (0, 5) and rel <= 1e-11, (code, rel)
         e = uh.cpu().numpy() - inp.bubble_field((N, N), h, s)
         einf, e2 = np.abs(e).max(), np.sqrt(h * h * np.sum(e * e))
         key = f"{alpha:.1f}"
-        assert einf == pytest.approx(TABLES[table]["inf"][key][k], rel=TOL[k]), (table, alpha, N, einf)
-        assert e2 == pytest.approx(TABLES[table]["two"][key][k], rel=TOL[k]), (table, alpha, N, e2)
+        assert einf == pytest.approx(TABLES[table]["inf"][key][k], rel=REL), (table, alpha, N, einf)
+        assert e2 == pytest.approx(TABLES[table]["two"][key][k], rel=REL), (table, alpha, N, e2)
 
 
 POISSON_F1 = json.load(open(os.path.join(HERE, "golden", "paper_poisson_f1_table.json")))
@@ -75,10 +79,6 @@ def test_poisson_f1_table_on_gpu(frlap, alpha):
 
 
 OPERATOR = json.load(open(os.path.join(HERE, "golden", "paper_operator_tables.json")))
-# relative tolerance at h = 1/16, 1/32, 1/64, 1/128 with the 2^-11 reference: the oracle with the same
-# reference lands within 3.3e-4, 5.7e-4, 1.1e-3, 4.1e-3 of the printed values (the gap to the paper's
-# 2^-12 reference); the oracle's own test, on a 2^-9 reference, allows 3e-3, 8e-3, 2.5e-2 up to 1/64
-TOL_OP = [6e-4, 1e-3, 2e-3, 6e-3]
 
 
 @pytest.mark.parametrize("table,alpha", [("table1", 0.1), ("table1", 0.4), ("table1", 0.7),
@@ -86,22 +86,22 @@ TOL_OP = [6e-4, 1e-3, 2e-3, 6e-3]
 def test_operator_table_on_gpu(frlap, table, alpha):
     """Example 5.1.1 (Tables Table1 and Table2 of Sec. 5.1) through frlap_apply: the consistency error
     e = A_h u - A_ref u of the operator on u = [(1-x^2)(1-y^2)]^s at the coarse nodes, with the
-    reference operator applied on h = 2^-11 (the paper's is 2^-12), for h = 1/16 .. 1/128."""
+    reference operator applied on the paper's h = 2^-12, for all printed h = 1/16 .. 1/512."""
     s = OPERATOR[table]["s"]
     href = 2.0 / NREF
     ref = frlap.Plan(2, alpha, href, (NREF, NREF), prec=frlap.FRLAP_DF64)
     yref = frlap.frlap_apply(ref, torch.from_numpy(inp.bubble_field((NREF, NREF), href, s)).cuda())
     del ref
     key = f"{alpha:.1f}"
-    for k, N in enumerate((32, 64, 128, 256)):
+    for k, N in enumerate(NS):
         h = 2.0 / N
         st = NREF // N
         plan = frlap.Plan(2, alpha, h, (N, N))
         y = frlap.frlap_apply(plan, torch.from_numpy(inp.bubble_field((N, N), h, s)).cuda())
         e = (y - yref[st - 1::st, st - 1::st]).cpu().numpy()
         einf, e2 = np.abs(e).max(), np.sqrt(h * h * np.sum(e * e))
-        assert einf == pytest.approx(OPERATOR[table]["inf"][key][k], rel=TOL_OP[k]), (table, alpha, N, einf)
-        assert e2 == pytest.approx(OPERATOR[table]["two"][key][k], rel=TOL_OP[k]), (table, alpha, N, e2)
+        assert einf == pytest.approx(OPERATOR[table]["inf"][key][k], rel=REL), (table, alpha, N, einf)
+        assert e2 == pytest.approx(OPERATOR[table]["two"][key][k], rel=REL), (table, alpha, N, e2)
 
 
 @pytest.mark.parametrize("d,Nref,Ns", [(2, 4096, (64, 128, 256, 512)), (3, 512, (16, 32, 64))])
