@@ -86,13 +86,15 @@ typedef enum {
   FRLAP_SOLVE_IR = 1       /* FP64 iterative refinement around FP32 CG (MIXED plans) */
 } frlap_solver;
 
-/* Preconditioners of frlap_pcg_solve.  Each is a Fourier multiplier applied
- * through the same circulant embedding as A (one FP32 apply per iteration),
- * so the outer FP64 iteration is flexible (Polak-Ribiere) PCG. */
+/* Preconditioners of frlap_pcg_solve.  Each is a multiplier applied through the
+ * apply pipeline (one FP32 apply per iteration), so the outer FP64 iteration is
+ * flexible (Polak-Ribiere) PCG: in the Fourier basis of A's circulant embedding
+ * (Strang, learned) or in the sine basis of the box (tau). */
 typedef enum {
   FRLAP_PRECOND_NONE = 0,
   FRLAP_PRECOND_STRANG = 1,   /* inverse of the multilevel Strang circulant (built by frlap_precond_strang) */
-  FRLAP_PRECOND_LEARNED = 2   /* a multiplier set by frlap_precond_set_symbol (e.g. the learned MLP's) */
+  FRLAP_PRECOND_LEARNED = 2,  /* a multiplier set by frlap_precond_set_symbol (e.g. the learned MLP's) */
+  FRLAP_PRECOND_TAU = 3       /* S diag(S A S)^-1 S, S the multilevel DST-I (built by frlap_precond_tau) */
 } frlap_precond;
 
 typedef struct frlap_plan frlap_plan;
@@ -244,6 +246,19 @@ frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* 
  * dominant); non-positive ones would be dropped and are counted in
  * *n_nonpositive (may be NULL).  Synchronises stream. */
 frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* stream);
+
+/* Build the sine-basis ("tau") preconditioner of a 2D plan (set-up call: allocates the
+ * multiplier and temporary scratch).  S, the orthonormal multilevel DST-I, holds the sine
+ * modes of the box, which vanish on its boundary as u does; M = S diag(S A S)^-1 S is the
+ * inverse of the member of the algebra S diagonalises that is closest to A in the
+ * Frobenius norm.  diag(S A S) is computed from the coefficients by one P-point DFT per
+ * line and axis; M is applied on odd extensions of the vector to P = 2 N_r points per
+ * axis (whose DFT is the DST) through the apply pipeline, one FP32 apply per iteration.
+ * Needs d = 2 and every N[r] a power of two in [16, 4096] (so that P_r = 2 N_r), else
+ * FRLAP_EINVAL.  Entries of diag(S A S) are Rayleigh quotients of A, positive for this
+ * operator; non-positive ones would be dropped and are counted in *n_nonpositive (may be
+ * NULL).  Synchronises stream. */
+frlap_status frlap_precond_tau(frlap_plan* plan, int* n_nonpositive, void* stream);
 
 /* z = M^-1 r for one of the plan's preconditioners, in FP32 (r, z: prod(n_r)
  * floats, not overlapping; d_work: frlap_workspace_bytes(plan, FRLAP_OP_APPLY)). */

@@ -17,6 +17,11 @@
   reaction term enters; this linear-per-step form is the reading.
 * strang_symbol / strang_solve: the multilevel Strang circulant of the Toeplitz
   matrix (first column t_{min(j, n-j)} per axis), inverted by FFTs of size n.
+* sine_modes / tau_symbol / tau_symbol_by_modes / tau_solve: the sine-basis ("tau")
+  preconditioner M = S diag(S A S)^-1 S with S the orthonormal multilevel DST-I.  The
+  paper has no preconditioner; this is one the library offers, restated here from its
+  definition: tau_symbol_by_modes forms each s_k^T A s_k with the operator itself,
+  tau_symbol sums the same quadratic forms through their closed form per axis.
 """
 from __future__ import annotations
 
@@ -83,6 +88,46 @@ def strang_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
 def strang_solve(lam_s: np.ndarray, r: np.ndarray) -> np.ndarray:
     """z = C^-1 r for the Strang circulant with eigenvalues lam_s."""
     return sfft.ifftn(sfft.fftn(r, workers=WORKERS) / lam_s, workers=WORKERS).real
+
+
+def sine_modes(n: int) -> np.ndarray:
+    """S[k-1, i-1] = sqrt(2/(n+1)) sin(pi i k / (n+1)), i, k = 1..n: orthonormal, symmetric."""
+    i = np.arange(1, n + 1)
+    return np.sqrt(2.0 / (n + 1)) * np.sin(np.pi * np.outer(i, i) / (n + 1))
+
+
+def tau_symbol_by_modes(apply, shape) -> np.ndarray:
+    """diag(S A S)[k] = s_k^T A s_k, one apply of A per 2D sine mode s_k = s_{k_y} (x) s_{k_x}."""
+    ny, nx = shape
+    Sy, Sx = sine_modes(ny), sine_modes(nx)
+    out = np.empty((ny, nx))
+    for ky in range(ny):
+        for kx in range(nx):
+            mode = np.outer(Sy[ky], Sx[kx])
+            out[ky, kx] = float(np.sum(mode * apply(mode)))
+    return out
+
+
+def tau_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
+    """diag(S A S) for the 2D Toeplitz A (A[i, j] = t_{|i - j|}, t = -c coef): the quadratic forms
+    s_k^T A s_k = sum over offsets d of t_{|d|} prod_r sum_i s_{k_r}(i) s_{k_r}(i + d_r), where per
+    axis the inner sum over both signs of d is
+    C[k][d] = m_d/(n+1) ((n - d) cos(a d) + sin(a (d+1))/sin(a)), a = pi k/(n+1), m_0 = 1, m_d = 2."""
+    def cmat(n):
+        k = np.arange(1, n + 1)[:, None]
+        d = np.arange(n)[None, :]
+        a = np.pi * k / (n + 1)
+        m = np.where(d == 0, 1.0, 2.0)
+        return m / (n + 1) * ((n - d) * np.cos(a * d) + np.sin(a * (d + 1)) / np.sin(a))
+    ny, nx = shape
+    t = -c * coef[:ny, :nx]
+    return cmat(ny) @ t @ cmat(nx).T
+
+
+def tau_solve(tau: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """z = S diag(tau)^-1 S r with the orthonormal 2D DST-I (SciPy's type-1 DST, norm='ortho')."""
+    rh = sfft.dstn(r, type=1, norm="ortho", workers=WORKERS)
+    return sfft.idstn(rh / tau, type=1, norm="ortho", workers=WORKERS)
 
 
 def allen_cahn_cn_rhs(apply, ubar: np.ndarray, tau: float, delta: float, alpha: float) -> np.ndarray:

@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("FRLAP_LIBRARY") or os.path.join(_HERE, "libfrlap.so")
 FRLAP_F64, FRLAP_F32, FRLAP_MIXED, FRLAP_DF64, FRLAP_MIXED_DF64 = 0, 1, 2, 3, 4
 FRLAP_OP_APPLY, FRLAP_OP_PCG, FRLAP_OP_AC = 0, 1, 2
 FRLAP_SOLVE_CG, FRLAP_SOLVE_IR = 0, 1
-FRLAP_PRECOND_NONE, FRLAP_PRECOND_STRANG, FRLAP_PRECOND_LEARNED = 0, 1, 2
+FRLAP_PRECOND_NONE, FRLAP_PRECOND_STRANG, FRLAP_PRECOND_LEARNED, FRLAP_PRECOND_TAU = 0, 1, 2, 3
 
 STATUS = {
     0: "FRLAP_OK", 1: "FRLAP_EINVAL", 2: "FRLAP_ENOMEM", 3: "FRLAP_EWORKSPACE", 4: "FRLAP_ECUDA",
@@ -51,6 +51,7 @@ _SIGS = {
     "frlap_apply_host": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "frlap_pcg_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P]),
     "frlap_precond_strang": (_I, [_P, ctypes.POINTER(_I), _P]),
+    "frlap_precond_tau": (_I, [_P, ctypes.POINTER(_I), _P]),
     "frlap_precond_set_symbol": (_I, [_P, _P, _P]),
     "frlap_precond_apply": (_I, [_P, _I, _P, _P, _P, _P]),
     "frlap_mlp_multiplier": (_I, [_P, _P, _P, _P]),
@@ -383,8 +384,15 @@ def frlap_precond_strang(plan: Plan, stream=None) -> int:
     return bad.value
 
 
+def frlap_precond_tau(plan: Plan, stream=None) -> int:
+    """Build the sine-basis (tau) preconditioner of a 2D plan; returns the number of dropped non-positive entries."""
+    bad = ctypes.c_int(0)
+    _check(lib().frlap_precond_tau(plan.handle, ctypes.byref(bad), _stream(stream)), "frlap_precond_tau")
+    return bad.value
+
+
 def frlap_precond_apply(plan: Plan, precond: int, r: torch.Tensor, z: torch.Tensor = None, work=None, stream=None):
-    """z = M^-1 r (FP32) for the plan's Strang or learned preconditioner."""
+    """z = M^-1 r (FP32) for the plan's Strang, learned or sine-basis preconditioner."""
     _check_vectors(plan, r, z, ("r", "z"))
     if z is None:
         z = torch.empty_like(r)

@@ -49,6 +49,8 @@ frlap_status ac_batch_impl(int nb, const frlap_plan* const* plans, double* const
 frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, double* E, double* R, int* npairs,
                            void* work, cudaStream_t st);
 cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host);
+size_t tau_scratch_bytes(const Plan& p);
+cudaError_t tau_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host);
 cudaError_t scale_to_f32_launch(const double* src, float* dst, size_t n, double s, cudaStream_t st);
 frlap_status allen_cahn_cn_impl(const Plan& p, double* ub, double tau, double delta, int nsteps, double rtol,
                                 int* iters, double* h_mass, void* work, cudaStream_t st);
@@ -178,6 +180,7 @@ frlap_status frlap_plan_destroy(frlap_plan* plan) {
   cudaFree(plan->lam32);
   cudaFree(plan->mu_strang);
   cudaFree(plan->mu_learned);
+  cudaFree(plan->mu_tau);
   cudaFree(plan->lamdf);
   for (int r = 0; r < 3; ++r) {
     cudaFree(plan->tw64[r]);
@@ -564,6 +567,9 @@ frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* 
   } else if (precond == FRLAP_PRECOND_LEARNED) {
     if (!plan->mu_learned) return fail(FRLAP_EINVAL, "no learned multiplier set (frlap_precond_set_symbol)");
     mu = plan->mu_learned;
+  } else if (precond == FRLAP_PRECOND_TAU) {
+    if (!plan->mu_tau) return fail(FRLAP_EINVAL, "sine-basis preconditioner not built (frlap_precond_tau)");
+    mu = plan->mu_tau;
   } else if (precond != FRLAP_PRECOND_NONE) {
     return fail(FRLAP_EINVAL, "unknown preconditioner");
   }
@@ -599,16 +605,41 @@ frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* st
   return FRLAP_OK;
 }
 
+frlap_status frlap_precond_tau(frlap_plan* plan, int* n_nonpositive, void* stream) {
+  if (!plan) return fail(FRLAP_EINVAL, "plan is NULL");
+  if (plan->d != 2) return fail(FRLAP_EINVAL, "the sine-basis preconditioner is built for 2D plans");
+  for (int r = 0; r < plan->d; ++r)
+    if (plan->P[r] != 2 * plan->N[r] || plan->P[r] > kMaxLine)
+      return fail(FRLAP_EINVAL, "the sine-basis preconditioner needs every N[r] a power of two in [16, 4096]");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!plan->mu_tau && cudaMalloc(&plan->mu_tau, plan->lam_count * sizeof(float)) != cudaSuccess)
+    return fail(FRLAP_ENOMEM, "sine-basis multiplier allocation failed");
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, tau_scratch_bytes(*plan), s) != cudaSuccess)
+    return fail(FRLAP_ENOMEM, "sine-basis scratch allocation failed");
+  unsigned bad = 0;
+  cudaError_t e = tau_build(*plan, scratch, s, &bad);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_tau");
+  if (n_nonpositive) *n_nonpositive = (int)bad;
+  return FRLAP_OK;
+}
+
 frlap_status frlap_precond_apply(const frlap_plan* plan, int precond, const float* d_r, float* d_z, void* d_work,
                                  void* stream) {
   if (!plan || !d_r || !d_z) return fail(FRLAP_EINVAL, "plan, d_r or d_z is NULL");
   if (ranges_overlap(d_r, d_z, vector_bytes(*plan, true))) return fail(FRLAP_EINVAL, "d_r and d_z must not overlap");
-  const float* mu = precond == FRLAP_PRECOND_STRANG ? plan->mu_strang
-                    : precond == FRLAP_PRECOND_LEARNED ? plan->mu_learned : nullptr;
+  const float* mu = precond == FRLAP_PRECOND_STRANG    ? plan->mu_strang
+                    : precond == FRLAP_PRECOND_LEARNED ? plan->mu_learned
+                    : precond == FRLAP_PRECOND_TAU     ? plan->mu_tau
+                                                       : nullptr;
   if (!mu) return fail(FRLAP_EINVAL, "preconditioner not available on this plan");
   frlap_status rc = check_work(d_work);
   if (rc != FRLAP_OK) return rc;
-  cudaError_t e = apply_launch<float>(*plan, d_r, d_z, d_work, (cudaStream_t)stream, nullptr, nullptr, mu);
+  cudaError_t e = apply_launch<float>(*plan, d_r, d_z, d_work, (cudaStream_t)stream, nullptr, nullptr, mu,
+                                      precond == FRLAP_PRECOND_TAU);
   if (e != cudaSuccess) return cuda_fail(e, "frlap_precond_apply");
   return FRLAP_OK;
 }

@@ -7,7 +7,7 @@ namespace frlap {
 
 // instantiated in apply_dfl.cu
 extern template cudaError_t apply_launch<dfl>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
-                                              cudaEvent_t const*, const dfl*);
+                                              cudaEvent_t const*, const dfl*, bool);
 
 size_t apply_work_bytes(const Plan& p, int real_bytes) {
   const size_t cb = 2 * (size_t)real_bytes;
@@ -25,7 +25,7 @@ cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaS
 template cudaError_t apply_batch_launch<double>(const Plan&, int, const double*, double*, size_t, void*, cudaStream_t,
                                                 const int*, int, const double*, size_t, cudaEvent_t const*);
 template cudaError_t apply_launch<double>(const Plan&, const double*, double*, void*, cudaStream_t, const int*,
-                                          cudaEvent_t const*, const double*);
+                                          cudaEvent_t const*, const double*, bool);
 
 size_t spectrum_elems(const Plan& p) {
   const size_t Hx1 = p.P[0] / 2 + 1;

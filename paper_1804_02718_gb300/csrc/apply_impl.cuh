@@ -220,7 +220,7 @@ inline int device_sm_count() {
 // The rest of the first stage for one tile of TL rows, once each thread holds its row's packed
 // samples in v (lane's q = lane + m G, see k_r2c_T): the half-length transform, the real-data
 // split and the transposed store of bins 0..H into out[k * ldo + line].
-template <typename T, int REM>
+template <typename T, int REM, bool ZIN = true>
 __device__ __forceinline__ void r2c_tile(cplx<T>* v, cplx<T>* smem, cplx<T>* __restrict__ out, int nlines, size_t ldo,
                                          int logH, int TL, const cplx<T>* __restrict__ tw, int logP, int line0, int l,
                                          int lane) {
@@ -228,7 +228,7 @@ __device__ __forceinline__ void r2c_tile(cplx<T>* v, cplx<T>* smem, cplx<T>* __r
   const int H = 1 << logH, G = H >> 4;
   const int LS = sline(H);
   C* buf = smem + (size_t)l * LS;
-  fft_regs<T, -1, true, REM>(v, buf, logH, lane, tw, logP, false);
+  fft_regs<T, -1, ZIN, REM>(v, buf, logH, lane, tw, logP, false);
   line_sync<T>(logH);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
@@ -293,7 +293,18 @@ __device__ __forceinline__ void r2c_tile(cplx<T>* v, cplx<T>* smem, cplx<T>* __r
   }
 }
 
-template <typename T, int REM, int LOGL = 0>
+// ODD: the row is extended oddly instead of by zeros, to P = 2H = 2(n + 1) points: z_j = x_{j-1} for
+// 1 <= j <= n, z_{P-j} = -z_j, z_0 = z_H = 0.  Its DFT is -2i times the row's sine transform (DST-I),
+// so the same pipeline applies a multiplier in the sine basis of the box (the tau preconditioner).
+template <typename V>
+__device__ __forceinline__ V odd_ext(const V* __restrict__ src, int j, int n, int H, bool valid) {
+  if (!valid) return V(0);
+  if (j >= 1 && j <= n) return FRLAP_GLD(src + (j - 1));
+  if (j > H && 2 * H - j - 1 < n) return -FRLAP_GLD(src + (2 * H - j - 1));
+  return V(0);
+}
+
+template <typename T, int REM, int LOGL = 0, bool ODD = false>
 __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int n, int ldi,
                         size_t ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
@@ -320,27 +331,37 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_T(const io_t<T>* __restri
   const io_t<T>* src = in + (size_t)(valid ? line : 0) * ldi;
   // packed samples z[q] = x[2q] + i x[2q+1]; lane holds q = lane + m G.  n <= H, so z is zero
   // for q >= H/2 (m >= 8): the upper half of the transform input.
-  // A row that starts on a pair boundary is read one pair (x[2q], x[2q+1]) per load.
-  using IO2 = io_pair<T>;
-  const bool pair_aligned = (reinterpret_cast<uintptr_t>(src) % sizeof(IO2)) == 0;
   C v[16];
+  if constexpr (ODD) {
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int q = lane + m * G;
-    io_t<T> re = io_t<T>(0), im = io_t<T>(0);
-    if (m < 8 && valid) {
-      if (pair_aligned && 2 * q + 1 < n) {
-        const IO2 t = FRLAP_GLD(reinterpret_cast<const IO2*>(src + 2 * q));
-        re = t.x;
-        im = t.y;
-      } else {
-        if (2 * q < n) re = FRLAP_GLD(src + 2 * q);
-        if (2 * q + 1 < n) im = FRLAP_GLD(src + 2 * q + 1);
-      }
+    for (int m = 0; m < 16; ++m) {
+      const int q = lane + m * G;
+      v[m] = mk<C>(from_io<T>(odd_ext(src, 2 * q, n, H, valid)), from_io<T>(odd_ext(src, 2 * q + 1, n, H, valid)));
     }
-    v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
+    r2c_tile<T, REM, false>(v, smem, out, nlines, ldo, logH, TL, tw, logP, line0, l, lane);
+    return;
+  } else {
+    // A row that starts on a pair boundary is read one pair (x[2q], x[2q+1]) per load.
+    using IO2 = io_pair<T>;
+    const bool pair_aligned = (reinterpret_cast<uintptr_t>(src) % sizeof(IO2)) == 0;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = lane + m * G;
+      io_t<T> re = io_t<T>(0), im = io_t<T>(0);
+      if (m < 8 && valid) {
+        if (pair_aligned && 2 * q + 1 < n) {
+          const IO2 t = FRLAP_GLD(reinterpret_cast<const IO2*>(src + 2 * q));
+          re = t.x;
+          im = t.y;
+        } else {
+          if (2 * q < n) re = FRLAP_GLD(src + 2 * q);
+          if (2 * q + 1 < n) im = FRLAP_GLD(src + 2 * q + 1);
+        }
+      }
+      v[m] = mk<C>(from_io<T>(re), from_io<T>(im));
+    }
+    r2c_tile<T, REM>(v, smem, out, nlines, ldo, logH, TL, tw, logP, line0, l, lane);
   }
-  r2c_tile<T, REM>(v, smem, out, nlines, ldo, logH, TL, tw, logP, line0, l, lane);
 }
 
 // Staging area of k_r2c_pf: the TL n elements of a tile's rows (E bytes each), shifted by the
@@ -467,7 +488,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_pf(const io_t<T>* __restr
   }
 }
 
-template <typename T, int REM, int LOGL = 0>
+template <typename T, int REM, int LOGL = 0, bool ODD = false>
 __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restrict__ in, io_t<T>* __restrict__ out, int nlines, int n, size_t ldi,
                         int ldo, int logH, int TL, const cplx<T>* __restrict__ tw, int logP,
                         const int* __restrict__ skip, Batch bt) {
@@ -527,7 +548,17 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2r_T(const cplx<T>* __restri
   }
   fft_regs<T, 1, false, REM>(v, buf, logH, lane, tw, logP, true);
   // v[m] = y[2q] + i y[2q+1] (times P), q = lane + m G; n <= H keeps only m < 8
-  if (line < nlines) {
+  if (ODD) {  // the odd extension's row: x_i = y_{i+1}, i < n = H - 1
+    if (line < nlines) {
+      io_t<T>* dst = out + (size_t)line * ldo;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int q = lane + m * G;
+        if (q >= 1 && 2 * q <= n) FRLAP_GST(dst + (2 * q - 1), to_io<T>(re(v[m])));
+        if (2 * q + 1 <= n) FRLAP_GST(dst + 2 * q, to_io<T>(im(v[m])));
+      }
+    }
+  } else if (line < nlines) {
     io_t<T>* dst = out + (size_t)line * ldo;
     using IO2 = io_pair<T>;
     const bool pair_aligned = (reinterpret_cast<uintptr_t>(dst) % sizeof(IO2)) == 0;
@@ -609,6 +640,24 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul_split(cplx<T>* __restr
   }
 }
 
+// ODD (see k_r2c_T): the column's entries are the transform's outputs 1 .. n, at offset -1.
+template <typename C>
+__device__ __forceinline__ void store_line_odd(const C* v, C* __restrict__ data, int ncols, int n, size_t ld,
+                                               int logP, int TL) {
+  unsigned tid;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+  const int G = 1 << (logP - 4);
+  const int lane = (int)tid & (G - 1);
+  const int col = (int)blockIdx.x * TL + ((int)tid >> (logP - 4));
+  if (col >= ncols) return;
+  C* out = data + (size_t)col * ld;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int j = lane + m * G;
+    if (j >= 1 && j <= n) FRLAP_GST(out + (j - 1), v[m]);
+  }
+}
+
 // The cropped output of k_colmul: column blockIdx.x * TL + tid / G, elements lane + m G < n
 // (m < 8; n <= P/2).  The thread's column and lane are re-derived from
 // the special registers here, not kept live across both transforms (that spilled).
@@ -632,7 +681,7 @@ __device__ __forceinline__ void store_line(const C* v, C* __restrict__ data, int
 // lines of length n (contiguous, stride ld) -> zero-pad to P, FFT, * lambda, IFFT, crop, in place
 // LOGP > 0: the line length 2^LOGP is fixed at compile time (the logP / logPtab arguments are
 // ignored), so stage spans, lane counts and shared-memory strides fold into constants.
-template <typename T, int REM, int LOGP = 0>
+template <typename T, int REM, int LOGP = 0, bool ODD = false>
 __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
                          const T* __restrict__ lam, LamMap map, const cplx<T>* __restrict__ tw, int logPtab,
                          const int* __restrict__ skip, Batch bt) {
@@ -657,12 +706,27 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
   const bool valid = col < ncols;
   C* buf = smem + (size_t)l * sline(P);
   C* line = data + (size_t)(valid ? col : 0) * ld;
-  // lane holds elements lane + m G; n <= P/2, so m >= 8 is the zero padding
+  // lane holds elements lane + m G; n <= P/2, so m >= 8 is the zero padding (ODD: the column's odd
+  // extension to P = 2(n + 1) points, as in k_r2c_T)
   C v[16];
+  if constexpr (ODD) {
+    const int H = P >> 1;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int i = lane + m * G;
-    v[m] = (m < 8 && valid && i < n) ? ld_stream(&line[i]) : czero<C>();
+    for (int m = 0; m < 16; ++m) {
+      const int j = lane + m * G;
+      C x = czero<C>();
+      if (valid) {
+        if (j >= 1 && j <= n) x = ld_stream(&line[j - 1]);
+        else if (j > H && 2 * H - j - 1 < n) x = czero<C>() - ld_stream(&line[2 * H - j - 1]);
+      }
+      v[m] = x;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int i = lane + m * G;
+      v[m] = (m < 8 && valid && i < n) ? ld_stream(&line[i]) : czero<C>();
+    }
   }
   // line-major symbol: the folded line of this column is contiguous
   auto symbol_row = [&]() -> const T* {
@@ -675,7 +739,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
   // once ran the inverse as conj(FFT(conj(.))) to execute a single copy of the stage code, which the
   // instruction cache favoured; with its arithmetic in paired instructions the code is half the size
   // and the two copies measured faster: 255^3 colmul 1.017 -> 0.992 ms.)
-  fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
+  fft_regs<T, -1, !ODD, REM>(v, buf, logP, lane, tw, logPtab, false);
   const T* __restrict__ lrow = symbol_row();
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
@@ -683,7 +747,8 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
     v[m] = ld_stream(&lrow[min(k, P - k)]) * v[m];
   }
   fft_regs<T, 1, false, REM>(v, buf, logP, lane, tw, logPtab, true);
-  store_line(v, data, ncols, n, ld, logP, TL);
+  if constexpr (ODD) store_line_odd(v, data, ncols, n, ld, logP, TL);
+  else store_line(v, data, ncols, n, ld, logP, TL);
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
@@ -984,7 +1049,10 @@ cudaError_t launch_r2c_pf(const io_t<T>* u, cplx<T>* S1, int nrows, int nx, size
 template <typename T>
 static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
                                   cudaStream_t s, const int* skip, int skip_stride, cudaEvent_t const* ev,
-                                  const T* lam_override, size_t lam_stride) {
+                                  const T* lam_override, size_t lam_stride, bool odd = false) {
+  // odd: the 2D pipeline on odd extensions (a multiplier in the sine basis, see k_r2c_T); FP32 plans'
+  // engine only, 2D, P_r = 2(n_r + 1) on both axes (the callers check)
+  if (odd && (!std::is_same<T, float>::value || p.d != 2 || p.P[1] > kMaxLine)) return cudaErrorNotSupported;
   int stage = 0;
   auto mark = [&]() -> cudaError_t {
     if (ev && ev[stage]) {
@@ -1040,7 +1108,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   b_out.skip = skip_stride;
 
   // ---- stage 1: rows of u -> S1[kx][row]
-  if (use_r2c_pf<T>(logPx - 1, u)) {
+  if (!odd && use_r2c_pf<T>(logPx - 1, u)) {
     const int G = Hx >> 4;
     const int q = G < 32 ? 32 / G : 1;
     int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
@@ -1057,13 +1125,25 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
-      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
-      cudaError_t e2 = set_smem(k_r2c_T<T, REM, LL>, sm);
-      if (e2 != cudaSuccess) return e2;
-      k_r2c_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
-      return cudaGetLastError();
-    });
+    if constexpr (std::is_same<T, float>::value) {
+      if (odd)
+        e = with_rem(logPx - 1, [&](auto tag) {
+          constexpr int REM = decltype(tag)::value;
+          cudaError_t e2 = set_smem(k_r2c_T<T, REM, 0, true>, sm);
+          if (e2 != cudaSuccess) return e2;
+          k_r2c_T<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0],
+                                                                      logPx, skip, b_in);
+          return cudaGetLastError();
+        });
+    }
+    if (!odd)
+      e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
+        constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+        cudaError_t e2 = set_smem(k_r2c_T<T, REM, LL>, sm);
+        if (e2 != cudaSuccess) return e2;
+        k_r2c_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(u, S1, nrows, nx, nx, ld1, logPx - 1, tl, tw[0], logPx, skip, b_in);
+        return cudaGetLastError();
+      });
     if (e != cudaSuccess) return e;
   }
   LamMap map;
@@ -1098,13 +1178,25 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     const int ncols = Hx + 1;
     const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_line_shape<T>(logPy, [&](auto tag) {
-      constexpr int REM = decltype(tag)::rem, LP = decltype(tag)::logp;
-      cudaError_t e2 = set_smem(k_colmul<T, REM, LP>, sm);
-      if (e2 != cudaSuccess) return e2;
-      k_colmul<T, REM, LP><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
-      return cudaGetLastError();
-    });
+    if constexpr (std::is_same<T, float>::value) {
+      if (odd)
+        e = with_rem(logPy, [&](auto tag) {
+          constexpr int REM = decltype(tag)::value;
+          cudaError_t e2 = set_smem(k_colmul<T, REM, 0, true>, sm);
+          if (e2 != cudaSuccess) return e2;
+          k_colmul<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1],
+                                                                       logPy, skip, b_ws);
+          return cudaGetLastError();
+        });
+    }
+    if (!odd)
+      e = with_line_shape<T>(logPy, [&](auto tag) {
+        constexpr int REM = decltype(tag)::rem, LP = decltype(tag)::logp;
+        cudaError_t e2 = set_smem(k_colmul<T, REM, LP>, sm);
+        if (e2 != cudaSuccess) return e2;
+        k_colmul<T, REM, LP><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
+        return cudaGetLastError();
+      });
     if (e != cudaSuccess) return e;
   } else {
     const int Py = p.P[1], Pz = p.P[2];
@@ -1171,13 +1263,25 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
-      constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
-      cudaError_t e2 = set_smem(k_c2r_T<T, REM, LL>, sm);
-      if (e2 != cudaSuccess) return e2;
-      k_c2r_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
-      return cudaGetLastError();
-    });
+    if constexpr (std::is_same<T, float>::value) {
+      if (odd)
+        e = with_rem(logPx - 1, [&](auto tag) {
+          constexpr int REM = decltype(tag)::value;
+          cudaError_t e2 = set_smem(k_c2r_T<T, REM, 0, true>, sm);
+          if (e2 != cudaSuccess) return e2;
+          k_c2r_T<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0],
+                                                                      logPx, skip, b_out);
+          return cudaGetLastError();
+        });
+    }
+    if (!odd)
+      e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
+        constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
+        cudaError_t e2 = set_smem(k_c2r_T<T, REM, LL>, sm);
+        if (e2 != cudaSuccess) return e2;
+        k_c2r_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
+        return cudaGetLastError();
+      });
     if (e != cudaSuccess) return e;
   }
   return mark();
@@ -1185,8 +1289,8 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
 
 template <typename T>
 cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s, const int* skip,
-                         cudaEvent_t const* ev, const T* lam_override) {
-  return apply_launch_b<T>(p, 1, u, y, 0, work, s, skip, 0, ev, lam_override, 0);
+                         cudaEvent_t const* ev, const T* lam_override, bool odd) {
+  return apply_launch_b<T>(p, 1, u, y, 0, work, s, skip, 0, ev, lam_override, 0, odd);
 }
 
 template <typename T>

@@ -433,12 +433,16 @@ cudaError_t twiddle_launch(int P, double2* tw64, float2* tw32, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam, cudaStream_t s) {
+cudaError_t generator_octant_launch(const Plan& p, const double* coef, double* lam, cudaStream_t s) {
   const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1, Hz1 = (p.d == 3) ? p.P[2] / 2 + 1 : 1;
   const size_t total = (size_t)Hx1 * Hy1 * Hz1;
   k_sym_init<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(coef, p.Nmax, p.d, p.n[0], p.n[1],
                                                              p.d == 3 ? p.n[2] : 1, Hx1, Hy1, Hz1, p.c, lam);
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam, cudaStream_t s) {
+  cudaError_t e = generator_octant_launch(p, coef, lam, s);
   if (e != cudaSuccess) return e;
   return symbol_axes_launch(p, lam, s);
 }

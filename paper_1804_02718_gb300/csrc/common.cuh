@@ -266,6 +266,7 @@ struct Plan {
   // preconditioner multipliers (line-major like lam32, FP32; nullptr until built)
   float* mu_strang = nullptr;   // inverse of the multilevel Strang circulant, embedded like A
   float* mu_learned = nullptr;  // learned Fourier multiplier
+  float* mu_tau = nullptr;      // inverse of diag(S A S) in the sine basis S (applied on odd extensions)
   // lines per CTA of each apply stage, per engine (0 FP32, 1 FP64, 2 double-float), set by
   // frlap_plan_autotune; 0 = the built-in choice
   int tl_tuned[3][5] = {};
@@ -290,8 +291,9 @@ cudaError_t wait_selftest(unsigned long long* timeouts);
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
 // T = compute type (float, double or dfl); vectors are io_t<T>, symbol overrides are T
 template <typename T>
+// odd: a multiplier lam_override in the sine basis (2D, FP32, P_r = 2(n_r + 1); see k_r2c_T)
 cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s, const int* skip,
-                         cudaEvent_t const* ev = nullptr, const T* lam_override = nullptr);
+                         cudaEvent_t const* ev = nullptr, const T* lam_override = nullptr, bool odd = false);
 // FP64 vectors through the plan's FP64 engine (native double or double-float)
 cudaError_t apply64(const Plan& p, const double* u, double* y, void* work, cudaStream_t s, const int* skip,
                     cudaEvent_t const* ev = nullptr);
@@ -317,6 +319,8 @@ cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int Nmax,
                           cudaStream_t s);
 size_t coeffs_scratch_bytes(int d, int Nmax);
 cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
+// the generator t_k = -c a_k (k_r <= n_r - 1, zero elsewhere) on the octant, natural order
+cudaError_t generator_octant_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
 // Entries of an FP64 / double-float twiddle table for embedding size P (a power of two >= 32).
 // [0, P): W_P^m = exp(-2 pi i m / P).  Then, for Ns = 1, 2, 4, ..., P/16, the twiddles of a
 // radix-16 Stockham stage with Ns: W_{16 Ns}^{r k} (r = 1..15, k < Ns) at

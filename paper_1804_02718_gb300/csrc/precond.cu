@@ -9,9 +9,21 @@
 // and its octant symbol is stored, so a preconditioner solve costs one FP32
 // apply and needs no FFT of the (generally odd) length n_r.  The size-n_r DFTs
 // of the set-up are direct O(n_r) sums per output in FP64.
+//
+// Sine-basis (tau) preconditioner, 2D.  The multilevel DST-I S (orthonormal sine modes of the box,
+// which vanish on its boundary like u) diagonalises the "tau" matrix algebra; the member closest to A
+// in the Frobenius norm is S diag(S A S) S, and its inverse M = S diag(S A S)^-1 S is the
+// preconditioner.  The diagonal is separable: with t the generator (t_d = -c a_d) and, per axis,
+//   C[k][d] = m_d / (n + 1) * ((n - d) cos(a_k d) + sin(a_k (d + 1)) / sin a_k),  a_k = pi k / (n + 1),
+// (m_0 = 1, m_d = 2 otherwise; the closed form of sum_i s_k(i) s_k(i + d) over the two signs of d),
+// diag(S A S)[k] = sum_d t_d prod_r C_r[k_r][d_r].  Each axis transform is one complex DFT of
+// P = 2(n + 1) points per line (k_tau_axis), so the set-up costs about two symbol transforms.  M is
+// applied as a multiplier on odd extensions to P points through the apply pipeline (its DFT is the
+// DST), one FP32 apply per iteration, and needs P_r = 2 N_r on every axis.
 #include <math.h>
 
 #include "common.cuh"
+#include "fft.cuh"
 
 namespace frlap {
 
@@ -157,6 +169,108 @@ cudaError_t strang_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_h
   double scale = 1.0;
   for (int r = 0; r < p.d; ++r) scale /= (double)p.P[r];
   if ((e = line_symbol_launch<float>(p, oct, p.mu_strang, scale, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+namespace {
+
+// One axis of diag(S A S): for each line v_d (d = 0 .. n-1, stored at entries 0 .. n-1 of the octant
+// line), out_k = sum_d C[k][d] v_d for k = 1 .. n, stored at entries 1 .. n (entries 0 and n + 1 = P/2
+// become 0).  With w1_d = m_d (n - d) v_d and w2_{d+1} = m_d v_d, one P-point DFT F of w1 + i w2 gives
+// the cosine sums A_k = Re DFT(w1)_k and the sine sums B_k = -Im DFT(w2)_k (separated by F_k and
+// conj F_{P-k}); out_k = (A_k + B_k / sin a_k) / (n + 1).  TL lines per CTA of P/16 threads each, in
+// whole warps (the FFT helpers end their short-line stages with warp barriers).
+__global__ void __launch_bounds__(512) k_tau_axis(double* oct, size_t nlines, int logP, size_t stride, size_t inner,
+                                                  int n, int TL, const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = 1 << logP, G = P >> 4, H = P / 2;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const size_t line = (size_t)blockIdx.x * TL + l;
+  const bool valid = line < nlines;
+  double2* buf = reinterpret_cast<double2*>(smem_raw) + (size_t)l * sline(P);
+  const size_t li = valid ? line : 0;
+  const size_t base = (li / inner) * inner * (size_t)(H + 1) + (li % inner);
+  for (int j = lane; j < P; j += G) {
+    const double w1 = (valid && j < n) ? (j == 0 ? 1.0 : 2.0) * (double)(n - j) * oct[base + (size_t)j * stride] : 0.0;
+    const double w2 = (valid && j >= 1 && j <= n) ? (j == 1 ? 1.0 : 2.0) * oct[base + (size_t)(j - 1) * stride] : 0.0;
+    buf[spad(j)] = make_double2(w1, w2);
+  }
+  __syncthreads();
+  fft_line<double, -1>(buf, logP, lane, tw, logP);
+  __syncthreads();
+  if (!valid) return;
+  for (int k = lane; k <= H; k += G) {
+    double out = 0.0;
+    if (k >= 1 && k <= n) {
+      const double2 f = buf[spad(k)], g = buf[spad(P - k)];
+      const double A = 0.5 * (f.x + g.x);  // Re of (F_k + conj F_{P-k}) / 2
+      const double B = 0.5 * (f.x - g.x);  // -Im of (F_k - conj F_{P-k}) / 2i
+      out = (A + B / sinpi((double)k / (n + 1))) / (n + 1);
+    }
+    oct[base + (size_t)k * stride] = out;
+  }
+}
+
+// mu = 1 / diag(S A S) on the modes k_r = 1 .. n_r (0 elsewhere); counts non-positive entries
+__global__ void k_tau_invert(double* oct, size_t total, int Hx1, int nx, int ny, unsigned* bad) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int kx = (int)(i % Hx1), ky = (int)(i / Hx1);
+  double v = 0.0;
+  if (kx >= 1 && kx <= nx && ky >= 1 && ky <= ny) {
+    const double t = oct[i];
+    if (t > 0.0) v = 1.0 / t;
+    else atomicAdd(bad, 1u);
+  }
+  oct[i] = v;
+}
+
+}  // namespace
+
+size_t tau_scratch_bytes(const Plan& p) {
+  const size_t N1 = (size_t)p.Nmax + 1;
+  const size_t ncoef = (p.d == 2) ? N1 * N1 : N1 * N1 * N1;
+  return align256(ncoef * 8) + align256(coeffs_scratch_bytes(p.d, p.Nmax)) + align256(p.lam_count * 8) + 256;
+}
+
+// Builds plan->mu_tau (line-major FP32, the 1/prod(P) of the apply pipeline folded in).  Needs d = 2
+// and P_r = 2 N_r <= 8192 (the caller checks).  *bad_host: entries of diag(S A S) that are not
+// positive (none for a symmetric positive definite A: each is a Rayleigh quotient of A).
+cudaError_t tau_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host) {
+  unsigned char* w = reinterpret_cast<unsigned char*>(scratch);
+  const size_t N1 = (size_t)p.Nmax + 1;
+  const size_t ncoef = (p.d == 2) ? N1 * N1 : N1 * N1 * N1;
+  double* coef = reinterpret_cast<double*>(w);
+  w += align256(ncoef * 8);
+  void* cscratch = w;
+  w += align256(coeffs_scratch_bytes(p.d, p.Nmax));
+  double* oct = reinterpret_cast<double*>(w);
+  w += align256(p.lam_count * 8);
+  unsigned* bad = reinterpret_cast<unsigned*>(w);
+  cudaError_t e = coeffs_launch(p.d, p.alpha, p.gamma, p.h, p.Nmax, coef, cscratch, s);
+  if (e != cudaSuccess) return e;
+  if ((e = generator_octant_launch(p, coef, oct, s)) != cudaSuccess) return e;
+  const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1;
+  const int H1[2] = {Hx1, Hy1};
+  const size_t total = (size_t)Hx1 * Hy1;
+  for (int r = 0; r < 2; ++r) {
+    const size_t stride = r == 0 ? 1 : (size_t)Hx1;
+    const size_t nlines = total / H1[r];
+    const int G = p.P[r] / 16;
+    const int tl = G < 32 ? 32 / G : 1;
+    const size_t sm = (size_t)tl * sline(p.P[r]) * sizeof(double2);
+    if ((e = cudaFuncSetAttribute(k_tau_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+      return e;
+    k_tau_axis<<<(unsigned)((nlines + tl - 1) / tl), tl * G, sm, s>>>(oct, nlines, p.logP[r], stride, stride, p.n[r],
+                                                                     tl, p.tw64[r]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  k_tau_invert<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(oct, total, Hx1, p.n[0], p.n[1], bad);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const double scale = 1.0 / ((double)p.P[0] * p.P[1]);
+  if ((e = line_symbol_launch<float>(p, oct, p.mu_tau, scale, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }

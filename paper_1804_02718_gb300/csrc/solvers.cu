@@ -421,19 +421,21 @@ static CgBufs carve(const Plan& p, void* work, int eb) {
   return b;
 }
 
-// z32 = M^-1 r: one FP32 apply with the preconditioner symbol mu (skipped once done)
+// z32 = M^-1 r: one FP32 apply with the preconditioner symbol mu (skipped once done); the plan's
+// sine-basis multiplier runs on odd extensions
 template <typename T>
 static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu, cudaStream_t st) {
+  const bool odd = mu != nullptr && mu == p.mu_tau;
   const float* src;
   if constexpr (sizeof(T) == 8) {
     k_to32<T><<<vgrid(p.M), kThreads, 0, st>>>(reinterpret_cast<const T*>(b.r), b.r32, p.M, b.S);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     src = b.r32;
-    return apply_launch<float>(p, src, b.z32, b.awork32, st, &b.S->done, nullptr, mu);
+    return apply_launch<float>(p, src, b.z32, b.awork32, st, &b.S->done, nullptr, mu, odd);
   } else {
     src = reinterpret_cast<const float*>(b.r);
-    return apply_launch<float>(p, src, b.z32, b.awork, st, &b.S->done, nullptr, mu);
+    return apply_launch<float>(p, src, b.z32, b.awork, st, &b.S->done, nullptr, mu, odd);
   }
 }
 

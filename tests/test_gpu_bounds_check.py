@@ -3,8 +3,8 @@
 In that build every global load and store of the apply kernels is first tested against the buffers
 its call registered; an access outside them is skipped and counted, so an indexing error shows up as
 a count instead of a fault.  The test builds the library, runs the checker's self-test and the small
-parity cases (all three engines, 2D and 3D, rectangular and ragged shapes, batched applies, the
-preconditioners, the learned multiplier's spectra, CG and the batched Allen-Cahn loop) in a child
+parity cases (all three engines, 2D and 3D, rectangular and ragged shapes, batched applies, 16384-point
+embeddings, the preconditioners, the learned multiplier's spectra, CG and the batched Allen-Cahn loop) in a child
 process that loads it, and expects every result to match the oracle and no access to be flagged.
 """
 import os
@@ -66,6 +66,17 @@ def _child():
                 x, it, rel, code = fl.frlap_pcg_solve(plan, f, rtol=1e-10, precond=fl.FRLAP_PRECOND_LEARNED)
                 assert code == 0 and rel <= 1e-10
             torch.cuda.synchronize()
+    # 16384-point embeddings: the split middle stage and symbol transform (y), 8192-point rows (x)
+    h = 2.0 / 4200
+    a, c = scheme.coefficients(2, 1.3, h, 4200), scheme.c_d_alpha(2, 1.3)
+    for Ns in ((40, 4200), (4200, 40)):
+        u = inp.normal_field(Ns, seed=77)
+        op = fast.FastOperator(a, c, u.shape)
+        for prec, tol in ((1, 1e-5), (3, 1e-12)):
+            plan = fl.Plan(2, 1.3, h, Ns, prec=prec)
+            dt = torch.float32 if prec == 1 else torch.float64
+            y = fl.frlap_apply(plan, torch.from_numpy(u).to("cuda", dt)).double().cpu().numpy()
+            assert np.linalg.norm(y - op(u)) <= tol * op.lam_max * np.linalg.norm(u), (Ns, prec)
     # the learned preconditioner's spectra (forward transform, multiplied inverse) and its training pairs
     plan = fl.Plan(2, 1.2, 2.0 / 32, (32, 32))
     pset = learned.PairSet(2, 1.2, 32, [inp.gaussian_sum_field((32, 32), 2.0 / 32, seed=6)], K=50)
