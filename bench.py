@@ -605,7 +605,7 @@ def run_pcg_rows(fl, torch, params_trained, d, N, alpha, seed=1):
     f = torch.from_numpy(inp.gaussian_sum_field(Ns, h, seed=seed)).cuda()
     F64, DF, MX = fl.FRLAP_F64, fl.FRLAP_DF64, fl.FRLAP_MIXED_DF64
     CG, IR = fl.FRLAP_SOLVE_CG, fl.FRLAP_SOLVE_IR
-    NONE, STR, LRN = fl.FRLAP_PRECOND_NONE, fl.FRLAP_PRECOND_STRANG, fl.FRLAP_PRECOND_LEARNED
+    NONE, STR, LRN, TAU = fl.FRLAP_PRECOND_NONE, fl.FRLAP_PRECOND_STRANG, fl.FRLAP_PRECOND_LEARNED, fl.FRLAP_PRECOND_TAU
     ref_plan = fl.Plan(d, alpha, h, Ns, prec=F64)
     fl.frlap_precond_strang(ref_plan)
     x_ref, it_ref, rel_ref, code_ref = fl.frlap_pcg_solve(ref_plan, f, rtol=1e-11, precond=STR, raise_on_error=False)
@@ -617,7 +617,9 @@ def run_pcg_rows(fl, torch, params_trained, d, N, alpha, seed=1):
             ("pcg_learned_trained_df64", DF, CG, LRN, "trained"),
             ("ir_strang_fp32inner", MX, IR, STR, None),
             ("ir_learned_untrained_fp32inner", MX, IR, LRN, "untrained"),
-            ("ir_learned_trained_fp32inner", MX, IR, LRN, "trained")]
+            ("ir_learned_trained_fp32inner", MX, IR, LRN, "trained"),
+            ("pcg_tau_df64", DF, CG, TAU, None),
+            ("ir_tau_fp32inner", MX, IR, TAU, None)]
     out = {"workload": f"{d}D {N - 1}^{d} alpha={alpha} Gaussian-sum f (seed {seed}), rtol 1e-10 (true residual)",
            "reference": {"iters": it_ref, "relres": rel_ref, "status": code_ref,
                          "how": "native FP64 plan, Strang PCG to 1e-11"}}
@@ -626,6 +628,8 @@ def run_pcg_rows(fl, torch, params_trained, d, N, alpha, seed=1):
         fl.frlap_plan_autotune(plan, 1)  # launch shapes (not part of the solve time)
         if pre == STR:
             fl.frlap_precond_strang(plan)
+        elif pre == TAU:
+            fl.frlap_precond_tau(plan)
         elif pre == LRN:
             learned.install(plan, learned.init_params(0) if which == "untrained" else params_trained)
         plan.workspace(fl.FRLAP_OP_PCG)
@@ -716,6 +720,8 @@ def run_solver_suite(args):
             fl.frlap_plan_autotune(plan, 1)  # launch shapes (not part of the solve time)
             if pre == fl.FRLAP_PRECOND_STRANG:
                 fl.frlap_precond_strang(plan)
+            elif pre == fl.FRLAP_PRECOND_TAU:
+                fl.frlap_precond_tau(plan)
             elif pre == fl.FRLAP_PRECOND_LEARNED:
                 learned.install(plan, params)
             plan.workspace(fl.FRLAP_OP_PCG)
@@ -735,10 +741,12 @@ def run_solver_suite(args):
     F64, DF, MX = fl.FRLAP_F64, fl.FRLAP_DF64, fl.FRLAP_MIXED_DF64
     CG, IR = fl.FRLAP_SOLVE_CG, fl.FRLAP_SOLVE_IR
     NONE, STR, LRN = fl.FRLAP_PRECOND_NONE, fl.FRLAP_PRECOND_STRANG, fl.FRLAP_PRECOND_LEARNED
+    TAU = fl.FRLAP_PRECOND_TAU
     full = [("plain_cg_fp64", F64, CG, NONE), ("plain_cg_df64", DF, CG, NONE), ("pcg_strang_df64", DF, CG, STR),
-            ("pcg_learned_df64", DF, CG, LRN), ("ir_learned_fp32inner", MX, IR, LRN)]
+            ("pcg_learned_df64", DF, CG, LRN), ("ir_learned_fp32inner", MX, IR, LRN), ("pcg_tau_df64", DF, CG, TAU),
+            ("ir_tau_fp32inner", MX, IR, TAU)]
     fast = [("pcg_strang_df64", DF, CG, STR), ("pcg_learned_df64", DF, CG, LRN), ("ir_strang_fp32inner", MX, IR, STR),
-            ("ir_learned_fp32inner", MX, IR, LRN)]
+            ("ir_learned_fp32inner", MX, IR, LRN), ("pcg_tau_df64", DF, CG, TAU), ("ir_tau_fp32inner", MX, IR, TAU)]
     out["2d_2047_alpha1.5"] = solve_row(2, 2048, 1.5, 1, full)
     for al in (0.5, 1.0, 1.5, 1.9):
         out[f"3d_255_alpha{al}"] = solve_row(3, 256, al, 1, full if al in (1.0, 1.9) else fast)

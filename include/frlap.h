@@ -247,15 +247,15 @@ frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* 
  * *n_nonpositive (may be NULL).  Synchronises stream. */
 frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* stream);
 
-/* Build the sine-basis ("tau") preconditioner of a 2D plan (set-up call: allocates the
+/* Build the sine-basis ("tau") preconditioner of the plan (set-up call: allocates the
  * multiplier and temporary scratch).  S, the orthonormal multilevel DST-I, holds the sine
  * modes of the box, which vanish on its boundary as u does; M = S diag(S A S)^-1 S is the
  * inverse of the member of the algebra S diagonalises that is closest to A in the
  * Frobenius norm.  diag(S A S) is computed from the coefficients by one P-point DFT per
  * line and axis; M is applied on odd extensions of the vector to P = 2 N_r points per
  * axis (whose DFT is the DST) through the apply pipeline, one FP32 apply per iteration.
- * Needs d = 2 and every N[r] a power of two in [16, 4096] (so that P_r = 2 N_r), else
- * FRLAP_EINVAL.  Entries of diag(S A S) are Rayleigh quotients of A, positive for this
+ * Needs every N[r] a power of two of at least 16 (so that P_r = 2 N_r; 2D N[r] <= 4096),
+ * else FRLAP_EINVAL.  Entries of diag(S A S) are Rayleigh quotients of A, positive for this
  * operator; non-positive ones would be dropped and are counted in *n_nonpositive (may be
  * NULL).  Synchronises stream. */
 frlap_status frlap_precond_tau(frlap_plan* plan, int* n_nonpositive, void* stream);

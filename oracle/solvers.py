@@ -97,21 +97,22 @@ def sine_modes(n: int) -> np.ndarray:
 
 
 def tau_symbol_by_modes(apply, shape) -> np.ndarray:
-    """diag(S A S)[k] = s_k^T A s_k, one apply of A per 2D sine mode s_k = s_{k_y} (x) s_{k_x}."""
-    ny, nx = shape
-    Sy, Sx = sine_modes(ny), sine_modes(nx)
-    out = np.empty((ny, nx))
-    for ky in range(ny):
-        for kx in range(nx):
-            mode = np.outer(Sy[ky], Sx[kx])
-            out[ky, kx] = float(np.sum(mode * apply(mode)))
+    """diag(S A S)[k] = s_k^T A s_k, one apply of A per sine mode s_k (the outer product of one mode per
+    axis; shape is the grid's C-order shape, 2D or 3D)."""
+    S = [sine_modes(n) for n in shape]
+    out = np.empty(shape)
+    for k in np.ndindex(*shape):
+        mode = S[0][k[0]]
+        for r in range(1, len(shape)):
+            mode = np.multiply.outer(mode, S[r][k[r]])
+        out[k] = float(np.sum(mode * apply(mode)))
     return out
 
 
 def tau_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
-    """diag(S A S) for the 2D Toeplitz A (A[i, j] = t_{|i - j|}, t = -c coef): the quadratic forms
-    s_k^T A s_k = sum over offsets d of t_{|d|} prod_r sum_i s_{k_r}(i) s_{k_r}(i + d_r), where per
-    axis the inner sum over both signs of d is
+    """diag(S A S) for the multilevel Toeplitz A (A[i, j] = t_{|i - j|}, t = -c coef; 2D or 3D): the
+    quadratic forms s_k^T A s_k = sum over offsets d of t_{|d|} prod_r sum_i s_{k_r}(i) s_{k_r}(i + d_r),
+    where per axis the inner sum over both signs of d is
     C[k][d] = m_d/(n+1) ((n - d) cos(a d) + sin(a (d+1))/sin(a)), a = pi k/(n+1), m_0 = 1, m_d = 2."""
     def cmat(n):
         k = np.arange(1, n + 1)[:, None]
@@ -119,9 +120,10 @@ def tau_symbol(coef: np.ndarray, c: float, shape) -> np.ndarray:
         a = np.pi * k / (n + 1)
         m = np.where(d == 0, 1.0, 2.0)
         return m / (n + 1) * ((n - d) * np.cos(a * d) + np.sin(a * (d + 1)) / np.sin(a))
-    ny, nx = shape
-    t = -c * coef[:ny, :nx]
-    return cmat(ny) @ t @ cmat(nx).T
+    out = -c * coef[tuple(slice(0, n) for n in shape)]
+    for r, n in enumerate(shape):  # contract axis r of the offsets with C_r
+        out = np.moveaxis(np.tensordot(cmat(n), out, axes=([1], [r])), 0, r)
+    return out
 
 
 def tau_solve(tau: np.ndarray, r: np.ndarray) -> np.ndarray:

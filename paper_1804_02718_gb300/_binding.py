@@ -385,7 +385,7 @@ def frlap_precond_strang(plan: Plan, stream=None) -> int:
 
 
 def frlap_precond_tau(plan: Plan, stream=None) -> int:
-    """Build the sine-basis (tau) preconditioner of a 2D plan; returns the number of dropped non-positive entries."""
+    """Build the sine-basis (tau) preconditioner; returns the number of dropped non-positive entries."""
     bad = ctypes.c_int(0)
     _check(lib().frlap_precond_tau(plan.handle, ctypes.byref(bad), _stream(stream)), "frlap_precond_tau")
     return bad.value

@@ -607,10 +607,10 @@ frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* st
 
 frlap_status frlap_precond_tau(frlap_plan* plan, int* n_nonpositive, void* stream) {
   if (!plan) return fail(FRLAP_EINVAL, "plan is NULL");
-  if (plan->d != 2) return fail(FRLAP_EINVAL, "the sine-basis preconditioner is built for 2D plans");
   for (int r = 0; r < plan->d; ++r)
     if (plan->P[r] != 2 * plan->N[r] || plan->P[r] > kMaxLine)
-      return fail(FRLAP_EINVAL, "the sine-basis preconditioner needs every N[r] a power of two in [16, 4096]");
+      return fail(FRLAP_EINVAL, "the sine-basis preconditioner needs every N[r] a power of two of at least 16 "
+                                "(and at most 4096)");
   cudaStream_t s = (cudaStream_t)stream;
   if (!plan->mu_tau && cudaMalloc(&plan->mu_tau, plan->lam_count * sizeof(float)) != cudaSuccess)
     return fail(FRLAP_ENOMEM, "sine-basis multiplier allocation failed");

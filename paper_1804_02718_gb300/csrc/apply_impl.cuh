@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
 }
 
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
-template <typename T, int REM, int LOGL = 0>
+template <typename T, int REM, int LOGL = 0, bool ODD = false>
 __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
@@ -781,12 +781,26 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __res
   C* buf = smem + (size_t)l * LS;
   const C* src = in + g * gin + (size_t)(valid ? line : 0) * ldi;
   C v[16];
+  if constexpr (ODD) {  // the line's odd extension to P = 2(n + 1) points (see k_r2c_T)
+    const int H = P >> 1;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int i = lane + m * G;
-    v[m] = (m < 8 && valid && i < n) ? FRLAP_GLD(src + i) : czero<C>();
+    for (int m = 0; m < 16; ++m) {
+      const int j = lane + m * G;
+      C x = czero<C>();
+      if (valid) {
+        if (j >= 1 && j <= n) x = FRLAP_GLD(src + (j - 1));
+        else if (j > H && 2 * H - j - 1 < n) x = czero<C>() - FRLAP_GLD(src + (2 * H - j - 1));
+      }
+      v[m] = x;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int i = lane + m * G;
+      v[m] = (m < 8 && valid && i < n) ? FRLAP_GLD(src + i) : czero<C>();
+    }
   }
-  fft_regs<T, -1, true, REM>(v, buf, logP, lane, tw, logPtab, false);
+  fft_regs<T, -1, !ODD, REM>(v, buf, logP, lane, tw, logPtab, false);
   line_sync<T>(logP);
 #pragma unroll
   for (int m = 0; m < 16; ++m) buf[spad(lane + m * G)] = v[m];
@@ -805,7 +819,7 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __res
 }
 
 // transposed in[g][k][line] (k < P) -> IFFT along k, crop to n, store out[g][line][i]
-template <typename T, int REM, int LOGL = 0>
+template <typename T, int REM, int LOGL = 0, bool ODD = false>
 __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_inv(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
                            size_t gin, int ldi, size_t gout, int ldo, int logP, int TL,
                            const cplx<T>* __restrict__ tw, int logPtab, const int* __restrict__ skip, Batch bt) {
@@ -844,7 +858,11 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_inv(const cplx<T>* __res
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int i = lane + m * G;
-      if (i < n) FRLAP_GST(dst + i, v[m]);
+      if (ODD) {  // outputs 1 .. n of the odd extension, at offset -1
+        if (i >= 1 && i <= n) FRLAP_GST(dst + (i - 1), v[m]);
+      } else if (i < n) {
+        FRLAP_GST(dst + i, v[m]);
+      }
     }
   }
 }
@@ -1050,9 +1068,9 @@ template <typename T>
 static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
                                   cudaStream_t s, const int* skip, int skip_stride, cudaEvent_t const* ev,
                                   const T* lam_override, size_t lam_stride, bool odd = false) {
-  // odd: the 2D pipeline on odd extensions (a multiplier in the sine basis, see k_r2c_T); FP32 plans'
-  // engine only, 2D, P_r = 2(n_r + 1) on both axes (the callers check)
-  if (odd && (!std::is_same<T, float>::value || p.d != 2 || p.P[1] > kMaxLine)) return cudaErrorNotSupported;
+  // odd: the pipeline on odd extensions (a multiplier in the sine basis, see k_r2c_T); the FP32
+  // engine only, P_r = 2(n_r + 1) on every axis (the callers check)
+  if (odd && (!std::is_same<T, float>::value || p.P[1] > kMaxLine)) return cudaErrorNotSupported;
   int stage = 0;
   auto mark = [&]() -> cudaError_t {
     if (ev && ev[stage]) {
@@ -1209,6 +1227,19 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
     if ((e = mark()) != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+      if (odd)
+        e = with_rem(logPy, [&](auto tag) {
+          constexpr int REM = decltype(tag)::value;
+          cudaError_t e2 = set_smem(k_c2cT_fwd<T, REM, 0, true>, sm);
+          if (e2 != cudaSuccess) return e2;
+          k_c2cT_fwd<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, nz, tiles, ny, (size_t)nz * ny, ny,
+                                                                         (size_t)Py * nz, nz, logPy, tl, tw[1], logPy,
+                                                                         skip, b_ws);
+          return cudaGetLastError();
+        });
+    }
+    if (!odd)
     e = with_line_shape<T, std::is_same<T, float>::value>(logPy, [&](auto tag) {
       constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
       cudaError_t e2 = set_smem(k_c2cT_fwd<T, REM, LL>, sm);
@@ -1227,6 +1258,18 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int ncols = (Hx + 1) * Py;
       const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+      if (odd)
+        e = with_rem(logPz, [&](auto tag) {
+          constexpr int REM = decltype(tag)::value;
+          cudaError_t e2 = set_smem(k_colmul<T, REM, 0, true>, sm);
+          if (e2 != cudaSuccess) return e2;
+          k_colmul<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map,
+                                                                       tw[2], logPz, skip, b_ws);
+          return cudaGetLastError();
+        });
+    }
+    if (!odd)
     e = with_line_shape<T>(logPz, [&](auto tag) {
       constexpr int REM = decltype(tag)::rem, LP = decltype(tag)::logp;
       cudaError_t e2 = set_smem(k_colmul<T, REM, LP>, sm);
@@ -1245,6 +1288,19 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
     if ((e = mark()) != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+      if (odd)
+        e = with_rem(logPy, [&](auto tag) {
+          constexpr int REM = decltype(tag)::value;
+          cudaError_t e2 = set_smem(k_c2cT_inv<T, REM, 0, true>, sm);
+          if (e2 != cudaSuccess) return e2;
+          k_c2cT_inv<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz,
+                                                                         (size_t)nz * ny, ny, logPy, tl, tw[1], logPy,
+                                                                         skip, b_ws);
+          return cudaGetLastError();
+        });
+    }
+    if (!odd)
     e = with_line_shape<T, std::is_same<T, float>::value>(logPy, [&](auto tag) {
       constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
       cudaError_t e2 = set_smem(k_c2cT_inv<T, REM, LL>, sm);

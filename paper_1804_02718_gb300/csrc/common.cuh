@@ -291,7 +291,7 @@ cudaError_t wait_selftest(unsigned long long* timeouts);
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
 // T = compute type (float, double or dfl); vectors are io_t<T>, symbol overrides are T
 template <typename T>
-// odd: a multiplier lam_override in the sine basis (2D, FP32, P_r = 2(n_r + 1); see k_r2c_T)
+// odd: a multiplier lam_override in the sine basis (FP32, P_r = 2(n_r + 1); see k_r2c_T)
 cudaError_t apply_launch(const Plan& p, const io_t<T>* u, io_t<T>* y, void* work, cudaStream_t s, const int* skip,
                          cudaEvent_t const* ev = nullptr, const T* lam_override = nullptr, bool odd = false);
 // FP64 vectors through the plan's FP64 engine (native double or double-float)

@@ -10,7 +10,7 @@
 // apply and needs no FFT of the (generally odd) length n_r.  The size-n_r DFTs
 // of the set-up are direct O(n_r) sums per output in FP64.
 //
-// Sine-basis (tau) preconditioner, 2D.  The multilevel DST-I S (orthonormal sine modes of the box,
+// Sine-basis (tau) preconditioner.  The multilevel DST-I S (orthonormal sine modes of the box,
 // which vanish on its boundary like u) diagonalises the "tau" matrix algebra; the member closest to A
 // in the Frobenius norm is S diag(S A S) S, and its inverse M = S diag(S A S)^-1 S is the
 // preconditioner.  The diagonal is separable: with t the generator (t_d = -c a_d) and, per axis,
@@ -212,13 +212,14 @@ __global__ void __launch_bounds__(512) k_tau_axis(double* oct, size_t nlines, in
   }
 }
 
-// mu = 1 / diag(S A S) on the modes k_r = 1 .. n_r (0 elsewhere); counts non-positive entries
-__global__ void k_tau_invert(double* oct, size_t total, int Hx1, int nx, int ny, unsigned* bad) {
+// mu = 1 / diag(S A S) on the modes k_r = 1 .. n_r (0 elsewhere); counts non-positive entries.
+// 2D: Hy1 = total / Hx1 and nz = 0 (no z axis).
+__global__ void k_tau_invert(double* oct, size_t total, int Hx1, int Hy1, int nx, int ny, int nz, unsigned* bad) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
-  const int kx = (int)(i % Hx1), ky = (int)(i / Hx1);
+  const int kx = (int)(i % Hx1), ky = (int)((i / Hx1) % Hy1), kz = (int)(i / ((size_t)Hx1 * Hy1));
   double v = 0.0;
-  if (kx >= 1 && kx <= nx && ky >= 1 && ky <= ny) {
+  if (kx >= 1 && kx <= nx && ky >= 1 && ky <= ny && (nz == 0 ? kz == 0 : (kz >= 1 && kz <= nz))) {
     const double t = oct[i];
     if (t > 0.0) v = 1.0 / t;
     else atomicAdd(bad, 1u);
@@ -234,8 +235,8 @@ size_t tau_scratch_bytes(const Plan& p) {
   return align256(ncoef * 8) + align256(coeffs_scratch_bytes(p.d, p.Nmax)) + align256(p.lam_count * 8) + 256;
 }
 
-// Builds plan->mu_tau (line-major FP32, the 1/prod(P) of the apply pipeline folded in).  Needs d = 2
-// and P_r = 2 N_r <= 8192 (the caller checks).  *bad_host: entries of diag(S A S) that are not
+// Builds plan->mu_tau (line-major FP32, the 1/prod(P) of the apply pipeline folded in).  Needs
+// P_r = 2 N_r <= 8192 on every axis (the caller checks).  *bad_host: entries of diag(S A S) that are not
 // positive (none for a symmetric positive definite A: each is a Rayleigh quotient of A).
 cudaError_t tau_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host) {
   unsigned char* w = reinterpret_cast<unsigned char*>(scratch);
@@ -251,11 +252,12 @@ cudaError_t tau_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host
   cudaError_t e = coeffs_launch(p.d, p.alpha, p.gamma, p.h, p.Nmax, coef, cscratch, s);
   if (e != cudaSuccess) return e;
   if ((e = generator_octant_launch(p, coef, oct, s)) != cudaSuccess) return e;
-  const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1;
-  const int H1[2] = {Hx1, Hy1};
-  const size_t total = (size_t)Hx1 * Hy1;
-  for (int r = 0; r < 2; ++r) {
-    const size_t stride = r == 0 ? 1 : (size_t)Hx1;
+  const int Hx1 = p.P[0] / 2 + 1, Hy1 = p.P[1] / 2 + 1, Hz1 = p.d == 3 ? p.P[2] / 2 + 1 : 1;
+  const int H1[3] = {Hx1, Hy1, Hz1};
+  const size_t total = (size_t)Hx1 * Hy1 * Hz1;
+  for (int r = 0; r < p.d; ++r) {
+    size_t stride = 1;
+    for (int q = 0; q < r; ++q) stride *= H1[q];
     const size_t nlines = total / H1[r];
     const int G = p.P[r] / 16;
     const int tl = G < 32 ? 32 / G : 1;
@@ -267,9 +269,11 @@ cudaError_t tau_build(Plan& p, void* scratch, cudaStream_t s, unsigned* bad_host
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-  k_tau_invert<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(oct, total, Hx1, p.n[0], p.n[1], bad);
+  k_tau_invert<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(oct, total, Hx1, Hy1, p.n[0], p.n[1],
+                                                               p.d == 3 ? p.n[2] : 0, bad);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const double scale = 1.0 / ((double)p.P[0] * p.P[1]);
+  double scale = 1.0;
+  for (int r = 0; r < p.d; ++r) scale /= (double)p.P[r];
   if ((e = line_symbol_launch<float>(p, oct, p.mu_tau, scale, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);

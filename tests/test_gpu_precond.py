@@ -90,15 +90,17 @@ def test_preconditioned_refinement(frlap):
     assert np.linalg.norm(x.cpu().numpy() - x_exact) <= 1e-10 * np.linalg.norm(x_exact)
 
 
-@pytest.mark.parametrize("Ns,alpha", [((64, 64), 1.5), ((128, 32), 0.8), ((16, 256), 1.9)])
+@pytest.mark.parametrize("Ns,alpha", [((64, 64), 1.5), ((128, 32), 0.8), ((16, 256), 1.9), ((16, 32, 16), 1.2),
+                                      ((32, 16, 64), 1.7)])
 def test_tau_preconditioner_matches_oracle(frlap, Ns, alpha):
     """z = S diag(S A S)^-1 S r on the GPU (FP32, odd extensions through the apply pipeline) against the
-    oracle's DST-I solve with its closed-form diagonal."""
+    oracle's DST-I solve with its closed-form diagonal, 2D and 3D."""
+    d = len(Ns)
     h = 2.0 / max(Ns)
-    a, c = _coef(2, alpha, h, max(Ns)), scheme.c_d_alpha(2, alpha)
+    a, c = _coef(d, alpha, h, max(Ns)), scheme.c_d_alpha(d, alpha)
     shape = tuple(n - 1 for n in reversed(Ns))
     tau = solvers.tau_symbol(a, c, shape)
-    plan = frlap.Plan(2, alpha, h, Ns, prec=frlap.FRLAP_MIXED)
+    plan = frlap.Plan(d, alpha, h, Ns, prec=frlap.FRLAP_MIXED)
     assert frlap.frlap_precond_tau(plan) == 0
     for seed in (1, 2):
         r = inp.normal_field(Ns, seed=seed)
@@ -107,20 +109,21 @@ def test_tau_preconditioner_matches_oracle(frlap, Ns, alpha):
         assert np.linalg.norm(z - z_ref) <= 1e-5 * np.linalg.norm(z_ref), seed
 
 
-@pytest.mark.parametrize("prec,solver", [(3, 0), (4, 1)])
-def test_tau_pcg_matches_oracle_solve(frlap, prec, solver):
+@pytest.mark.parametrize("Ns,prec,solver", [((256, 256), 3, 0), ((256, 256), 4, 1), ((64, 64, 64), 3, 0),
+                                            ((64, 64, 64), 4, 1)])
+def test_tau_pcg_matches_oracle_solve(frlap, Ns, prec, solver):
     """PCG (double-float plan) and FP32-inner refinement (mixed plan) with the sine-basis preconditioner
-    on the 255^2, alpha = 1.5 Poisson problem: a few iterations, and the solution within 1e-10 of the
-    oracle's FP64 solve (CG preconditioned by the oracle's own tau solve, to 1e-12)."""
-    Ns, alpha = (256, 256), 1.5
-    h = 2.0 / 256
-    a, c = _coef(2, alpha, h, 256), scheme.c_d_alpha(2, alpha)
-    shape = (255, 255)
+    on the 255^2 and 63^3, alpha = 1.5 Poisson problems: a few iterations, and the solution within 1e-10
+    of the oracle's FP64 solve (CG preconditioned by the oracle's own tau solve, to 1e-12)."""
+    d, alpha = len(Ns), 1.5
+    h = 2.0 / Ns[0]
+    a, c = _coef(d, alpha, h, Ns[0]), scheme.c_d_alpha(d, alpha)
+    shape = tuple(n - 1 for n in Ns)
     f = inp.gaussian_sum_field(Ns, h, seed=1)
     op = fast.FastOperator(a, c, shape)
     tau = solvers.tau_symbol(a, c, shape)
     x_ref, it_ref, _ = solvers.cg(op, f, rtol=1e-12, precond=lambda r: solvers.tau_solve(tau, r))
-    plan = frlap.Plan(2, alpha, h, Ns, prec=prec)
+    plan = frlap.Plan(d, alpha, h, Ns, prec=prec)
     frlap.frlap_precond_tau(plan)
     x, it, rel, code = frlap.frlap_pcg_solve(plan, _t(f), rtol=1e-10, solver=solver, precond=frlap.FRLAP_PRECOND_TAU,
                                              inner_rtol=1e-4)
@@ -131,8 +134,15 @@ def test_tau_pcg_matches_oracle_solve(frlap, prec, solver):
 
 
 def test_tau_preconditioner_refusals(frlap):
-    """2D plans whose N is not a power of two (P_r != 2 N_r) and 3D plans are refused before any launch."""
+    """Plans with an N that is not a power of two of at least 16 (P_r != 2 N_r) are refused before any
+    launch, and a solve asking for the preconditioner before it is built is refused."""
     with pytest.raises(frlap.FrlapError):
         frlap.frlap_precond_tau(frlap.Plan(2, 1.2, 2.0 / 100, (100, 64)))
     with pytest.raises(frlap.FrlapError):
-        frlap.frlap_precond_tau(frlap.Plan(3, 1.2, 2.0 / 16, (16, 16, 16)))
+        frlap.frlap_precond_tau(frlap.Plan(3, 1.2, 2.0 / 16, (16, 16, 12)))
+    with pytest.raises(frlap.FrlapError):
+        frlap.frlap_precond_tau(frlap.Plan(2, 1.2, 2.0 / 8, (8, 8)))
+    plan = frlap.Plan(2, 1.2, 2.0 / 64, (64, 64))
+    with pytest.raises(frlap.FrlapError):
+        frlap.frlap_pcg_solve(plan, torch.ones(plan.shape, dtype=torch.float64, device="cuda"),
+                              precond=frlap.FRLAP_PRECOND_TAU)

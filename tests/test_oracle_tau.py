@@ -1,5 +1,5 @@
 """Pins of the oracle's sine-basis (tau) preconditioner, M = S diag(S A S)^-1 S with S the
-orthonormal 2D DST-I (oracle/solvers.py).  The paper has no preconditioner; these check the oracle
+orthonormal multilevel DST-I (oracle/solvers.py).  The paper has no preconditioner; these check the oracle
 against its definition and against what the mathematics fixes:
 * the closed-form quadratic forms equal s_k^T A s_k formed with the dense matrix of the scheme;
 * tau_solve equals S diag(tau)^-1 S with the sine modes written out;
@@ -17,10 +17,12 @@ def _op(alpha, N, shape):
     return a, scheme.c_d_alpha(2, alpha)
 
 
-@pytest.mark.parametrize("alpha,shape", [(0.5, (7, 9)), (1.3, (11, 6)), (1.9, (8, 8))])
+@pytest.mark.parametrize("alpha,shape", [(0.5, (7, 9)), (1.3, (11, 6)), (1.9, (8, 8)), (1.1, (4, 6, 5)),
+                                         (1.8, (5, 5, 3))])
 def test_tau_symbol_is_the_quadratic_forms_of_the_dense_matrix(alpha, shape):
     N = max(shape) + 1
-    a, c = _op(alpha, N, shape)
+    a = scheme.coefficients(len(shape), alpha, 2.0 / N, N)
+    c = scheme.c_d_alpha(len(shape), alpha)
     by_modes = solvers.tau_symbol_by_modes(lambda u: scheme.apply_dense(a, c, u), shape)
     closed = solvers.tau_symbol(a, c, shape)
     assert np.abs(closed - by_modes).max() <= 1e-13 * np.abs(by_modes).max()
