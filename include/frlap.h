@@ -277,8 +277,10 @@ frlap_status frlap_precond_set_symbol(frlap_plan* plan, const double* d_m, void*
  * (I + tau eps^2 A) u^{n+1} = u^n + tau (u^n - (u^n)^3), each solved by CG
  * from u^n to relative residual rtol (the paper's model, eqs. AC-1/AC-2, steps
  * with Crank-Nicolson and CG; this is the semi-implicit form of the same
- * space discretisation).  d_u: prod(n_r) doubles, updated in place.
- * *iters (may be NULL): total CG iterations.  Synchronises stream. */
+ * space discretisation).  When the plan's sine-basis preconditioner is built
+ * (frlap_precond_tau), each solve is PCG with S diag(1 + tau eps^2 S A S)^-1 S.
+ * d_u: prod(n_r) doubles, updated in place.  *iters (may be NULL): total CG
+ * iterations.  Synchronises stream. */
 frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double tau, double eps, int nsteps,
                                    double rtol, int* iters, void* d_work, void* stream);
 
@@ -289,7 +291,8 @@ frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double t
  *   (I + tau/2 A) ubar^{n+1} = (I - tau/2 A) ubar^n - tau delta^{-alpha} u^n ((u^n)^2 - 1)
  * by CG from ubar^n to relative residual rtol (the reaction term taken at t_n: the
  * paper states Crank-Nicolson with one CG solve per step but not how the reaction
- * enters).  d_ubar: prod(n_r) doubles, updated in place.  h_mass (host, may be NULL):
+ * enters; with the plan's sine-basis preconditioner built (frlap_precond_tau), PCG with
+ * S diag(1 + tau/2 S A S)^-1 S).  d_ubar: prod(n_r) doubles, updated in place.  h_mass (host, may be NULL):
  * nsteps doubles, h^d sum ubar after each step (the bubbles' area or volume).
  * *iters (may be NULL): total CG iterations.  d_work: frlap_workspace_bytes(plan,
  * FRLAP_OP_AC) bytes.  Synchronises stream.  F32 plans are refused (FRLAP_EINVAL). */

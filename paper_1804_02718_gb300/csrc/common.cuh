@@ -319,6 +319,9 @@ cudaError_t coeffs_launch(int d, double alpha, double gamma, double h, int Nmax,
                           cudaStream_t s);
 size_t coeffs_scratch_bytes(int d, int Nmax);
 cudaError_t symbol_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
+// the sine-basis preconditioner of sigma I + s A from the plan's mu_tau (built), into mu_b
+// (lam_count floats, line-major like mu_tau)
+cudaError_t shifted_tau_launch(const Plan& p, double sigma, double s, float* mu_b, cudaStream_t st);
 // the generator t_k = -c a_k (k_r <= n_r - 1, zero elsewhere) on the octant, natural order
 cudaError_t generator_octant_launch(const Plan& p, const double* coef, double* lam_oct, cudaStream_t s);
 // Entries of an FP64 / double-float twiddle table for embedding size P (a power of two >= 32).

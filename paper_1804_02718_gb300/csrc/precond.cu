@@ -229,6 +229,25 @@ __global__ void k_tau_invert(double* oct, size_t total, int Hx1, int Hy1, int nx
 
 }  // namespace
 
+namespace {
+// mu_b = scale / (sigma + s tau) from mu = scale / tau (0 stays 0): the sine-basis preconditioner of
+// sigma I + s A, whose diagonal in the sine basis is sigma + s diag(S A S)
+__global__ void k_tau_shift(const float* __restrict__ mu, float* __restrict__ mu_b, size_t n, double scale,
+                            double sigma, double s) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double m = mu[i];
+  mu_b[i] = m == 0.0 ? 0.0f : (float)(scale * m / (sigma * m + s * scale));
+}
+}  // namespace
+
+cudaError_t shifted_tau_launch(const Plan& p, double sigma, double s, float* mu_b, cudaStream_t st) {
+  double scale = 1.0;
+  for (int r = 0; r < p.d; ++r) scale /= (double)p.P[r];
+  k_tau_shift<<<(unsigned)((p.lam_count + 255) / 256), 256, 0, st>>>(p.mu_tau, mu_b, p.lam_count, scale, sigma, s);
+  return cudaGetLastError();
+}
+
 size_t tau_scratch_bytes(const Plan& p) {
   const size_t N1 = (size_t)p.Nmax + 1;
   const size_t ncoef = (p.d == 2) ? N1 * N1 : N1 * N1 * N1;

@@ -421,11 +421,10 @@ static CgBufs carve(const Plan& p, void* work, int eb) {
   return b;
 }
 
-// z32 = M^-1 r: one FP32 apply with the preconditioner symbol mu (skipped once done); the plan's
-// sine-basis multiplier runs on odd extensions
+// z32 = M^-1 r: one FP32 apply with the preconditioner symbol mu (skipped once done); odd: mu is a
+// multiplier in the sine basis (applied on odd extensions)
 template <typename T>
-static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu, cudaStream_t st) {
-  const bool odd = mu != nullptr && mu == p.mu_tau;
+static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu, bool odd, cudaStream_t st) {
   const float* src;
   if constexpr (sizeof(T) == 8) {
     k_to32<T><<<vgrid(p.M), kThreads, 0, st>>>(reinterpret_cast<const T*>(b.r), b.r32, p.M, b.S);
@@ -443,7 +442,7 @@ static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu,
 // mu = FP32 preconditioner symbol (octant) or nullptr for plain CG.
 template <typename T>
 static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double s, double rtol, int maxit,
-                           int use_x0, const float* mu, void* work, cudaStream_t st, CgState* hS,
+                           int use_x0, const float* mu, bool odd, void* work, cudaStream_t st, CgState* hS,
                            T* snap = nullptr, int nsnap = 0) {
   const CgBufs b = carve(p, work, sizeof(T));
   T* r = reinterpret_cast<T*>(b.r);
@@ -462,7 +461,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   k_cg_init<T><<<vgrid(n), kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
   FRLAP_LAUNCH_CHECK("k_cg_init");
   if (mu) {
-    cudaError_t e = precondition<T>(p, b, mu, st);
+    cudaError_t e = precondition<T>(p, b, mu, odd, st);
     if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
     k_pcg_start<T, float><<<vgrid(n), kThreads, 0, st>>>(r, b.z32, z, pv, n, b.partials, S);
   } else {
@@ -482,7 +481,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
       if (e != cudaSuccess) return e;
     }
     if (mu) {
-      e = precondition<T>(p, b, mu, ss);
+      e = precondition<T>(p, b, mu, odd, ss);
       if (e != cudaSuccess) return e;
       k_pcg_beta<T, float><<<vgrid(n), kThreads, 0, ss>>>(r, b.z32, z, q, n, b.partials, S);
     }
@@ -581,7 +580,7 @@ frlap_status cg_pairs_impl(const Plan& p, const double* f, int K, double rtol, d
   double* x = reinterpret_cast<double*>(b.z);  // the solution lives in the (unused) z buffer
   FRLAP_CUDA_TRY(cudaMemsetAsync(x, 0, p.M * sizeof(double), st));
   CgState hS;
-  frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, 1000000, 0, nullptr, work, st, &hS, E, K);
+  frlap_status rc = run_cg<double>(p, f, x, 0.0, 1.0, rtol, 1000000, 0, nullptr, false, work, st, &hS, E, K);
   if (rc != FRLAP_OK) return rc;
   if (hS.status != FRLAP_OK) return fail((frlap_status)hS.status, "CG for the training pairs stopped early");
   // x_0 .. x_{iters-1}: the last iterate is the solution itself (zero error) and is left out
@@ -604,7 +603,10 @@ size_t ir_work_bytes(const Plan& p) {
 }
 
 // CG workspace, two vectors (right-hand side, A ubar) and a slot for the mass of the Crank-Nicolson model
-size_t ac_work_bytes(const Plan& p) { return cg_work_bytes(p, 8) + 2 * vec_bytes(p, 8) + 256; }
+// CG workspace, two FP64 vectors, the shifted sine-basis multiplier (FP32 octant), the mass slot
+size_t ac_work_bytes(const Plan& p) {
+  return cg_work_bytes(p, 8) + 2 * vec_bytes(p, 8) + align256(p.lam_count * sizeof(float)) + 256;
+}
 
 // Workspace of frlap_pcg_solve: the CG or refinement workspace, and on double-float plans the
 // scaled right-hand side (one FP64 vector) behind it.
@@ -655,6 +657,7 @@ static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, do
                                    const float* mu, double inner_rtol, int* iters, double* relres, void* work,
                                    cudaStream_t st) {
   CgState hS;
+  const bool odd = mu != nullptr && mu == p.mu_tau;  // the sine-basis multiplier runs on odd extensions
   if (solver == FRLAP_SOLVE_CG) {
     // CG, then the true residual; if rounding left the true residual above rtol while the
     // recursive one met it, restart from the current x (at most 4 restarts, within maxit).
@@ -665,7 +668,7 @@ static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, do
     frlap_status rc = FRLAP_OK;
     for (int restart = 0; restart < 5; ++restart) {
       const double rt = restart == 0 ? rtol : 0.1 * rtol;
-      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, restart == 0 ? 1 : 2, mu, work, st, &hS);
+      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, restart == 0 ? 1 : 2, mu, odd, work, st, &hS);
       if (rc != FRLAP_OK) return rc;
       total += hS.iters;
       rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
@@ -708,7 +711,7 @@ static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, do
     if (rel <= rtol || outer == max_outer || total >= maxit) break;
     k_to_f32<<<vgrid(p.M), kThreads, 0, st>>>(r64, rnorm, r32, d32, p.M);
     FRLAP_LAUNCH_CHECK("k_to_f32");
-    rc = run_cg<float>(p, r32, d32, 0.0, 1.0, inner_rtol, maxit - total, 0, mu, work32, st, &hS);
+    rc = run_cg<float>(p, r32, d32, 0.0, 1.0, inner_rtol, maxit - total, 0, mu, odd, work32, st, &hS);
     if (rc != FRLAP_OK) return rc;
     total += hS.iters;
     if (hS.status == FRLAP_ENAN) return fail(FRLAP_ENAN, "non-finite value in the FP32 inner solve");
@@ -733,7 +736,14 @@ frlap_status allen_cahn_cn_impl(const Plan& p, double* ub, double tau, double de
   w += vec_bytes(p, 8);
   double* aub = reinterpret_cast<double*>(w);
   w += vec_bytes(p, 8);
+  float* mu_b = reinterpret_cast<float*>(w);
+  w += align256(p.lam_count * sizeof(float));
   double* dmass = reinterpret_cast<double*>(w);
+  const float* mu = nullptr;
+  if (p.mu_tau) {  // (I + tau/2 A) preconditioned in the sine basis
+    FRLAP_CUDA_TRY(shifted_tau_launch(p, 1.0, 0.5 * tau, mu_b, st));
+    mu = mu_b;
+  }
   const CgBufs b = carve(p, cgw, 8);  // its apply workspace is free between the solves
   const double kdel = pow(delta, -p.alpha);
   const double hd = pow(p.h, (double)p.d);
@@ -744,7 +754,7 @@ frlap_status allen_cahn_cn_impl(const Plan& p, double* ub, double tau, double de
     if (e != cudaSuccess) return cuda_fail(e, "apply (Crank-Nicolson right-hand side)");
     k_cn_rhs<<<vgrid(p.M), kThreads, 0, st>>>(ub, aub, rhs, p.M, tau, kdel);
     FRLAP_LAUNCH_CHECK("k_cn_rhs");
-    frlap_status rc = run_cg<double>(p, rhs, ub, 1.0, 0.5 * tau, rtol, 100000, 1, nullptr, cgw, st, &hS);
+    frlap_status rc = run_cg<double>(p, rhs, ub, 1.0, 0.5 * tau, rtol, 100000, 1, mu, mu != nullptr, cgw, st, &hS);
     if (rc != FRLAP_OK) return rc;
     total += hS.iters;
     if (hS.status != FRLAP_OK) {
@@ -768,12 +778,21 @@ frlap_status allen_cahn_impl(const Plan& p, double* u, double tau, double eps, i
   void* cgw = w;
   w += cg_work_bytes(p, 8);
   double* rhs = reinterpret_cast<double*>(w);
+  w += vec_bytes(p, 8);
+  w += vec_bytes(p, 8);
+  float* mu_b = reinterpret_cast<float*>(w);
+  const float* mu = nullptr;
+  if (p.mu_tau) {  // (I + tau eps^2 A) preconditioned in the sine basis
+    FRLAP_CUDA_TRY(shifted_tau_launch(p, 1.0, tau * eps * eps, mu_b, st));
+    mu = mu_b;
+  }
   int total = 0;
   CgState hS;
   for (int step = 0; step < nsteps; ++step) {
     k_ac_rhs<<<vgrid(p.M), kThreads, 0, st>>>(u, rhs, p.M, tau);
     FRLAP_LAUNCH_CHECK("k_ac_rhs");
-    frlap_status rc = run_cg<double>(p, rhs, u, 1.0, tau * eps * eps, rtol, 100000, 1, nullptr, cgw, st, &hS);
+    frlap_status rc = run_cg<double>(p, rhs, u, 1.0, tau * eps * eps, rtol, 100000, 1, mu, mu != nullptr, cgw, st,
+                                     &hS);
     if (rc != FRLAP_OK) return rc;
     total += hS.iters;
     if (hS.status != FRLAP_OK) {

@@ -69,7 +69,10 @@ def test_iterative_refinement_reaches_fp64_solution(frlap, d, Ns, alpha, prec):
     assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
 
 
-def test_allen_cahn_steps_match_oracle(frlap):
+@pytest.mark.parametrize("tau_pre", [False, True])
+def test_allen_cahn_steps_match_oracle(frlap, tau_pre):
+    """Semi-implicit Allen-Cahn steps against the oracle; with the plan's sine-basis preconditioner built,
+    each solve is PCG with it (same result, fewer iterations)."""
     Ns, alpha, tau, eps = (64, 64), 1.6, 1e-3, 0.05
     h = 2.0 / 64
     a, c = _coef(2, alpha, h, 64), scheme.c_d_alpha(2, alpha)
@@ -79,9 +82,14 @@ def test_allen_cahn_steps_match_oracle(frlap):
     for _ in range(3):
         u_ref, _, _ = solvers.allen_cahn_step(op, u_ref, tau, eps, rtol=1e-13)
     plan = frlap.Plan(2, alpha, h, Ns)
+    if tau_pre:
+        frlap.frlap_precond_tau(plan)
     u = _t(u0)
     it = frlap.frlap_allen_cahn_step(plan, u, tau, eps, nsteps=3, rtol=1e-13)
     assert it > 0
+    if tau_pre:
+        it_plain = frlap.frlap_allen_cahn_step(frlap.Plan(2, alpha, h, Ns), _t(u0), tau, eps, nsteps=3, rtol=1e-13)
+        assert it < it_plain, (it, it_plain)
     u = u.cpu().numpy()
     assert np.abs(u - u_ref).max() <= 1e-11
     assert np.abs(u).max() <= 1.0  # discrete maximum principle
@@ -128,10 +136,12 @@ def test_double_float_cg_reaches_fp64_residual(frlap):
     assert d <= 1e-8
 
 
-@pytest.mark.parametrize("d,N,prec", [(2, 64, 0), (2, 64, 3), (3, 16, 3)])
-def test_allen_cahn_cn_matches_oracle(frlap, d, N, prec):
+@pytest.mark.parametrize("d,N,prec,tau_pre", [(2, 64, 0, False), (2, 64, 3, False), (3, 16, 3, False),
+                                              (2, 64, 3, True), (3, 16, 3, True)])
+def test_allen_cahn_cn_matches_oracle(frlap, d, N, prec, tau_pre):
     """The paper's Allen-Cahn model (Crank-Nicolson for ubar = u + 1, u = -1 outside) from the kissing
-    bubbles on (0,1)^d: four steps and the masses after each against the oracle."""
+    bubbles on (0,1)^d: four steps and the masses after each against the oracle; with the sine-basis
+    preconditioner built, each solve is PCG with it (same result, fewer iterations)."""
     alpha, tau, delta = 1.5, 1e-3, 0.1
     h = 1.0 / N
     a, c = _coef(d, alpha, h, N), scheme.c_d_alpha(d, alpha)
@@ -142,9 +152,15 @@ def test_allen_cahn_cn_matches_oracle(frlap, d, N, prec):
         ref, _, _ = solvers.allen_cahn_cn_step(op, ref, tau, delta, alpha, rtol=1e-13)
         masses.append(solvers.bubble_mass(ref, h))
     plan = frlap.Plan(d, alpha, h, (N,) * d, prec=prec)
+    if tau_pre:
+        frlap.frlap_precond_tau(plan)
     ub = _t(ub0)
     it, m = frlap.frlap_allen_cahn_cn(plan, ub, tau, delta, nsteps=4, rtol=1e-13)
     assert it > 0
+    if tau_pre:
+        it_plain, _ = frlap.frlap_allen_cahn_cn(frlap.Plan(d, alpha, h, (N,) * d, prec=prec), _t(ub0), tau, delta,
+                                                nsteps=4, rtol=1e-13)
+        assert it < it_plain, (it, it_plain)
     assert np.abs(ub.cpu().numpy() - ref).max() <= 1e-10
     np.testing.assert_allclose(m, masses, rtol=1e-11)
     assert m[-1] < solvers.bubble_mass(ub0, h)  # the bubbles shrink
