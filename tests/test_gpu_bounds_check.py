@@ -66,6 +66,20 @@ def _child():
                 x, it, rel, code = fl.frlap_pcg_solve(plan, f, rtol=1e-10, precond=fl.FRLAP_PRECOND_LEARNED)
                 assert code == 0 and rel <= 1e-10
             torch.cuda.synchronize()
+    # the sine-basis preconditioner: its set-up transforms and the odd-extension pipeline, 2D and 3D
+    for d, Ns in ((2, (32, 64)), (3, (16, 32, 16))):
+        hh = 2.0 / max(Ns)
+        plan = fl.Plan(d, 1.4, hh, Ns, prec=fl.FRLAP_MIXED_DF64)
+        assert fl.frlap_precond_tau(plan) == 0
+        fl.frlap_precond_apply(plan, fl.FRLAP_PRECOND_TAU,
+                               torch.from_numpy(inp.normal_field(Ns, seed=9)).to("cuda", torch.float32))
+        f = torch.from_numpy(inp.gaussian_sum_field(Ns, hh, seed=3)).cuda()
+        for solver in (fl.FRLAP_SOLVE_CG, fl.FRLAP_SOLVE_IR):
+            x, it, rel, code = fl.frlap_pcg_solve(plan, f, rtol=1e-10, solver=solver, precond=fl.FRLAP_PRECOND_TAU)
+            assert code == 0 and rel <= 1e-10
+        u = torch.from_numpy(inp.uniform_field(Ns, seed=5)).cuda()  # an Allen-Cahn step: the shifted multiplier
+        fl.frlap_allen_cahn_step(plan, u, 1e-3, 0.05, nsteps=1, rtol=1e-10)
+        torch.cuda.synchronize()
     # 16384-point embeddings: the split middle stage and symbol transform (y), 8192-point rows (x)
     h = 2.0 / 4200
     a, c = scheme.coefficients(2, 1.3, h, 4200), scheme.c_d_alpha(2, 1.3)
