@@ -164,7 +164,8 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
 /* frlap_apply_batch from and to HOST buffers: y_b = A u_b for b = 0..nbatch-1, with
  * h_u, h_y in host memory (nbatch vectors back to back, element type as in
  * frlap_apply).  The batch moves in chunks of `chunk` vectors through two device
- * slots: the copy in of chunk i+1 and the copy out of chunk i-1 run on internal
+ * slots (when chunk > 1 and nbatch > 2 the first and the last chunk hold one vector, so
+ * that filling and draining the pipeline costs one vector's copy): the copy in of chunk i+1 and the copy out of chunk i-1 run on internal
  * streams while chunk i is applied (the two slots compute on `stream` and on an
  * internal stream, so consecutive chunks' kernels may overlap).  For the copies to overlap,
  * h_u and h_y must be pinned (page-locked); pageable buffers give the same

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -452,7 +453,26 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
     awork[k] = dy[k] + align256((size_t)chunk * vbytes);
   }
   const cudaStream_t cs = (cudaStream_t)stream;
-  const int nchunks = (nbatch + chunk - 1) / chunk;
+  // Chunk boundaries: with chunks of more than one vector the first and the last chunk hold one vector,
+  // so the pipeline fills (first copy in) and drains (last copy out) at the cost of one vector's copy.
+  std::vector<int> c0, cn;  // first vector and count of each chunk
+  {
+    int v = 0;
+    const bool ends = chunk > 1 && nbatch > 2;
+    if (ends) {
+      c0.push_back(0);
+      cn.push_back(1);
+      v = 1;
+    }
+    while (v < nbatch) {
+      int nb = nbatch - v < chunk ? nbatch - v : chunk;
+      if (ends && v + nb == nbatch && nb > 1) --nb;  // leave one vector for the last chunk
+      c0.push_back(v);
+      cn.push_back(nb);
+      v += nb;
+    }
+  }
+  const int nchunks = (int)c0.size();
   // slot k computes on comp[k] (comp[0] = the caller's stream): the kernels of consecutive
   // chunks overlap, filling each other's last partial wave
   cudaStream_t sin = nullptr, sout = nullptr, c1 = nullptr;
@@ -474,11 +494,11 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c1, done[0], 0);
   auto copy_in = [&](int c) -> cudaError_t {
     const int k = c & 1;
-    const int nb = (c + 1) * chunk <= nbatch ? chunk : nbatch - c * chunk;
+    const int nb = cn[c];
     cudaError_t r = cudaSuccess;
     if (c >= 2) r = cudaStreamWaitEvent(sin, done[k], 0);  // slot k's previous apply has read its input
     if (r == cudaSuccess)
-      r = cudaMemcpyAsync(du[k], static_cast<const unsigned char*>(h_u) + (size_t)c * chunk * vbytes,
+      r = cudaMemcpyAsync(du[k], static_cast<const unsigned char*>(h_u) + (size_t)c0[c] * vbytes,
                           (size_t)nb * vbytes, cudaMemcpyHostToDevice, sin);
     if (r == cudaSuccess) r = cudaEventRecord(in[k], sin);
     return r;
@@ -486,7 +506,7 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   if (e == cudaSuccess) e = copy_in(0);
   for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
     const int k = c & 1;
-    const int nb = (c + 1) * chunk <= nbatch ? chunk : nbatch - c * chunk;
+    const int nb = cn[c];
     if (c + 1 < nchunks) e = copy_in(c + 1);
     const cudaStream_t ks = comp[k];
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, in[k], 0);
@@ -505,7 +525,7 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
     if (e == cudaSuccess) e = cudaEventRecord(done[k], ks);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[k], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(static_cast<unsigned char*>(h_y) + (size_t)c * chunk * vbytes, dy[k], (size_t)nb * vbytes,
+      e = cudaMemcpyAsync(static_cast<unsigned char*>(h_y) + (size_t)c0[c] * vbytes, dy[k], (size_t)nb * vbytes,
                           cudaMemcpyDeviceToHost, sout);
     if (e == cudaSuccess) e = cudaEventRecord(out[k], sout);
   }
