@@ -45,8 +45,8 @@ BATCH = 8  # vectors per step of the 2D workload
 BATCH_2D = BATCH
 NGRID_3D, ALPHA_3D, BATCH_3D = 256, 1.0, 2
 # vectors per chunk of the host-buffer pipeline, per engine, as measured at 2047^2 (chunks of 1, 2, 4, 8;
-# first and last chunk of one vector): double-float 10.3, 10.3, 8.8, 7.0 G unknowns/s; FP32 25.2, 25.2,
-# 21.6, 18.4 (the copies share about 215 GB/s of host link)
+# three device slots; first and last chunk of one vector): double-float 11.2, 10.6, 9.0, 6.9 G unknowns/s;
+# FP32 24.2, 24.0, 22.0, 18.2 (the copies share about 215 GB/s of host link)
 E2E_CHUNK = {"df64": 1, "f64": 1, "f32": 2}
 METRIC = "apply unknowns/s & %HBM peak; PCG time to 1e-10 of FP64 sol vs plain FP64 CG"
 UNIT = "unknowns/s"

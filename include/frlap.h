@@ -163,16 +163,17 @@ frlap_status frlap_apply_batch(const frlap_plan* plan, int nbatch, const void* d
 
 /* frlap_apply_batch from and to HOST buffers: y_b = A u_b for b = 0..nbatch-1, with
  * h_u, h_y in host memory (nbatch vectors back to back, element type as in
- * frlap_apply).  The batch moves in chunks of `chunk` vectors through two device
- * slots (when chunk > 1 and nbatch > 2 the first and the last chunk hold one vector, so
- * that filling and draining the pipeline costs one vector's copy): the copy in of chunk i+1 and the copy out of chunk i-1 run on internal
- * streams while chunk i is applied (the two slots compute on `stream` and on an
- * internal stream, so consecutive chunks' kernels may overlap).  For the copies to overlap,
- * h_u and h_y must be pinned (page-locked); pageable buffers give the same
- * result with serialised copies.  h_u and h_y must not overlap.  d_work:
- * frlap_apply_host_workspace_bytes(plan,
- * chunk) bytes, 256-byte aligned.  Synchronises `stream`: h_y is complete on
- * return.  1 <= chunk <= 65535, nbatch >= 1, else FRLAP_EINVAL. */
+ * frlap_apply).  The batch moves in chunks of `chunk` vectors through three device
+ * slots: the copies in of chunks i+1 and i+2 and the copy out of chunk i-1 run on
+ * internal streams while chunk i is applied, and consecutive chunks compute on
+ * `stream` and on an internal stream, so their kernels may overlap.  When chunk > 1
+ * and nbatch > 2 the first and the last chunk hold one vector, so that filling and
+ * draining the pipeline costs one vector's copy.  For the copies to overlap, h_u and
+ * h_y must be pinned (page-locked); pageable buffers give the same result with
+ * serialised copies.  h_u and h_y must not overlap.  d_work:
+ * frlap_apply_host_workspace_bytes(plan, chunk) bytes, 256-byte aligned.
+ * Synchronises `stream`: h_y is complete on return.  1 <= chunk <= 65535,
+ * nbatch >= 1, else FRLAP_EINVAL. */
 /* Autotuner of the apply's launch shapes.  For each stage of the apply, and for each
  * engine the plan uses (FP32, and FP64 or double-float), times every admissible
  * number of FFT lines per CTA (powers of two up to 512 threads and 227 KB of shared

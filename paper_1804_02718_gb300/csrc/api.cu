@@ -429,9 +429,13 @@ static size_t host_slot_bytes(const frlap_plan* plan, int chunk) {
   return 2 * align256(vb) + align256(frlap_apply_batch_workspace_bytes(plan, chunk));
 }
 
+// device slots of frlap_apply_host (input, output and apply workspace for one chunk each): three, so that
+// the copy in of chunk c+2 and the copy out of chunk c-1 overlap the apply of chunk c
+constexpr int kHostSlots = 3;
+
 size_t frlap_apply_host_workspace_bytes(const frlap_plan* plan, int chunk) {
   if (!plan || chunk < 1) return 0;
-  return 2 * host_slot_bytes(plan, chunk);
+  return kHostSlots * host_slot_bytes(plan, chunk);
 }
 
 frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, const void* h_u, void* h_y,
@@ -444,10 +448,10 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   const size_t vbytes = plan->M * eb;
   if (ranges_overlap(h_u, h_y, (size_t)nbatch * vbytes)) return fail(FRLAP_EINVAL, "h_u and h_y must not overlap");
   unsigned char* w = reinterpret_cast<unsigned char*>(d_work);
-  unsigned char* du[2];
-  unsigned char* dy[2];
-  void* awork[2];
-  for (int k = 0; k < 2; ++k) {
+  unsigned char* du[kHostSlots];
+  unsigned char* dy[kHostSlots];
+  void* awork[kHostSlots];
+  for (int k = 0; k < kHostSlots; ++k) {
     du[k] = w + k * host_slot_bytes(plan, chunk);
     dy[k] = du[k] + align256((size_t)chunk * vbytes);
     awork[k] = dy[k] + align256((size_t)chunk * vbytes);
@@ -473,16 +477,16 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
     }
   }
   const int nchunks = (int)c0.size();
-  // slot k computes on comp[k] (comp[0] = the caller's stream): the kernels of consecutive
-  // chunks overlap, filling each other's last partial wave
+  // chunk c uses slot c mod kHostSlots and computes on comp[c mod 2] (comp[0] = the caller's stream): the
+  // kernels of consecutive chunks overlap, filling each other's last partial wave
   cudaStream_t sin = nullptr, sout = nullptr, c1 = nullptr;
   // in[k]: slot k's input has arrived; done[k]: slot k's apply finished; out[k]: slot k's output copied
-  cudaEvent_t in[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, out[2] = {nullptr, nullptr};
+  cudaEvent_t in[kHostSlots] = {}, done[kHostSlots] = {}, out[kHostSlots] = {};
   cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c1, cudaStreamNonBlocking);
   const cudaStream_t comp[2] = {cs, c1};
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < kHostSlots && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&in[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out[k], cudaEventDisableTiming);
@@ -493,24 +497,24 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[0], 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c1, done[0], 0);
   auto copy_in = [&](int c) -> cudaError_t {
-    const int k = c & 1;
+    const int k = c % kHostSlots;
     const int nb = cn[c];
     cudaError_t r = cudaSuccess;
-    if (c >= 2) r = cudaStreamWaitEvent(sin, done[k], 0);  // slot k's previous apply has read its input
+    if (c >= kHostSlots) r = cudaStreamWaitEvent(sin, done[k], 0);  // slot k's previous apply has read its input
     if (r == cudaSuccess)
       r = cudaMemcpyAsync(du[k], static_cast<const unsigned char*>(h_u) + (size_t)c0[c] * vbytes,
                           (size_t)nb * vbytes, cudaMemcpyHostToDevice, sin);
     if (r == cudaSuccess) r = cudaEventRecord(in[k], sin);
     return r;
   };
-  if (e == cudaSuccess) e = copy_in(0);
+  for (int c = 0; c < kHostSlots - 1 && c < nchunks && e == cudaSuccess; ++c) e = copy_in(c);
   for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
-    const int k = c & 1;
+    const int k = c % kHostSlots;
     const int nb = cn[c];
-    if (c + 1 < nchunks) e = copy_in(c + 1);
-    const cudaStream_t ks = comp[k];
+    if (c + kHostSlots - 1 < nchunks) e = copy_in(c + kHostSlots - 1);
+    const cudaStream_t ks = comp[c & 1];
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, in[k], 0);
-    if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(ks, out[k], 0);  // slot k's output copied out
+    if (e == cudaSuccess && c >= kHostSlots) e = cudaStreamWaitEvent(ks, out[k], 0);  // slot k's output copied out
     if (e == cudaSuccess) {
       if (plan->prec == FRLAP_F32)
         e = apply_batch_launch<float>(*plan, nb, (const float*)du[k], (float*)dy[k], plan->M, awork[k], ks, nullptr,
@@ -530,13 +534,13 @@ frlap_status frlap_apply_host(const frlap_plan* plan, int nbatch, int chunk, con
     if (e == cudaSuccess) e = cudaEventRecord(out[k], sout);
   }
   // `stream` ends after the last copy out; then wait for everything
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(cs, out[k], 0);
+  for (int k = 0; k < kHostSlots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(cs, out[k], 0);
   cudaError_t es = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = es;
   if (sin) cudaStreamSynchronize(sin);
   if (sout) cudaStreamSynchronize(sout);
   if (c1) cudaStreamSynchronize(c1);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kHostSlots; ++k) {
     if (in[k]) cudaEventDestroy(in[k]);
     if (done[k]) cudaEventDestroy(done[k]);
     if (out[k]) cudaEventDestroy(out[k]);
