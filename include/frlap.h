@@ -301,7 +301,7 @@ frlap_status frlap_allen_cahn_step(const frlap_plan* plan, double* d_u, double t
 frlap_status frlap_allen_cahn_cn(const frlap_plan* plan, double* d_ubar, double tau, double delta, int nsteps,
                                  double rtol, int* iters, double* h_mass, void* d_work, void* stream);
 
-/* ---- learned preconditioner (spec extension; the paper has no learned part) ----
+/* ---- learned preconditioner (an extension; the paper has no learned part) ----
  * A per-frequency MLP on the symbol octant: features (alpha, kappa_x, kappa_y,
  * kappa_z), kappa_r = k_r / (P_r/2) (kappa_z = 0 in 2D), two tanh layers of
  * FRLAP_MLP_HIDDEN units, scalar output s; multiplier m(k) = exp(s(k)) / lambda(k)
