@@ -178,6 +178,22 @@ __device__ __forceinline__ void load_transposed(C* smem, const C* __restrict__ s
 template <typename T>
 constexpr int kMaxCta = std::is_same<T, float>::value ? 1024 : 512;
 
+// Shared-memory stride between the transform lines of one first-stage (k_r2c_T) CTA.  Its transposed
+// store has a warp read TL lines x 32/TL consecutive bins; for FP32 (16 complex values per 128-byte
+// wavefront) the lines are offset by 32/TL slots modulo 16, so that one warp's reads fill whole
+// wavefronts: 2047^2 FP32 r2c 20.1 -> 18.2 us per vector.  Lines of at least 512 points only (the
+// 256-point rows of 255^3 measured no better); the same offset on the last stage's transposed load
+// measured slower (2047^2: 18.2 -> 19.4 us), so it keeps sline.
+template <typename T>
+__host__ __device__ __forceinline__ int r2c_line_stride(int L, int TL) {
+  int s = sline(L);
+  if (std::is_same<T, float>::value && TL > 1 && L >= 512) {
+    const int want = (32 / TL) & 15;
+    s += ((want - s % 16) + 16) % 16;
+  }
+  return s;
+}
+
 // The real-data split of the first and last stages: computed per output element inside the
 // transposed store / the transform's register load (one complex product per element, no
 // shared-memory write-back), or in place per pair of bins (one product per pair, one more pass
@@ -226,7 +242,7 @@ __device__ __forceinline__ void r2c_tile(cplx<T>* v, cplx<T>* smem, cplx<T>* __r
                                          int lane) {
   using C = cplx<T>;
   const int H = 1 << logH, G = H >> 4;
-  const int LS = sline(H);
+  const int LS = r2c_line_stride<T>(H, TL);
   C* buf = smem + (size_t)l * LS;
   fft_regs<T, -1, ZIN, REM>(v, buf, logH, lane, tw, logP, false);
   line_sync<T>(logH);
@@ -1139,7 +1155,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   } else {
     const int G = Hx >> 4;
     const int tl = pick_tl_tuned(tuned[0], sline(Hx), eb, G, budget, (long long)nrows * B);
-    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    const size_t sm = (size_t)tl * r2c_line_stride<T>(Hx, tl) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
@@ -1384,7 +1400,7 @@ cudaError_t spectrum_forward(const Plan& p, const T* u, cplx<T>* SP, void* work,
   {
     const int G = Hx >> 4;
     const int tl = pick_tl(sline(Hx), eb, G, budget, 64);
-    const size_t sm = (size_t)tl * sline(Hx) * eb;
+    const size_t sm = (size_t)tl * r2c_line_stride<T>(Hx, tl) * eb;
     e = with_rem(p.logP[0] - 1, [&](auto tag) {
       constexpr int REM = decltype(tag)::value;
       cudaError_t e2 = set_smem(k_r2c_T<T, REM>, sm);
@@ -1539,7 +1555,8 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
     float best_ms = 0.f;
     for (int t = 1; t <= 64 && e == cudaSuccess; t *= 2) {
       const size_t smem = (st == 0 && use_r2c_pf<T>(p.logP[0] - 1, u)) ? r2c_pf_smem_bytes<T>(t, L, p.n[0])
-                                                         : (size_t)t * sline(L) * eb;
+                          : st == 0                                     ? (size_t)t * r2c_line_stride<T>(L, t) * eb
+                                                                         : (size_t)t * sline(L) * eb;
       if (t * G > kMaxCta<T> || smem > kMaxSmem) break;
       if (G < 32 && t < 32 / G) continue;
       p.tl_tuned[eng][st] = t;
