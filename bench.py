@@ -65,8 +65,8 @@ def peaks():
 # kernel, engine): dram__bytes_read.sum + dram__bytes_write.sum from the ncu captures summarised in
 # profiles/apply_2d_2047_batch8.md and profiles/apply_3d_255_batch2.md; an entry is dropped when its
 # kernel changes after the capture
-MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1285.1e6, (2, "colmul", "f32"): 587.9e6,
-                    (3, "colmul", "df64"): 2458.1e6, (3, "colmul", "f32"): 1218.6e6}
+MEASURED_TRAFFIC = {(2, "colmul", "df64"): 1285.1e6, (2, "colmul", "f32"): 588.4e6,
+                    (3, "colmul", "df64"): 2457.5e6, (3, "colmul", "f32"): 1219.4e6}
 
 
 def measure_fp32_fma_tflops(torch, tf32=False):
