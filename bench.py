@@ -14,9 +14,10 @@ end to end through host buffers, and the CPU oracle timed on all host cores.  Af
 the timed region: the metric's second half (time to a 1e-10 residual for plain FP64
 CG, Strang and learned PCG and FP32-inner refinement at 2047^2 and 255^3, each with
 its solution error against a tighter reference solve), native FP64, FP32 and 3D
-applies, and cuFFT as a comparison.  `--suite solvers` instead runs
-the solver configurations (time to 1e-10 for plain CG, refinement, Strang and
-learned preconditioning; the batched Allen-Cahn launch) and prints them.
+applies, cuFFT as a comparison, and the radix-16 FFT stage on CUDA cores against its
+split-TF32 tensor-core form.  `--suite solvers` instead runs the solver configurations
+(time to 1e-10 for plain CG, refinement, Strang and learned preconditioning; the
+batched Allen-Cahn launch) and prints them; `--suite dft16` only the radix-16 stage.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl frlap|reference] [--prec df64|f64|f32]
 """
@@ -92,6 +93,39 @@ def measure_fp32_fma_tflops(torch, tf32=False):
         return 2 * n ** 3 / (best / 1e3) / 1e12
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def measure_dft16_stages(fl, torch, ntiles=152 * 16, reps=64):
+    """The radix-16 FFT stage on CUDA cores against its split-TF32 tensor-core form
+    (frlap_dft16_stages): time per point and stage, on chip.  Each engine is timed at `reps` stages
+    and at 0 (load and store only, subtracted), best of 5 launches after 3 warm-ups."""
+    x = torch.randn(ntiles, 128, 32, device="cuda")
+    y = torch.empty_like(x)
+
+    def best_ms(engine, r):
+        for _ in range(3):
+            fl.frlap_dft16_stages(engine, x, r, out=y)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fl.frlap_dft16_stages(engine, x, r, out=y)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {"tiles": ntiles, "points_per_tile": 2048, "stages": reps}
+    for name, engine in (("cuda_cores", 0), ("tensor_cores_split_tf32", 1)):
+        t = (best_ms(engine, reps) - best_ms(engine, 0)) / 1e3
+        out[name + "_ps_per_point_stage"] = round(t / (ntiles * 2048 * reps) * 1e12, 4)
+    a = fl.frlap_dft16_stages(0, x, 8)
+    b = fl.frlap_dft16_stages(1, x, 8)
+    out["rel_diff_after_8_stages"] = float((torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(a)).item())
+    out["tensor_over_cuda_cores"] = round(out["tensor_cores_split_tf32_ps_per_point_stage"] /
+                                          out["cuda_cores_ps_per_point_stage"], 3)
+    del x, y, a, b
+    return out
 
 
 def cpu_model():
@@ -347,7 +381,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="frlap", choices=["frlap", "reference"])
     ap.add_argument("--prec", default="df64", choices=["f64", "f32", "df64"])
-    ap.add_argument("--suite", default="apply", choices=["apply", "solvers"])
+    ap.add_argument("--suite", default="apply", choices=["apply", "solvers", "dft16"],
+                    help="dft16: only the radix-16 stage on CUDA cores against tensor cores")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pcg", action="store_true", help="skip the PCG half of the metric (profiling runs)")
@@ -364,6 +399,14 @@ def main():
         return
     if args.suite == "solvers":
         run_solver_suite(args)
+        return
+    if args.suite == "dft16":
+        import torch
+        import paper_1804_02718_gb300 as fl
+        from paper_1804_02718_gb300 import build as _build
+        _build.build()
+        torch.cuda.set_device(local)
+        print(json.dumps({"suite": "dft16", "dft16_stage": measure_dft16_stages(fl, torch)}))
         return
 
     import torch
@@ -532,6 +575,7 @@ def run_extras(fl, torch, args):
         del plan, U, Y, work
         torch.cuda.empty_cache()
     out["tf32_gemm_tflops_measured"] = round(measure_fp32_fma_tflops(torch, tf32=True), 1)
+    out["dft16_stage"] = measure_dft16_stages(fl, torch)
     # plan creation (coefficients, symbol, twiddles; host wall time, synchronised), after a small warm-up plan
     fl.Plan(3, 1.0, 2.0 / 16, (16, 16, 16), prec=fl.FRLAP_DF64)
     torch.cuda.synchronize()

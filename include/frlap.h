@@ -375,7 +375,8 @@ frlap_status frlap_set_loop_pass_limit(unsigned max_passes);
  * memory by bulk asynchronous copies and waits for each on an mbarrier.  Every such wait is
  * bounded (about a second); a wait that gives up is counted, and that kernel returns without
  * storing its remaining tiles (the call's result is then wrong).  frlap_async_wait_report returns
- * in *timeouts the count since the previous report (summed over the engines, then reset).
+ * in *timeouts the count since the previous report (summed over the engines and the tensor-core
+ * waits of frlap_dft16_stages, then reset).
  * Synchronises the device.  A tool for tests and health checks; the paper has no counterpart. */
 frlap_status frlap_async_wait_report(unsigned long long* timeouts);
 /* The give-up path of that wait: one warp waits on an mbarrier phase that nothing completes (no
@@ -383,6 +384,26 @@ frlap_status frlap_async_wait_report(unsigned long long* timeouts);
  * *timeouts the waits that gave up (1 expected; the counter is reset before and after), leaving the
  * context usable.  Synchronises the device.  For tests. */
 frlap_status frlap_async_wait_selftest(unsigned long long* timeouts);
+
+/* Radix-16 FFT stages in two engines, to measure the tensor-core form of the stages the apply's
+ * transforms are made of (the apply itself runs them on CUDA cores).  Textbook FFT arithmetic, not
+ * from the paper, which only states that the Toeplitz products are computed by FFT (Sec. 2 after
+ * eq. product, Sec. 4 after eq. A3D).
+ * Data: ntiles tiles of 128 rows x 16 complex FP32 values (re, im interleaved; 4096 floats, 16 KB
+ * per tile), row r = 16 a + b (a < 8, b < 16).  Each tile is loaded once, then `reps` stages run
+ * on chip, each
+ *   x'[a,b][q] = v[a,b][q] W_256^{bq} / 4;  v[a,q][k] = sum_b x'[a,b][q] W_16^{bk}   (W_L = exp(-2 pi i/L)),
+ * i.e. twiddles (scaled so that a stage keeps the norm), the transposing exchange of a Stockham stage
+ * and a 16-point DFT per row; then the
+ * tile is stored to d_out.  engine 0: CUDA cores (shared-memory exchange, register radix-16
+ * butterflies, as in the apply); engine 1: tensor cores (tcgen05.mma kind::tf32, the DFT as a real
+ * 32 x 32 matrix product with both operands split into TF32 high and low parts, three products
+ * accumulated in FP32 in tensor memory; relative error about 1e-6 per stage).  d_in, d_out: device,
+ * 16-byte aligned, equal (in place) or not overlapping; 0 <= ntiles <= 2^24, 0 <= reps <= 65536.
+ * Asynchronous on `stream`.  A stage whose tensor-core completion wait gives up (about a second)
+ * leaves its tile unwritten and counts in frlap_async_wait_report.  FRLAP_EINVAL on bad arguments,
+ * FRLAP_ECUDA on a launch error. */
+frlap_status frlap_dft16_stages(int engine, const float* d_in, float* d_out, int ntiles, int reps, void* stream);
 
 /* Bounds-checked builds (compiled with -DFRLAP_BOUNDS_CHECK; the package's build script makes
  * them as libfrlap_bc.so).  There every global load and store of the apply kernels is first tested

@@ -70,6 +70,7 @@ _SIGS = {
     "frlap_bounds_check_selftest": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_async_wait_report": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_async_wait_selftest": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "frlap_dft16_stages": (_I, [_I, _P, _P, _I, _I, _P]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
 
@@ -542,6 +543,23 @@ def frlap_async_wait_selftest() -> int:
     n = ctypes.c_ulonglong(0)
     _check(lib().frlap_async_wait_selftest(ctypes.byref(n)), "frlap_async_wait_selftest")
     return int(n.value)
+
+
+def frlap_dft16_stages(engine: int, x: torch.Tensor, reps: int, out: torch.Tensor = None, stream=None):
+    """`reps` radix-16 FFT stages on tiles of 128 x 16 complex FP32 values held on chip, on CUDA
+    cores (engine 0) or tensor cores (engine 1, split TF32); x has shape (ntiles, 128, 32) float32
+    (re, im interleaved).  Returns out (allocated if None; may be x itself)."""
+    if x.dim() != 3 or x.shape[1] != 128 or x.shape[2] != 32:
+        raise ValueError("x must have shape (ntiles, 128, 32)")
+    p = _dev(x, torch.float32, "x")
+    if out is None:
+        out = torch.empty_like(x)
+    elif out.shape != x.shape:
+        raise ValueError("out must have the shape of x")
+    q = _dev(out, torch.float32, "out")
+    _check(lib().frlap_dft16_stages(int(engine), p, q, int(x.shape[0]), int(reps), _stream(stream)),
+           "frlap_dft16_stages")
+    return out
 
 
 def frlap_bounds_check_selftest() -> int:

@@ -100,7 +100,27 @@ frlap_status frlap_async_wait_report(unsigned long long* timeouts) {
     FRLAP_CUDA_TRY(fn(&c));
     total += c;
   }
+  {
+    unsigned long long c = 0ull;
+    FRLAP_CUDA_TRY(dft16_wait_collect(&c));
+    total += c;
+  }
   *timeouts = total;
+  return FRLAP_OK;
+}
+
+frlap_status frlap_dft16_stages(int engine, const float* d_in, float* d_out, int ntiles, int reps, void* stream) {
+  if (engine != 0 && engine != 1) return fail(FRLAP_EINVAL, "engine must be 0 (CUDA cores) or 1 (tensor cores)");
+  if (ntiles < 0 || ntiles > (1 << 24)) return fail(FRLAP_EINVAL, "ntiles must be in [0, 2^24]");
+  if (reps < 0 || reps > (1 << 16)) return fail(FRLAP_EINVAL, "reps must be in [0, 65536]");
+  if (ntiles == 0) return FRLAP_OK;
+  if (!d_in || !d_out) return fail(FRLAP_EINVAL, "d_in and d_out must not be NULL");
+  if (reinterpret_cast<uintptr_t>(d_in) % 16 || reinterpret_cast<uintptr_t>(d_out) % 16)
+    return fail(FRLAP_EINVAL, "d_in and d_out must be 16-byte aligned");
+  const size_t bytes = (size_t)ntiles * 4096 * sizeof(float);
+  if (d_in != d_out && ranges_overlap(d_in, d_out, bytes))
+    return fail(FRLAP_EINVAL, "d_in and d_out must be equal or not overlap");
+  FRLAP_CUDA_TRY(dft16_stages_launch(engine, d_in, d_out, ntiles, reps, static_cast<cudaStream_t>(stream)));
   return FRLAP_OK;
 }
 

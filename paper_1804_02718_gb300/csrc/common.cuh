@@ -287,6 +287,9 @@ cudaError_t bc_collect(unsigned long long* count, unsigned long long* first);
 cudaError_t bc_selftest(unsigned long long* flagged);
 // Runs one bounded mbarrier wait that nothing completes; *timeouts = waits that gave up (1 expected).
 cudaError_t wait_selftest(unsigned long long* timeouts);
+// radix-16 stages on CUDA cores (engine 0) or tensor cores (engine 1); see dft16_tc.cu
+cudaError_t dft16_stages_launch(int engine, const float* in, float* out, int ntiles, int reps, cudaStream_t s);
+cudaError_t dft16_wait_collect(unsigned long long* count);
 
 // apply pipeline (apply.cu); work must hold apply_work_bytes(plan, sizeof(T)) bytes
 // T = compute type (float, double or dfl); vectors are io_t<T>, symbol overrides are T
