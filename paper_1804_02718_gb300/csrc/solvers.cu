@@ -549,15 +549,18 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
 }
 
 // true relative residual ||f - B x|| / ||f|| in FP64 (uses the apply work and q buffer)
+// (zero_x: x is known to be zero, so A x = 0 needs no apply)
 static frlap_status true_residual(const Plan& p, const double* f, const double* x, double sigma, double s,
                                   void* work, cudaStream_t st, double* relres, double* rvec,
-                                  double* rnorm_dev, bool native = true) {
+                                  double* rnorm_dev, bool native = true, bool zero_x = false) {
   const CgBufs b = carve(p, work, 8);
   double* q = reinterpret_cast<double*>(b.q);
   CgState* S = b.S;
   // the reduction ticket must start at zero (this workspace may not have run a CG yet)
   FRLAP_CUDA_TRY(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), st));
-  cudaError_t e = native ? apply_residual<double>(p, x, q, b.awork, st) : apply64(p, x, q, b.awork, st, nullptr);
+  cudaError_t e = zero_x   ? cudaMemsetAsync(q, 0, p.M * sizeof(double), st)
+                  : native ? apply_residual<double>(p, x, q, b.awork, st)
+                           : apply64(p, x, q, b.awork, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "apply (true residual)");
   double* out = &S->alpha;  // reuse two scalar slots (alpha, beta) for the norms
   k_resid<<<vgrid(p.M), kThreads, 0, st>>>(f, x, q, p.M, sigma, s, b.partials, &S->counter, out, rvec, rnorm_dev);
@@ -618,34 +621,41 @@ size_t pcg_work_bytes(const Plan& p) { return pcg_base_bytes(p) + (p.df64 ? vec_
 
 static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                                    const float* mu, double inner_rtol, int* iters, double* relres, void* work,
-                                   cudaStream_t st);
+                                   cudaStream_t st, bool x0_zero);
 
-// Double-float keeps FP32's exponent range, so on double-float plans the system is solved for
-// 2^-e f with 2^e the power of two at or below max |f_i| (and x0 scaled alike), and x is
-// scaled back: every scaling is by a power of two, exact in FP64, so the solve is the same up
+// max |f_i| and max |x0_i| first (one synchronisation): a zero x0 needs no apply for the initial
+// residual (r = f), and on double-float plans, which keep FP32's exponent range, the system is
+// solved for 2^-e f with 2^e the power of two at or below max |f_i| (and x0 scaled alike), and x
+// is scaled back: every scaling is by a power of two, exact in FP64, so the solve is the same up
 // to the double-float range it now stays inside.
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                             const float* mu, double inner_rtol, int* iters, double* relres, void* work,
                             cudaStream_t st) {
-  if (!p.df64) return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
-  double* fs = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(work) + pcg_base_bytes(p));
   const CgBufs b = carve(p, work, 8);
-  unsigned long long* slot = reinterpret_cast<unsigned long long*>(&b.S->alpha);
-  FRLAP_CUDA_TRY(cudaMemsetAsync(slot, 0, sizeof(unsigned long long), st));
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(&b.S->alpha);  // alpha, beta: two slots
+  FRLAP_CUDA_TRY(cudaMemsetAsync(slot, 0, 2 * sizeof(unsigned long long), st));
   k_maxabs<<<vgrid(p.M), kThreads, 0, st>>>(f, p.M, slot);
+  k_maxabs<<<vgrid(p.M), kThreads, 0, st>>>(x, p.M, slot + 1);
   FRLAP_LAUNCH_CHECK("k_maxabs");
-  unsigned long long bits = 0;
-  FRLAP_CUDA_TRY(cudaMemcpyAsync(&bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  unsigned long long bits[2] = {0ull, 0ull};
+  FRLAP_CUDA_TRY(cudaMemcpyAsync(bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, st));
   FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
-  double fmax = 0.0;
-  memcpy(&fmax, &bits, sizeof(fmax));
+  double fmax = 0.0, xmax = 0.0;
+  memcpy(&fmax, &bits[0], sizeof(fmax));
+  memcpy(&xmax, &bits[1], sizeof(xmax));
+  const bool x0_zero = xmax == 0.0;  // false for a non-finite x0 (its pattern is a NaN)
+  if (!p.df64)
+    return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st, x0_zero);
   if (!isfinite(fmax)) return fail(FRLAP_ENAN, "non-finite value in the right-hand side");
   const int e = fmax > 0.0 ? ilogb(fmax) : 0;
-  if (e == 0) return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
+  if (e == 0)
+    return pcg_solve_core(p, f, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st, x0_zero);
+  double* fs = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(work) + pcg_base_bytes(p));
   k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(f, fs, p.M, -e);
-  k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(x, x, p.M, -e);
+  if (!x0_zero) k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(x, x, p.M, -e);
   FRLAP_LAUNCH_CHECK("k_scale_pow2");
-  const frlap_status rc = pcg_solve_core(p, fs, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st);
+  const frlap_status rc = pcg_solve_core(p, fs, x, rtol, maxit, solver, mu, inner_rtol, iters, relres, work, st,
+                                         x0_zero);
   k_scale_pow2<<<vgrid(p.M), kThreads, 0, st>>>(x, x, p.M, e);
   cudaError_t ce = cudaGetLastError();
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -655,7 +665,7 @@ frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rt
 
 static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                                    const float* mu, double inner_rtol, int* iters, double* relres, void* work,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool x0_zero) {
   CgState hS;
   const bool odd = mu != nullptr && mu == p.mu_tau;  // the sine-basis multiplier runs on odd extensions
   if (solver == FRLAP_SOLVE_CG) {
@@ -668,7 +678,8 @@ static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, do
     frlap_status rc = FRLAP_OK;
     for (int restart = 0; restart < 5; ++restart) {
       const double rt = restart == 0 ? rtol : 0.1 * rtol;
-      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, restart == 0 ? 1 : 2, mu, odd, work, st, &hS);
+      const int use_x0 = restart > 0 ? 2 : x0_zero ? 0 : 1;
+      rc = run_cg<double>(p, f, x, 0.0, 1.0, rt, maxit - total, use_x0, mu, odd, work, st, &hS);
       if (rc != FRLAP_OK) return rc;
       total += hS.iters;
       rc = true_residual(p, f, x, 0.0, 1.0, work, st, &rel, nullptr, nullptr);
@@ -702,7 +713,7 @@ static frlap_status pcg_solve_core(const Plan& p, const double* f, double* x, do
   double prev = 1.0;
   for (int outer = 0; outer <= max_outer; ++outer) {
     const bool native = prev <= 1e-6;
-    frlap_status rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm, native);
+    frlap_status rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm, native, outer == 0 && x0_zero);
     if (rc == FRLAP_OK && !native && rel <= 1e-6)
       rc = true_residual(p, f, x, 0.0, 1.0, work64, st, &rel, r64, rnorm, true);
     if (rc != FRLAP_OK) return rc;
