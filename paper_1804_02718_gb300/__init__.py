@@ -15,5 +15,5 @@ from ._binding import (  # noqa: F401
     frlap_mlp_multiplier, frlap_learn_workspace_bytes, frlap_learn_grad, frlap_adam_step, frlap_cg_pairs, MLP_NPARAM,
     frlap_allen_cahn_batch, frlap_allen_cahn_batch_workspace_bytes, frlap_plan_create, frlap_plan_destroy,
     frlap_workspace_bytes, frlap_set_loop_pass_limit, frlap_bounds_check_report, frlap_bounds_check_selftest,
-    frlap_async_wait_report, frlap_async_wait_selftest, frlap_dft16_stages, lib,
+    frlap_async_wait_report, frlap_async_wait_selftest, frlap_dft16_stages, frlap_residual, lib,
 )

@@ -71,6 +71,7 @@ _SIGS = {
     "frlap_async_wait_report": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_async_wait_selftest": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "frlap_dft16_stages": (_I, [_I, _P, _P, _I, _I, _P]),
+    "frlap_residual": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P, _P]),
     "frlap_last_error": (ctypes.c_char_p, []),
 }
 
@@ -376,6 +377,24 @@ def frlap_pcg_solve(plan: Plan, f: torch.Tensor, x: torch.Tensor = None, rtol: f
     if raise_on_error:
         _check(code, "frlap_pcg_solve")
     return x, it.value, rel.value, code
+
+
+def frlap_residual(plan: Plan, f: torch.Tensor, x: torch.Tensor, r: torch.Tensor = None, want_r: bool = True,
+                   work: torch.Tensor = None, stream=None):
+    """r = f - A x and ||r|| / ||f|| with the apply that decides frlap_pcg_solve's convergence;
+    returns (r or None, relres)."""
+    _check_vectors(plan, f, x, ("f", "x"))
+    if want_r and r is None:
+        r = torch.empty_like(f)
+    if r is not None:
+        _check_vectors(plan, r, None, ("r", "r"))
+    if work is None:
+        work = plan.workspace(FRLAP_OP_PCG)
+    rel = ctypes.c_double(0.0)
+    _check(lib().frlap_residual(plan.handle, _dev(f, torch.float64, "f"), _dev(x, torch.float64, "x"),
+                                _dev(r, torch.float64, "r") if r is not None else None, ctypes.byref(rel),
+                                ctypes.c_void_p(work.data_ptr()), _stream(stream)), "frlap_residual")
+    return r, rel.value
 
 
 def frlap_precond_strang(plan: Plan, stream=None) -> int:

@@ -36,6 +36,8 @@ size_t ac_work_bytes(const Plan& p);
 frlap_status pcg_solve_impl(const Plan& p, const double* f, double* x, double rtol, int maxit, int solver,
                             const float* mu, double inner_rtol, int* iters, double* relres, void* work,
                             cudaStream_t st);
+frlap_status residual_impl(const Plan& p, const double* f, const double* x, double* r, double* relres, void* work,
+                           cudaStream_t st);
 size_t strang_scratch_bytes(const Plan& p);
 size_t learn_work_bytes(const Plan& p, int B);
 cudaError_t mlp_multiplier_launch(const Plan& p, const float* params, double* m, cudaStream_t s);
@@ -100,9 +102,9 @@ frlap_status frlap_async_wait_report(unsigned long long* timeouts) {
     FRLAP_CUDA_TRY(fn(&c));
     total += c;
   }
-  {
+  for (auto fn : {dft16_wait_collect, hyb_wait_collect}) {
     unsigned long long c = 0ull;
-    FRLAP_CUDA_TRY(dft16_wait_collect(&c));
+    FRLAP_CUDA_TRY(fn(&c));
     total += c;
   }
   *timeouts = total;
@@ -134,8 +136,8 @@ frlap_status frlap_bounds_check_report(int* enabled, unsigned long long* violati
                                        unsigned long long* first_address) {
   if (!violations) return fail(FRLAP_EINVAL, "violations is NULL");
   unsigned long long total = 0ull, first = ~0ull;
-  cudaError_t (*collect[3])(unsigned long long*, unsigned long long*) = {bc_collect<float>, bc_collect<double>,
-                                                                         bc_collect<dfl>};
+  cudaError_t (*collect[4])(unsigned long long*, unsigned long long*) = {bc_collect<float>, bc_collect<double>,
+                                                                         bc_collect<dfl>, hyb_bc_collect};
   for (auto fn : collect) {
     unsigned long long c = 0ull, f = ~0ull;
     FRLAP_CUDA_TRY(fn(&c, &f));
@@ -629,6 +631,18 @@ frlap_status frlap_pcg_solve(const frlap_plan* plan, const double* d_f, double* 
   if (rc != FRLAP_OK) return rc;
   return pcg_solve_impl(*plan, d_f, d_x, rtol, maxit, solver, mu, inner_rtol, iters, relres, d_work,
                         (cudaStream_t)stream);
+}
+
+frlap_status frlap_residual(const frlap_plan* plan, const double* d_f, const double* d_x, double* d_r,
+                            double* relres, void* d_work, void* stream) {
+  if (!plan || !d_f || !d_x || !relres) return fail(FRLAP_EINVAL, "plan, d_f, d_x or relres is NULL");
+  if (plan->prec == FRLAP_F32) return fail(FRLAP_EINVAL, "the residual needs an F64, MIXED or double-float plan");
+  const size_t vb = vector_bytes(*plan, false);
+  if (d_r && (ranges_overlap(d_r, d_f, vb) || ranges_overlap(d_r, d_x, vb)))
+    return fail(FRLAP_EINVAL, "d_r must not overlap d_f or d_x");
+  frlap_status rc = check_work(d_work);
+  if (rc != FRLAP_OK) return rc;
+  return residual_impl(*plan, d_f, d_x, d_r, relres, d_work, (cudaStream_t)stream);
 }
 
 frlap_status frlap_precond_strang(frlap_plan* plan, int* n_nonpositive, void* stream) {

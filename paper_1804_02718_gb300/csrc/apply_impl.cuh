@@ -767,6 +767,55 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_colmul(cplx<T>* __restrict__ 
   else store_line(v, data, ncols, n, ld, logP, TL);
 }
 
+// The middle stage of the residual apply of double-float plans (apply_launch_b<double, dfl>): the
+// forward transform and the symbol product in FP64, then each value split into a double-float pair
+// and the inverse transform in double-float.  The column is read as FP64 and written back in place
+// as double-float (16 bytes per complex value either way).  Rounding in the forward transform
+// reaches the product multiplied by up to lambda_max, so that transform keeps FP64; the inverse
+// transform's rounding is relative to the product itself, where double-float's 2^-48 suffices.
+template <int REM>
+__global__ void __launch_bounds__(kMaxCta<double>, 1)
+    k_colmul_hyb(double2* __restrict__ data, int ncols, int n, size_t ld, int logP, int TL,
+                 const double* __restrict__ lam, LamMap map, const double2* __restrict__ tw64,
+                 const cdf* __restrict__ twdf, const int* __restrict__ skip, Batch bt) {
+  {
+    const size_t bi = blockIdx.y;
+    data += bi * bt.in;
+    lam += bi * bt.lam;
+    if (skip) skip += bi * bt.skip;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* smem = reinterpret_cast<double2*>(smem_raw);
+  if (skip && FRLAP_GLD(skip)) return;
+  const int P = 1 << logP, G = P >> 4;
+  const int l = threadIdx.x / G, lane = threadIdx.x % G;
+  const int col = blockIdx.x * TL + l;
+  const bool valid = col < ncols;
+  double2* buf = smem + (size_t)l * sline(P);
+  const double2* line = data + (size_t)(valid ? col : 0) * ld;
+  double2 v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int i = lane + m * G;
+    v[m] = (m < 8 && valid && i < n) ? ld_stream(&line[i]) : czero<double2>();
+  }
+  fft_regs<double, -1, true, REM>(v, buf, logP, lane, tw64, logP, false);
+  const int c = valid ? col : 0;
+  const double* __restrict__ lrow =
+      map.d == 2 ? lam + (size_t)c * map.Hy1
+                 : lam + ((size_t)(c >> map.logPy) * map.Hy1 + min(c & (map.Py - 1), map.Py - (c & (map.Py - 1)))) *
+                             map.Hz1;
+  cdf w[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int k = lane + m * G;
+    const double2 t = ld_stream(&lrow[min(k, P - k)]) * v[m];
+    w[m] = make_cdf(df_from(t.x), df_from(t.y));
+  }
+  fft_regs<dfl, 1, false, REM>(w, reinterpret_cast<cdf*>(buf), logP, lane, twdf, logP, true);
+  store_line(w, reinterpret_cast<cdf*>(data), ncols, n, ld, logP, TL);
+}
+
 // groups of contiguous lines of length n -> pad, FFT, transposed store out[g][k][line]
 template <typename T, int REM, int LOGL = 0, bool ODD = false>
 __global__ void __launch_bounds__(kMaxCta<T>, 1) k_c2cT_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nlines, int tiles, int n,
@@ -1080,10 +1129,33 @@ cudaError_t launch_r2c_pf(const io_t<T>* u, cplx<T>* S1, int nrows, int nx, size
   }
 }
 
-template <typename T>
-static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T>* y, size_t vstride, void* work,
+// The hybrid middle stage (k_colmul_hyb), one instance per REM; a template so that only the
+// translation unit that runs it compiles it.
+template <int UNUSED = 0>
+cudaError_t launch_colmul_hyb(double2* data, int ncols, int n, size_t ld, int logP, int tl, const double* lam,
+                              LamMap map, const double2* tw64, const cdf* twdf, const int* skip, Batch b, int grid,
+                              int B, size_t sm, cudaStream_t s) {
+  const int G = 1 << (logP - 4);
+  return with_rem(logP, [&](auto tag) {
+    constexpr int REM = decltype(tag)::value;
+    cudaError_t e = set_smem(k_colmul_hyb<REM>, sm);
+    if (e != cudaSuccess) return e;
+    k_colmul_hyb<REM><<<dim3(grid, B), tl * G, sm, s>>>(data, ncols, n, ld, logP, tl, lam, map, tw64, twdf, skip, b);
+    return cudaGetLastError();
+  });
+}
+
+// TI: the engine of the inverse transforms (the last stage, the 3D inverse y stage and the middle
+// stage's inverse half); TI = T but for the residual apply of double-float plans, <double, dfl>
+// (k_colmul_hyb), which plans with the split middle stage do not take.
+template <typename T, typename TI = T>
+static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<TI>* y, size_t vstride, void* work,
                                   cudaStream_t s, const int* skip, int skip_stride, cudaEvent_t const* ev,
                                   const T* lam_override, size_t lam_stride, bool odd = false) {
+  constexpr bool kHyb = !std::is_same<T, TI>::value;
+  static_assert(!kHyb || (std::is_same<T, double>::value && std::is_same<TI, dfl>::value),
+                "apply_launch_b: the only mixed form is FP64 forward, double-float inverse");
+  if (kHyb && (odd || (p.d == 2 && p.P[1] > kMaxLine))) return cudaErrorNotSupported;
   // odd: the pipeline on odd extensions (a multiplier in the sine basis, see k_r2c_T); the FP32
   // engine only, P_r = 2(n_r + 1) on every axis (the callers check)
   if (odd && (!std::is_same<T, float>::value || p.P[1] > kMaxLine)) return cudaErrorNotSupported;
@@ -1102,6 +1174,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
   const int* tuned = p.tl_tuned[engine_index<T>()];
   const C* tw[3];
   for (int r = 0; r < 3; ++r) tw[r] = twiddle_table<T>(p, r);
+  using CI = cplx<TI>;
+  static_assert(sizeof(CI) == sizeof(C), "apply_launch_b: both engines keep the same bytes per value");
+  const int* tunedI = p.tl_tuned[engine_index<TI>()];
+  const CI* twI[3];
+  for (int r = 0; r < 3; ++r) twI[r] = twiddle_table<TI>(p, r);
   const T* lam = lam_override ? lam_override : symbol_table<T>(p);
   C* S1 = reinterpret_cast<C*>(work);
   C* S2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(work) + align256(p.s1_elems * eb));
@@ -1121,6 +1198,8 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     r.add(work, (size_t)B * apply_work_bytes(p, sizeof(T)));
     r.add(lam, ((size_t)(B - 1) * lam_stride + p.lam_count) * sizeof(T));
     for (int a = 0; a < p.d; ++a) r.add(tw[a], (size_t)twiddle_entries(p.P[a]) * sizeof(C));
+    if (kHyb)
+      for (int a = 0; a < p.d; ++a) r.add(twI[a], (size_t)twiddle_entries(p.P[a]) * sizeof(CI));
     if (skip) r.add(skip, ((size_t)(B - 1) * skip_stride + 1) * sizeof(int));
     cudaError_t e = r.commit(s);
     if (e != cudaSuccess) return e;
@@ -1197,13 +1276,17 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     Batch b_split = b_ws;  // columns in S1, the even half in S2 (same per-instance stride)
     cudaError_t e;
     if ((e = mark()) != cudaSuccess) return e;
-    if ((e = set_smem(k_colmul_split<T, false>, sm)) != cudaSuccess) return e;
-    if ((e = set_smem(k_colmul_split<T, true>, sm)) != cudaSuccess) return e;
-    k_colmul_split<T, false><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, ncols, ny, ld1, tl, lam, map.Hy1, tw[1], skip,
-                                                              b_split);
-    k_colmul_split<T, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, ncols, ny, ld1, tl, lam, map.Hy1, tw[1], skip,
-                                                             b_split);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if constexpr (kHyb) {
+      return cudaErrorNotSupported;  // refused above; no split instances in the hybrid's unit
+    } else {
+      if ((e = set_smem(k_colmul_split<T, false>, sm)) != cudaSuccess) return e;
+      if ((e = set_smem(k_colmul_split<T, true>, sm)) != cudaSuccess) return e;
+      k_colmul_split<T, false><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, ncols, ny, ld1, tl, lam, map.Hy1, tw[1],
+                                                                skip, b_split);
+      k_colmul_split<T, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, S2, ncols, ny, ld1, tl, lam, map.Hy1, tw[1],
+                                                               skip, b_split);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   } else if (p.d == 2) {
     const int G = p.P[1] >> 4;
     const int tl = pick_tl_tuned(tuned[1], sline(p.P[1]), eb, G, budget, (long long)(Hx + 1) * B);
@@ -1212,6 +1295,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
     const int ncols = Hx + 1;
     const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
+    if constexpr (kHyb) {
+      e = launch_colmul_hyb(reinterpret_cast<double2*>(S1), ncols, ny, ld1, logPy, tl,
+                            reinterpret_cast<const double*>(lam), map, reinterpret_cast<const double2*>(tw[1]),
+                            reinterpret_cast<const cdf*>(twI[1]), skip, b_ws, grid, B, sm, s);
+    } else {
     if constexpr (std::is_same<T, float>::value) {
       if (odd)
         e = with_rem(logPy, [&](auto tag) {
@@ -1231,6 +1319,7 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
         k_colmul<T, REM, LP><<<dim3(grid, B), tl * G, sm, s>>>(S1, ncols, ny, ld1, logPy, tl, lam, map, tw[1], logPy, skip, b_ws);
         return cudaGetLastError();
       });
+    }
     if (e != cudaSuccess) return e;
   } else {
     const int Py = p.P[1], Pz = p.P[2];
@@ -1274,6 +1363,11 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       const int ncols = (Hx + 1) * Py;
       const int grid = (ncols + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
+    if constexpr (kHyb) {
+      e = launch_colmul_hyb(reinterpret_cast<double2*>(S2), ncols, nz, (size_t)nz, logPz, tl,
+                            reinterpret_cast<const double*>(lam), map, reinterpret_cast<const double2*>(tw[2]),
+                            reinterpret_cast<const cdf*>(twI[2]), skip, b_ws, grid, B, sm, s);
+    } else {
     if constexpr (std::is_same<T, float>::value) {
       if (odd)
         e = with_rem(logPz, [&](auto tag) {
@@ -1293,65 +1387,69 @@ static cudaError_t apply_launch_b(const Plan& p, int B, const io_t<T>* u, io_t<T
       k_colmul<T, REM, LP><<<dim3(grid, B), tl * G, sm, s>>>(S2, ncols, nz, (size_t)nz, logPz, tl, lam, map, tw[2], logPz, skip, b_ws);
       return cudaGetLastError();
     });
+    }
     if (e != cudaSuccess) return e;
     }
-    // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y]
+    // ---- stage 4: S2[kx][ky][z] -> IFFT_y -> S1[kx][z][y] (engine TI)
     {
+      CI* S1i = reinterpret_cast<CI*>(S1);
+      CI* S2i = reinterpret_cast<CI*>(S2);
       const int G = Py >> 4;
-      const int tl = pick_tl_tuned(tuned[3], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
+      const int tl = pick_tl_tuned(tunedI[3], sline(Py), eb, G, budget, (long long)nz * (Hx + 1) * B);
       const size_t sm = (size_t)tl * sline(Py) * eb;
       cudaError_t e;
       const int tiles = (nz + tl - 1) / tl;
       const int grid = (Hx + 1) * tiles;
     if ((e = mark()) != cudaSuccess) return e;
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<TI, float>::value) {
       if (odd)
         e = with_rem(logPy, [&](auto tag) {
           constexpr int REM = decltype(tag)::value;
-          cudaError_t e2 = set_smem(k_c2cT_inv<T, REM, 0, true>, sm);
+          cudaError_t e2 = set_smem(k_c2cT_inv<TI, REM, 0, true>, sm);
           if (e2 != cudaSuccess) return e2;
-          k_c2cT_inv<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz,
-                                                                         (size_t)nz * ny, ny, logPy, tl, tw[1], logPy,
-                                                                         skip, b_ws);
+          k_c2cT_inv<TI, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S2i, S1i, nz, tiles, ny, (size_t)Py * nz, nz,
+                                                                          (size_t)nz * ny, ny, logPy, tl, twI[1], logPy,
+                                                                          skip, b_ws);
           return cudaGetLastError();
         });
     }
     if (!odd)
-    e = with_line_shape<T, std::is_same<T, float>::value>(logPy, [&](auto tag) {
+    e = with_line_shape<TI, std::is_same<TI, float>::value>(logPy, [&](auto tag) {
       constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
-      cudaError_t e2 = set_smem(k_c2cT_inv<T, REM, LL>, sm);
+      cudaError_t e2 = set_smem(k_c2cT_inv<TI, REM, LL>, sm);
       if (e2 != cudaSuccess) return e2;
-      k_c2cT_inv<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S2, S1, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny, logPy, tl, tw[1], logPy, skip, b_ws);
+      k_c2cT_inv<TI, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S2i, S1i, nz, tiles, ny, (size_t)Py * nz, nz, (size_t)nz * ny, ny, logPy, tl, twI[1], logPy, skip, b_ws);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
     }
   }
-  // ---- last stage: S1[kx][row] -> rows of y
+  // ---- last stage: S1[kx][row] -> rows of y (engine TI)
   {
+    const CI* S1i = reinterpret_cast<const CI*>(S1);
     const int G = Hx >> 4;
-    const int tl = pick_tl_tuned(tuned[p.d == 2 ? 2 : 4], sline(Hx), eb, G, budget, (long long)nrows * B);
+    const int tl = pick_tl_tuned(tunedI[p.d == 2 ? 2 : 4], sline(Hx), eb, G, budget, (long long)nrows * B);
     const size_t sm = (size_t)tl * sline(Hx) * eb;
     cudaError_t e;
     const int grid = (nrows + tl - 1) / tl;
     if ((e = mark()) != cudaSuccess) return e;
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<TI, float>::value) {
       if (odd)
         e = with_rem(logPx - 1, [&](auto tag) {
           constexpr int REM = decltype(tag)::value;
-          cudaError_t e2 = set_smem(k_c2r_T<T, REM, 0, true>, sm);
+          cudaError_t e2 = set_smem(k_c2r_T<TI, REM, 0, true>, sm);
           if (e2 != cudaSuccess) return e2;
-          k_c2r_T<T, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0],
-                                                                      logPx, skip, b_out);
+          k_c2r_T<TI, REM, 0, true><<<dim3(grid, B), tl * G, sm, s>>>(S1i, y, nrows, nx, ld1, nx, logPx - 1, tl, twI[0],
+                                                                       logPx, skip, b_out);
           return cudaGetLastError();
         });
     }
     if (!odd)
-      e = with_line_shape<T, std::is_same<T, float>::value>(logPx - 1, [&](auto tag) {
+      e = with_line_shape<TI, std::is_same<TI, float>::value>(logPx - 1, [&](auto tag) {
         constexpr int REM = decltype(tag)::rem, LL = decltype(tag)::logp;
-        cudaError_t e2 = set_smem(k_c2r_T<T, REM, LL>, sm);
+        cudaError_t e2 = set_smem(k_c2r_T<TI, REM, LL>, sm);
         if (e2 != cudaSuccess) return e2;
-        k_c2r_T<T, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S1, y, nrows, nx, ld1, nx, logPx - 1, tl, tw[0], logPx, skip, b_out);
+        k_c2r_T<TI, REM, LL><<<dim3(grid, B), tl * G, sm, s>>>(S1i, y, nrows, nx, ld1, nx, logPx - 1, tl, twI[0], logPx, skip, b_out);
         return cudaGetLastError();
       });
     if (e != cudaSuccess) return e;
@@ -1579,8 +1677,9 @@ cudaError_t autotune_engine(Plan& p, int B, io_t<T>* u, io_t<T>* y, void* work, 
   return e;
 }
 
-template <typename T>
-cudaError_t wait_collect(unsigned long long* count) {
+// The give-up count and the bounds-check state of the including translation unit (every unit that
+// includes this header has its own), read and reset.
+[[maybe_unused]] static cudaError_t unit_wait_collect(unsigned long long* count) {
   unsigned long long c = 0ull;
   cudaError_t e = cudaMemcpyFromSymbol(&c, g_wait_timeouts, sizeof(c));
   if (e != cudaSuccess) return e;
@@ -1590,8 +1689,7 @@ cudaError_t wait_collect(unsigned long long* count) {
   return e;
 }
 
-template <typename T>
-cudaError_t bc_collect(unsigned long long* count, unsigned long long* first) {
+[[maybe_unused]] static cudaError_t unit_bc_collect(unsigned long long* count, unsigned long long* first) {
 #ifdef FRLAP_BOUNDS_CHECK
   BcState st;
   cudaError_t e = cudaMemcpyFromSymbol(&st, g_bc_state, sizeof(st));
@@ -1606,6 +1704,15 @@ cudaError_t bc_collect(unsigned long long* count, unsigned long long* first) {
   *first = ~0ull;
   return cudaSuccess;
 #endif
+}
+
+template <typename T>
+cudaError_t wait_collect(unsigned long long* count) {
+  return unit_wait_collect(count);
+}
+template <typename T>
+cudaError_t bc_collect(unsigned long long* count, unsigned long long* first) {
+  return unit_bc_collect(count, first);
 }
 
 }  // namespace frlap

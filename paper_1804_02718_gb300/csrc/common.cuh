@@ -287,6 +287,11 @@ cudaError_t bc_collect(unsigned long long* count, unsigned long long* first);
 cudaError_t bc_selftest(unsigned long long* flagged);
 // Runs one bounded mbarrier wait that nothing completes; *timeouts = waits that gave up (1 expected).
 cudaError_t wait_selftest(unsigned long long* timeouts);
+// the residual apply of double-float plans (FP64 forward, double-float inverse transforms; see
+// apply_hyb.cu); cudaErrorNotSupported for other plans and for plans with a split middle stage
+cudaError_t apply_residual_hyb(const Plan& p, const double* u, double* y, void* work, cudaStream_t s);
+cudaError_t hyb_wait_collect(unsigned long long* count);
+cudaError_t hyb_bc_collect(unsigned long long* count, unsigned long long* first);
 // radix-16 stages on CUDA cores (engine 0) or tensor cores (engine 1); see dft16_tc.cu
 cudaError_t dft16_stages_launch(int engine, const float* in, float* out, int ntiles, int reps, cudaStream_t s);
 cudaError_t dft16_wait_collect(unsigned long long* count);

@@ -360,15 +360,25 @@ static cudaError_t apply_T(const Plan& p, const T* u, T* y, void* work, cudaStre
   else return apply_launch<float>(p, u, y, work, s, skip);
 }
 
-// The residuals f - B x that restart a solve or decide its convergence: FP64 vectors go
-// through the native FP64 engine, also on double-float plans.  The iterations may run on
-// double-float (48-bit products, 3x faster), but a residual computed with it carries that
-// rounding (about 5e-15 lambda_max ||x||), which at 2047^2 already sits near 1e-10 ||f||;
-// the native residual lets a restart remove the drift, as in iterative refinement.
+// The residuals f - B x that restart a solve or decide its convergence.  The iterations may run
+// on double-float (48-bit products, 5.6x faster than native FP64), but a residual computed with it
+// carries the forward transforms' rounding times up to lambda_max (about 5e-15 lambda_max ||x||),
+// which at 2047^2 already sits near 1e-10 ||f||.  So the forward transforms of a residual run in
+// native FP64: on double-float plans the hybrid apply (FP64 forward, double-float inverse
+// transforms, apply_hyb.cu), as accurate as native FP64 near a solution and 1.7x faster; native FP64
+// throughout on F64 plans and on plans with a split middle stage.  A restart from such a residual
+// removes the recurrence's drift, as in iterative refinement.
 template <typename T>
 static cudaError_t apply_residual(const Plan& p, const T* u, T* y, void* work, cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) return apply_launch<double>(p, u, y, work, s, nullptr);
-  else return apply_launch<float>(p, u, y, work, s, nullptr);
+  if constexpr (sizeof(T) == 8) {
+    if (p.df64) {
+      const cudaError_t e = apply_residual_hyb(p, u, y, work, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
+    return apply_launch<double>(p, u, y, work, s, nullptr);
+  } else {
+    return apply_launch<float>(p, u, y, work, s, nullptr);
+  }
 }
 
 // workspace of one (P)CG solve in precision T:
@@ -570,6 +580,12 @@ static frlap_status true_residual(const Plan& p, const double* f, const double* 
   FRLAP_CUDA_TRY(cudaStreamSynchronize(st));
   *relres = (h[1] > 0.0) ? sqrt(h[0] / h[1]) : 0.0;
   return FRLAP_OK;
+}
+
+// r = f - A x (r may be null) and ||r|| / ||f||, with the apply that decides convergence
+frlap_status residual_impl(const Plan& p, const double* f, const double* x, double* r, double* relres, void* work,
+                           cudaStream_t st) {
+  return true_residual(p, f, x, 0.0, 1.0, work, st, relres, r, nullptr, true);
 }
 
 // E[j] <- xs - E[j]
