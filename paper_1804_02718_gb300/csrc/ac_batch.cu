@@ -78,6 +78,12 @@ __device__ __forceinline__ bool inst_sum(double v, double* partials, unsigned* c
 }
 
 #define INST_LOOP(i, n) for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+// The iteration kernels take kU elements per thread and pass, one grid apart, all loaded before any
+// arithmetic (several loads in flight per warp; see the CG kernels); the u-th is base + u * gstride.
+constexpr int kU = 4;
+#define INST_LOOP_U(base, n)                                                                                 \
+  for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gstride = (size_t)gridDim.x * blockDim.x; \
+       base < (n); base += kU * gstride)
 
 // two per-instance sums (partial arrays pa, pb); true in thread 0 of the instance's last block
 __device__ __forceinline__ bool inst_sum2(double a, double b, double* pa, double* pb, unsigned* counter,
@@ -173,11 +179,25 @@ __global__ void k_ac_pq(const double* __restrict__ p, double* q, size_t M, size_
   p += b * vs;
   q += b * vs;
   double acc = 0.0;
-  INST_LOOP(i, M) {
-    const double pi = p[i];
-    const double qi = pi + s * q[i];
-    q[i] = qi;
-    acc += pi * qi;
+  INST_LOOP_U(b0, M) {
+    double pv[kU], qv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < M) {
+        pv[u] = p[i];
+        qv[u] = q[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < M) {
+        const double qi = pv[u] + s * qv[u];
+        q[i] = qi;
+        acc += pv[u] * qi;
+      }
+    }
   }
   double tot;
   if (inst_sum(acc, partials + (size_t)b * gridDim.x, &st->counter, &tot)) {
@@ -203,11 +223,28 @@ __global__ void k_ac_update(double* x, double* r, const double* __restrict__ p, 
   q += b * vs;
   const double al = st->alpha;
   double acc = 0.0;
-  INST_LOOP(i, M) {
-    x[i] += al * p[i];
-    const double ri = r[i] - al * q[i];
-    r[i] = ri;
-    acc += ri * ri;
+  INST_LOOP_U(b0, M) {
+    double xv[kU], rv[kU], pv[kU], qv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < M) {
+        xv[u] = x[i];
+        rv[u] = r[i];
+        pv[u] = p[i];
+        qv[u] = q[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < M) {
+        x[i] = xv[u] + al * pv[u];
+        const double ri = rv[u] - al * qv[u];
+        r[i] = ri;
+        acc += ri * ri;
+      }
+    }
   }
   double tot;
   if (inst_sum(acc, partials + (size_t)b * gridDim.x, &st->counter, &tot)) {
@@ -233,7 +270,22 @@ __global__ void k_ac_dir(const double* __restrict__ r, double* p, size_t M, size
   r += b * vs;
   p += b * vs;
   const double be = S[b].beta;
-  INST_LOOP(i, M) p[i] = r[i] + be * p[i];
+  INST_LOOP_U(b0, M) {
+    double rv[kU], pv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < M) {
+        rv[u] = r[i];
+        pv[u] = p[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < M) p[i] = rv[u] + be * pv[u];
+    }
+  }
 }
 
 // keep looping while an instance is unfinished; bounded by max_passes

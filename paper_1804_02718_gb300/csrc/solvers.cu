@@ -20,7 +20,7 @@ namespace frlap {
 
 namespace {
 
-constexpr int kBlocks = 2 * 152;  // grid of the vector kernels: two CTAs per SM
+constexpr int kBlocks = 2 * 152;  // grid of the vector kernels: two CTAs per SM (four measured slower)
 constexpr int kThreads = 512;
 // grid for n elements: two CTAs per SM, fewer for short vectors (the reductions use gridDim.x)
 inline unsigned vgrid(size_t n) {
@@ -93,6 +93,15 @@ __device__ __forceinline__ bool grid_sum2(double a, double b, double* partials, 
 #define GRID_STRIDE(i, n) \
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
 
+// The vector kernels of an iteration give each thread kU elements per pass, one grid apart (so each
+// warp's accesses stay coalesced), and load all of them before any arithmetic: with one element per
+// pass a warp had one or two loads in flight, and these kernels ran at 1-2 TB/s, latency-bound.
+// Inside, the u-th element of the pass is i = base + u * gstride (valid while i < n).
+constexpr int kU = 4;
+#define GRID_STRIDE_U(base, n)                                                                              \
+  for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gstride = (size_t)gridDim.x * blockDim.x; \
+       base < (n); base += kU * gstride)
+
 // r = f - (sigma x + s q) (q = A x when use_x); rr = r.r, fnorm2 = f.f; sets tol2, done
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, const T* __restrict__ q, T* r, size_t n,
@@ -130,11 +139,25 @@ template <typename T, typename TP>
 __global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, T* z, T* p, size_t n,
                             double* partials, CgState* S) {
   double a = 0.0;
-  GRID_STRIDE(i, n) {
-    const T zi = zp ? (T)zp[i] : r[i];
-    if (zp) z[i] = zi;
-    p[i] = zi;
-    a += (double)r[i] * (double)zi;
+  GRID_STRIDE_U(b0, n) {
+    T rv[kU], zv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        rv[u] = r[i];
+        zv[u] = zp ? (T)zp[i] : rv[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        if (zp) z[i] = zv[u];
+        p[i] = zv[u];
+        a += (double)rv[u] * (double)zv[u];
+      }
+    }
   }
   double ta, tb;
   if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
@@ -151,12 +174,31 @@ template <typename T>
 __global__ void k_cg_pq(const T* __restrict__ p, T* q, size_t n, double* partials, CgState* S) {
   if (S->done) return;
   const double sg = S->sigma, sc = S->s;
+  const bool plain = sg == 0.0 && sc == 1.0;  // B = A (the Poisson problem): q is already B p
   double a = 0.0;
-  GRID_STRIDE(i, n) {
-    const double pi = (double)p[i];
-    const T qi = (T)(sg * pi + sc * (double)q[i]);
-    q[i] = qi;
-    a += pi * (double)qi;
+  GRID_STRIDE_U(b0, n) {
+    T pv[kU], qv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        pv[u] = p[i];
+        qv[u] = q[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        const double pi = (double)pv[u];
+        T qi = qv[u];
+        if (!plain) {
+          qi = (T)(sg * pi + sc * (double)qi);
+          q[i] = qi;
+        }
+        a += pi * (double)qi;
+      }
+    }
   }
   double ta, tb;
   if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
@@ -178,11 +220,28 @@ __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __rest
   if (S->done) return;
   const double al = S->alpha;
   double a = 0.0;
-  GRID_STRIDE(i, n) {
-    x[i] = (T)((double)x[i] + al * (double)p[i]);
-    const T ri = (T)((double)r[i] - al * (double)q[i]);
-    r[i] = ri;
-    a += (double)ri * (double)ri;
+  GRID_STRIDE_U(b0, n) {
+    T xv[kU], rv[kU], pv[kU], qv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        xv[u] = x[i];
+        rv[u] = r[i];
+        pv[u] = p[i];
+        qv[u] = q[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        x[i] = (T)((double)xv[u] + al * (double)pv[u]);
+        const T ri = (T)((double)rv[u] - al * (double)qv[u]);
+        r[i] = ri;
+        a += (double)ri * (double)ri;
+      }
+    }
   }
   double ta, tb;
   if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
@@ -211,11 +270,27 @@ __global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, T
                            size_t n, double* partials, CgState* S) {
   if (S->done) return;
   double a = 0.0, b = 0.0;
-  GRID_STRIDE(i, n) {
-    const T zi = (T)zp[i];
-    if ((const void*)zp != (const void*)z) z[i] = zi;
-    a += (double)r[i] * (double)zi;
-    b += (double)zi * (double)q[i];
+  const bool copy = (const void*)zp != (const void*)z;
+  GRID_STRIDE_U(b0, n) {
+    T zv[kU], rv[kU], qv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        zv[u] = (T)zp[i];
+        rv[u] = r[i];
+        qv[u] = q[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        if (copy) z[i] = zv[u];
+        a += (double)rv[u] * (double)zv[u];
+        b += (double)zv[u] * (double)qv[u];
+      }
+    }
   }
   double ta, tb;
   if (grid_sum2(a, b, partials, &S->counter, &ta, &tb)) {
@@ -234,14 +309,41 @@ template <typename T>
 __global__ void k_cg_dir(const T* __restrict__ z, T* p, size_t n, const CgState* S) {
   if (S->done) return;
   const double b = S->beta;
-  GRID_STRIDE(i, n) p[i] = (T)((double)z[i] + b * (double)p[i]);
+  GRID_STRIDE_U(b0, n) {
+    T zv[kU], pv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) {
+        zv[u] = z[i];
+        pv[u] = p[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) p[i] = (T)((double)zv[u] + b * (double)pv[u]);
+    }
+  }
 }
 
 // FP32 copy of r for the preconditioner solve
 template <typename T>
 __global__ void k_to32(const T* __restrict__ r, float* r32, size_t n, const CgState* S) {
   if (S && S->done) return;
-  GRID_STRIDE(i, n) r32[i] = (float)r[i];
+  GRID_STRIDE_U(b0, n) {
+    T rv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) rv[u] = r[i];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * gstride;
+      if (i < n) r32[i] = (float)rv[u];
+    }
+  }
 }
 
 __global__ void k_set_state(CgState* S, double sigma, double s) {
