@@ -420,7 +420,6 @@ __global__ void __launch_bounds__(kMaxCta<T>, 1) k_r2c_pf(const io_t<T>* __restr
   using C = cplx<T>;
   using IO = io_t<T>;
   constexpr int E = (int)sizeof(IO);
-  constexpr int A = 16 / E;  // elements per 16 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
   const int H = 1 << logH, G = H >> 4;
