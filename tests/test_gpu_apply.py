@@ -111,6 +111,16 @@ def test_apply_fp32_matches_oracle(frlap, d, Ns, alpha):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("d,Ns,alpha", [(2, (40, 256), 1.3), (3, (12, 10, 256), 0.9), (2, (256, 256), 1.7),
+                                        (3, (9, 256, 5), 1.2)])
+def test_apply_fp32_512_point_lines(frlap, d, Ns, alpha):
+    """FP32 applies with 512-point lines (the 255^3 workload's z stage, and the 2D middle stage at
+    N_y = 256), with ragged column counts; the last case has its 512-point lines on y."""
+    u = inp.normal_field(Ns, seed=4)
+    err, *_ = _apply_case(frlap, d, Ns, alpha, u, frlap.FRLAP_F32)
+    assert err <= 1e-5, err
+
+
 @pytest.mark.parametrize("d,Ns,alpha,gamma", [(2, (40, 56), 1.3, 1.7), (3, (12, 10, 14), 0.9, 1.5)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-12), (1, 1e-5)])
 def test_apply_gamma_variant_matches_oracle(frlap, d, Ns, alpha, gamma, prec, tol):
@@ -188,7 +198,8 @@ def test_apply_255_cubed_sampled_rows(frlap, prec, tol):
 
 @pytest.mark.parametrize("d,Ns,alpha,prec,tol", [
     (2, (64, 40), 1.3, 0, 1e-12), (2, (64, 40), 1.3, 1, 1e-5), (2, (64, 40), 1.3, 3, 1e-12),
-    (3, (12, 20, 9), 0.7, 0, 1e-12), (3, (12, 20, 9), 0.7, 1, 1e-5), (3, (12, 20, 9), 0.7, 3, 1e-12)])
+    (3, (12, 20, 9), 0.7, 0, 1e-12), (3, (12, 20, 9), 0.7, 1, 1e-5), (3, (12, 20, 9), 0.7, 3, 1e-12),
+    (3, (8, 6, 256), 1.1, 1, 1e-5), (2, (24, 256), 1.6, 1, 1e-5)])
 def test_apply_batch_matches_oracle(frlap, d, Ns, alpha, prec, tol):
     """frlap_apply_batch: every instance of the batch against the oracle, and bit for bit equal to
     frlap_apply of that instance (the batch only adds a grid dimension)."""
