@@ -102,10 +102,11 @@ constexpr int kU = 4;
   for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gstride = (size_t)gridDim.x * blockDim.x; \
        base < (n); base += kU * gstride)
 
-// r = f - (sigma x + s q) (q = A x when use_x); rr = r.r, fnorm2 = f.f; sets tol2, done
+// r = f - (sigma x + s q) (q = A x when use_x); rr = r.r, fnorm2 = f.f; sets tol2, done; r32 (may be
+// null): an FP32 copy of r for the preconditioner
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, const T* __restrict__ q, T* r, size_t n,
-                          double* partials, CgState* S, double rtol, int use_x) {
+                          double* partials, CgState* S, double rtol, int use_x, float* __restrict__ r32) {
   double a = 0.0, b = 0.0;
   const double sg = S->sigma, sc = S->s;
   GRID_STRIDE(i, n) {
@@ -114,6 +115,7 @@ __global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, cons
     if (use_x) ri = fi - (sg * (double)x[i] + sc * (double)q[i]);
     const T rt = (T)ri;
     r[i] = rt;
+    if (r32) r32[i] = (float)rt;
     a += (double)rt * (double)rt;
     b += fi * fi;
   }
@@ -134,10 +136,10 @@ __global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, cons
   }
 }
 
-// z (from the preconditioner output zp, or r itself), p = z, rz = r.z
+// p = z (the preconditioner output zp, or r itself), rz = r.z
 template <typename T, typename TP>
-__global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, T* z, T* p, size_t n,
-                            double* partials, CgState* S) {
+__global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, T* p, size_t n, double* partials,
+                            CgState* S) {
   double a = 0.0;
   GRID_STRIDE_U(b0, n) {
     T rv[kU], zv[kU];
@@ -153,7 +155,6 @@ __global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, 
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
       if (i < n) {
-        if (zp) z[i] = zv[u];
         p[i] = zv[u];
         a += (double)rv[u] * (double)zv[u];
       }
@@ -214,9 +215,10 @@ __global__ void k_cg_pq(const T* __restrict__ p, T* q, size_t n, double* partial
 
 // x += alpha p ; r -= alpha q ; rr = r.r ; convergence test.  Without a preconditioner also
 // beta = rr_new / rr_old (z = r).  With one, beta is formed after the preconditioner solve.
+// r32 (may be null): an FP32 copy of the new r for the preconditioner
 template <typename T>
 __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __restrict__ q, size_t n,
-                            double* partials, CgState* S, int maxit, int precond) {
+                            double* partials, CgState* S, int maxit, int precond, float* __restrict__ r32) {
   if (S->done) return;
   const double al = S->alpha;
   double a = 0.0;
@@ -239,6 +241,7 @@ __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __rest
         x[i] = (T)((double)xv[u] + al * (double)pv[u]);
         const T ri = (T)((double)rv[u] - al * (double)qv[u]);
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         a += (double)ri * (double)ri;
       }
     }
@@ -263,14 +266,13 @@ __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __rest
   }
 }
 
-// after z = M^-1 r: z from the preconditioner output; rz_new = r.z, zq = z.q;
+// after z = M^-1 r (the preconditioner output zp): rz_new = r.z, zq = z.q;
 // flexible (Polak-Ribiere) beta = z.(r_new - r_old) / rz_old = -alpha zq / rz_old
 template <typename T, typename TP>
-__global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, T* z, const T* __restrict__ q,
-                           size_t n, double* partials, CgState* S) {
+__global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, const T* __restrict__ q, size_t n,
+                           double* partials, CgState* S) {
   if (S->done) return;
   double a = 0.0, b = 0.0;
-  const bool copy = (const void*)zp != (const void*)z;
   GRID_STRIDE_U(b0, n) {
     T zv[kU], rv[kU], qv[kU];
 #pragma unroll
@@ -286,7 +288,6 @@ __global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, T
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
       if (i < n) {
-        if (copy) z[i] = zv[u];
         a += (double)rv[u] * (double)zv[u];
         b += (double)zv[u] * (double)qv[u];
       }
@@ -304,13 +305,14 @@ __global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, T
   }
 }
 
-// p = z + beta p
-template <typename T>
-__global__ void k_cg_dir(const T* __restrict__ z, T* p, size_t n, const CgState* S) {
+// p = z + beta p (z: the preconditioner output, or r itself)
+template <typename T, typename TZ>
+__global__ void k_cg_dir(const TZ* __restrict__ z, T* p, size_t n, const CgState* S) {
   if (S->done) return;
   const double b = S->beta;
   GRID_STRIDE_U(b0, n) {
-    T zv[kU], pv[kU];
+    TZ zv[kU];
+    T pv[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
@@ -327,24 +329,6 @@ __global__ void k_cg_dir(const T* __restrict__ z, T* p, size_t n, const CgState*
   }
 }
 
-// FP32 copy of r for the preconditioner solve
-template <typename T>
-__global__ void k_to32(const T* __restrict__ r, float* r32, size_t n, const CgState* S) {
-  if (S && S->done) return;
-  GRID_STRIDE_U(b0, n) {
-    T rv[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const size_t i = b0 + u * gstride;
-      if (i < n) rv[u] = r[i];
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const size_t i = b0 + u * gstride;
-      if (i < n) r32[i] = (float)rv[u];
-    }
-  }
-}
 
 __global__ void k_set_state(CgState* S, double sigma, double s) {
   S->sigma = sigma;
@@ -539,10 +523,7 @@ template <typename T>
 static cudaError_t precondition(const Plan& p, const CgBufs& b, const float* mu, bool odd, cudaStream_t st) {
   const float* src;
   if constexpr (sizeof(T) == 8) {
-    k_to32<T><<<vgrid(p.M), kThreads, 0, st>>>(reinterpret_cast<const T*>(b.r), b.r32, p.M, b.S);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    src = b.r32;
+    src = b.r32;  // written with r by k_cg_init / k_cg_update
     return apply_launch<float>(p, src, b.z32, b.awork32, st, &b.S->done, nullptr, mu, odd);
   } else {
     src = reinterpret_cast<const float*>(b.r);
@@ -560,7 +541,6 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
   T* r = reinterpret_cast<T*>(b.r);
   T* pv = reinterpret_cast<T*>(b.p);
   T* q = reinterpret_cast<T*>(b.q);
-  T* z = mu ? reinterpret_cast<T*>(b.z) : r;
   CgState* S = b.S;
   const size_t n = p.M;
   k_set_state<<<1, 1, 0, st>>>(S, sigma, s);
@@ -570,14 +550,15 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
     cudaError_t e = use_x0 == 2 ? apply_residual<T>(p, x, q, b.awork, st) : apply_T<T>(p, x, q, b.awork, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "apply (initial residual)");
   }
-  k_cg_init<T><<<vgrid(n), kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0);
+  float* r32 = (mu && sizeof(T) == 8) ? b.r32 : nullptr;  // FP64 solves hand the preconditioner an FP32 r
+  k_cg_init<T><<<vgrid(n), kThreads, 0, st>>>(f, x, q, r, n, b.partials, S, rtol, use_x0, r32);
   FRLAP_LAUNCH_CHECK("k_cg_init");
   if (mu) {
     cudaError_t e = precondition<T>(p, b, mu, odd, st);
     if (e != cudaSuccess) return cuda_fail(e, "preconditioner");
-    k_pcg_start<T, float><<<vgrid(n), kThreads, 0, st>>>(r, b.z32, z, pv, n, b.partials, S);
+    k_pcg_start<T, float><<<vgrid(n), kThreads, 0, st>>>(r, b.z32, pv, n, b.partials, S);
   } else {
-    k_pcg_start<T, T><<<vgrid(n), kThreads, 0, st>>>(r, nullptr, z, pv, n, b.partials, S);
+    k_pcg_start<T, T><<<vgrid(n), kThreads, 0, st>>>(r, nullptr, pv, n, b.partials, S);
   }
   FRLAP_LAUNCH_CHECK("k_pcg_start");
   if (snap && nsnap > 0) FRLAP_CUDA_TRY(cudaMemcpyAsync(snap, x, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
@@ -587,7 +568,7 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
     cudaError_t e = apply_T<T>(p, pv, q, b.awork, ss, done);
     if (e != cudaSuccess) return e;
     k_cg_pq<T><<<vgrid(n), kThreads, 0, ss>>>(pv, q, n, b.partials, S);
-    k_cg_update<T><<<vgrid(n), kThreads, 0, ss>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr);
+    k_cg_update<T><<<vgrid(n), kThreads, 0, ss>>>(x, r, pv, q, n, b.partials, S, maxit, mu != nullptr, r32);
     if (snap && it + 1 < nsnap) {
       e = cudaMemcpyAsync(snap + (size_t)(it + 1) * n, x, n * sizeof(T), cudaMemcpyDeviceToDevice, ss);
       if (e != cudaSuccess) return e;
@@ -595,9 +576,11 @@ static frlap_status run_cg(const Plan& p, const T* f, T* x, double sigma, double
     if (mu) {
       e = precondition<T>(p, b, mu, odd, ss);
       if (e != cudaSuccess) return e;
-      k_pcg_beta<T, float><<<vgrid(n), kThreads, 0, ss>>>(r, b.z32, z, q, n, b.partials, S);
+      k_pcg_beta<T, float><<<vgrid(n), kThreads, 0, ss>>>(r, b.z32, q, n, b.partials, S);
+      k_cg_dir<T, float><<<vgrid(n), kThreads, 0, ss>>>(b.z32, pv, n, S);
+    } else {
+      k_cg_dir<T, T><<<vgrid(n), kThreads, 0, ss>>>(r, pv, n, S);
     }
-    k_cg_dir<T><<<vgrid(n), kThreads, 0, ss>>>(z, pv, n, S);
     return cudaGetLastError();
   };
   // The first iterations run as plain launches; when the solve goes on (and takes no
