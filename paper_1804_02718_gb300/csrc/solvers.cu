@@ -12,6 +12,8 @@
 // in block order), so results are deterministic.
 #include <math.h>
 
+#include <type_traits>
+
 #include <vector>
 
 #include "common.cuh"
@@ -98,6 +100,12 @@ __device__ __forceinline__ bool grid_sum2(double a, double b, double* partials, 
 // pass a warp had one or two loads in flight, and these kernels ran at 1-2 TB/s, latency-bound.
 // Inside, the u-th element of the pass is i = base + u * gstride (valid while i < n).
 constexpr int kU = 4;
+// Element arithmetic and per-thread partial sums of the iteration kernels: FP32 for FP32 vectors (the
+// inner solves of iterative refinement, which aim at 1e-4), FP64 otherwise; the block and grid sums are
+// FP64 either way.  FP64 arithmetic and FP32-FP64 conversions run far below the FP32 rate here, and in
+// FP64 they made the FP32 update kernel 3x slower than its memory traffic.
+template <typename T>
+using acc_t = typename std::conditional<sizeof(T) == 4, float, double>::type;
 #define GRID_STRIDE_U(base, n)                                                                              \
   for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gstride = (size_t)gridDim.x * blockDim.x; \
        base < (n); base += kU * gstride)
@@ -140,7 +148,8 @@ __global__ void k_cg_init(const T* __restrict__ f, const T* __restrict__ x, cons
 template <typename T, typename TP>
 __global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, T* p, size_t n, double* partials,
                             CgState* S) {
-  double a = 0.0;
+  using A = acc_t<T>;
+  A a = 0;
   GRID_STRIDE_U(b0, n) {
     T rv[kU], zv[kU];
 #pragma unroll
@@ -156,12 +165,12 @@ __global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, 
       const size_t i = b0 + u * gstride;
       if (i < n) {
         p[i] = zv[u];
-        a += (double)rv[u] * (double)zv[u];
+        a += (A)rv[u] * (A)zv[u];
       }
     }
   }
   double ta, tb;
-  if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
+  if (grid_sum2((double)a, 0.0, partials, &S->counter, &ta, &tb)) {
     S->rz = ta;
     if (zp && !(ta > 0.0) && !S->done) {
       S->status = isfinite(ta) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
@@ -174,9 +183,10 @@ __global__ void k_pcg_start(const T* __restrict__ r, const TP* __restrict__ zp, 
 template <typename T>
 __global__ void k_cg_pq(const T* __restrict__ p, T* q, size_t n, double* partials, CgState* S) {
   if (S->done) return;
-  const double sg = S->sigma, sc = S->s;
-  const bool plain = sg == 0.0 && sc == 1.0;  // B = A (the Poisson problem): q is already B p
-  double a = 0.0;
+  using A = acc_t<T>;
+  const A sg = (A)S->sigma, sc = (A)S->s;
+  const bool plain = S->sigma == 0.0 && S->s == 1.0;  // B = A (the Poisson problem): q is already B p
+  A a = 0;
   GRID_STRIDE_U(b0, n) {
     T pv[kU], qv[kU];
 #pragma unroll
@@ -191,18 +201,18 @@ __global__ void k_cg_pq(const T* __restrict__ p, T* q, size_t n, double* partial
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
       if (i < n) {
-        const double pi = (double)pv[u];
+        const A pi = (A)pv[u];
         T qi = qv[u];
         if (!plain) {
-          qi = (T)(sg * pi + sc * (double)qi);
+          qi = (T)(sg * pi + sc * (A)qi);
           q[i] = qi;
         }
-        a += pi * (double)qi;
+        a += pi * (A)qi;
       }
     }
   }
   double ta, tb;
-  if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
+  if (grid_sum2((double)a, 0.0, partials, &S->counter, &ta, &tb)) {
     S->pq = ta;
     if (!(ta > 0.0) || !isfinite(ta)) {
       S->status = isfinite(ta) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
@@ -220,8 +230,9 @@ template <typename T>
 __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __restrict__ q, size_t n,
                             double* partials, CgState* S, int maxit, int precond, float* __restrict__ r32) {
   if (S->done) return;
-  const double al = S->alpha;
-  double a = 0.0;
+  using A = acc_t<T>;
+  const A al = (A)S->alpha;
+  A a = 0;
   GRID_STRIDE_U(b0, n) {
     T xv[kU], rv[kU], pv[kU], qv[kU];
 #pragma unroll
@@ -238,16 +249,16 @@ __global__ void k_cg_update(T* x, T* r, const T* __restrict__ p, const T* __rest
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
       if (i < n) {
-        x[i] = (T)((double)xv[u] + al * (double)pv[u]);
-        const T ri = (T)((double)rv[u] - al * (double)qv[u]);
+        x[i] = (T)((A)xv[u] + al * (A)pv[u]);
+        const T ri = (T)((A)rv[u] - al * (A)qv[u]);
         r[i] = ri;
         if (r32) r32[i] = (float)ri;
-        a += (double)ri * (double)ri;
+        a += (A)ri * (A)ri;
       }
     }
   }
   double ta, tb;
-  if (grid_sum2(a, 0.0, partials, &S->counter, &ta, &tb)) {
+  if (grid_sum2((double)a, 0.0, partials, &S->counter, &ta, &tb)) {
     if (!precond) {
       S->beta = ta / S->rz;
       S->rz = ta;
@@ -272,7 +283,8 @@ template <typename T, typename TP>
 __global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, const T* __restrict__ q, size_t n,
                            double* partials, CgState* S) {
   if (S->done) return;
-  double a = 0.0, b = 0.0;
+  using A = acc_t<T>;
+  A a = 0, b = 0;
   GRID_STRIDE_U(b0, n) {
     T zv[kU], rv[kU], qv[kU];
 #pragma unroll
@@ -288,13 +300,13 @@ __global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, c
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
       if (i < n) {
-        a += (double)rv[u] * (double)zv[u];
-        b += (double)zv[u] * (double)qv[u];
+        a += (A)rv[u] * (A)zv[u];
+        b += (A)zv[u] * (A)qv[u];
       }
     }
   }
   double ta, tb;
-  if (grid_sum2(a, b, partials, &S->counter, &ta, &tb)) {
+  if (grid_sum2((double)a, (double)b, partials, &S->counter, &ta, &tb)) {
     if (!(ta > 0.0) || !isfinite(ta)) {
       S->status = isfinite(ta) ? FRLAP_EBREAKDOWN : FRLAP_ENAN;
       S->done = 1;
@@ -309,7 +321,8 @@ __global__ void k_pcg_beta(const T* __restrict__ r, const TP* __restrict__ zp, c
 template <typename T, typename TZ>
 __global__ void k_cg_dir(const TZ* __restrict__ z, T* p, size_t n, const CgState* S) {
   if (S->done) return;
-  const double b = S->beta;
+  using A = acc_t<T>;
+  const A b = (A)S->beta;
   GRID_STRIDE_U(b0, n) {
     TZ zv[kU];
     T pv[kU];
@@ -324,7 +337,7 @@ __global__ void k_cg_dir(const TZ* __restrict__ z, T* p, size_t n, const CgState
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const size_t i = b0 + u * gstride;
-      if (i < n) p[i] = (T)((double)zv[u] + b * (double)pv[u]);
+      if (i < n) p[i] = (T)((A)zv[u] + b * (A)pv[u]);
     }
   }
 }
