@@ -88,3 +88,25 @@ def test_short_vectors_refused_before_any_launch(fn):
         call(plan, torch.zeros(100, dtype=dt), torch.zeros(50, dtype=dt))
     with pytest.raises(ValueError, match="f has 7 entries"):
         _binding.frlap_pcg_solve(plan, torch.zeros(7, dtype=torch.float64))
+
+
+def test_residual_and_dft16_refused_before_any_launch(built):
+    """frlap_residual and frlap_dft16_stages check their arguments on the host: wrong lengths and shapes
+    in the binding, a NULL plan, an invalid engine and misaligned or negative sizes in the library."""
+    import torch
+    from paper_1804_02718_gb300 import _binding
+    plan = _FakePlan(100)
+    with pytest.raises(ValueError, match="x has 99 entries"):
+        _binding.frlap_residual(plan, torch.zeros(100, dtype=torch.float64), torch.zeros(99, dtype=torch.float64))
+    with pytest.raises(ValueError, match="shape"):
+        _binding.frlap_dft16_stages(0, torch.zeros(2, 64, 32), 1)
+    with pytest.raises(TypeError):  # a host tensor never reaches the library
+        _binding.frlap_dft16_stages(0, torch.zeros(2, 128, 32), 1)
+    L = _binding.lib()
+    rel = ctypes.c_double()
+    assert L.frlap_residual(None, None, None, None, ctypes.byref(rel), None, None) == 1
+    assert L.frlap_dft16_stages(2, None, None, 1, 1, None) == 1          # unknown engine
+    assert L.frlap_dft16_stages(0, None, None, -1, 1, None) == 1         # negative tile count
+    assert L.frlap_dft16_stages(1, None, None, 0, 1, None) == 0          # nothing to do
+    assert L.frlap_dft16_stages(0, None, None, 1, 1, None) == 1          # NULL buffers
+    assert L.frlap_dft16_stages(0, ctypes.c_void_p(8), ctypes.c_void_p(8), 1, 1, None) == 1  # misaligned
